@@ -1,0 +1,323 @@
+/*
+ * ORACLE -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow CPU restatement of what the subgraph-matching path computes.
+ * Only the test suite, the package smoke check and the benchmark's CPU
+ * baseline may load it; the CUDA library never does, and the two share no
+ * code.
+ *
+ * Contents
+ *   1. Data graph: symmetrised, loop-free, duplicate-free adjacency with sorted
+ *      neighbour lists (the paper studies simple undirected graphs, Sec. II-A).
+ *   2. oracle_match: the problem statement of Sec. II-A -- every injective map
+ *      M: V(q) -> V(G) with l_q(u) = l_G(M(u)) and (M(u), M(u')) in E(G) for
+ *      every query edge (Definition 1) -- found by plain backtracking over G
+ *      with no auxiliary structure.  Optional per-query-vertex allowed sets
+ *      restrict M(u) (used to count one partition of the search space, and to
+ *      count the partial results that a search over the candidate search
+ *      tree must extend).
+ *   3. CST restatement (Algorithm 1, Sec. IV-A), the workload estimate
+ *      (Sec. IV-C) and the partition of Algorithm 2 live in cst_ref.c.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int64_t n;
+    int64_t* off;      /* [n+1] */
+    int32_t* adj;      /* [off[n]] sorted, unique, no self loops */
+    int32_t* lab;      /* [n] */
+} og;
+
+static int cmp_i32(const void* a, const void* b) {
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+og* oracle_graph_new(int64_t n, int64_t m, const int32_t* edges, const int32_t* labels) {
+    og* g = (og*)calloc(1, sizeof(og));
+    if (!g) return NULL;
+    g->n = n;
+    g->off = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    g->lab = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!g->off || !g->lab || !deg) return NULL;
+    memcpy(g->lab, labels, (size_t)n * sizeof(int32_t));
+    for (int64_t e = 0; e < m; e++) {
+        int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        if (a < 0 || b < 0 || a >= n || b >= n) { free(deg); return NULL; }
+        if (a == b) continue;
+        deg[a]++; deg[b]++;
+    }
+    int64_t* pos = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+    pos[0] = 0;
+    for (int64_t v = 0; v < n; v++) pos[v + 1] = pos[v] + deg[v];
+    int32_t* raw = (int32_t*)malloc((size_t)(pos[n] > 0 ? pos[n] : 1) * sizeof(int32_t));
+    int64_t* cur = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+    memcpy(cur, pos, ((size_t)n + 1) * sizeof(int64_t));
+    for (int64_t e = 0; e < m; e++) {
+        int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        if (a == b) continue;
+        raw[cur[a]++] = b; raw[cur[b]++] = a;
+    }
+    /* sort each list, drop repeats */
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t v = 0; v < n; v++) {
+        int64_t s = pos[v], e = pos[v + 1];
+        qsort(raw + s, (size_t)(e - s), sizeof(int32_t), cmp_i32);
+        int64_t w = s;
+        for (int64_t i = s; i < e; i++)
+            if (i == s || raw[i] != raw[i - 1]) raw[w++] = raw[i];
+        deg[v] = w - s;
+    }
+    for (int64_t v = 0; v < n; v++) g->off[v + 1] = g->off[v] + deg[v];
+    g->adj = (int32_t*)malloc((size_t)(g->off[n] > 0 ? g->off[n] : 1) * sizeof(int32_t));
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t v = 0; v < n; v++)
+        memcpy(g->adj + g->off[v], raw + pos[v], (size_t)deg[v] * sizeof(int32_t));
+    free(raw); free(cur); free(pos); free(deg);
+    return g;
+}
+
+void oracle_graph_free(og* g) {
+    if (!g) return;
+    free(g->off); free(g->adj); free(g->lab); free(g);
+}
+
+int64_t oracle_graph_nadj(const og* g) { return g->off[g->n]; }
+
+void oracle_graph_csr(const og* g, int64_t* off, int32_t* adj) {
+    memcpy(off, g->off, ((size_t)g->n + 1) * sizeof(int64_t));
+    memcpy(adj, g->adj, (size_t)g->off[g->n] * sizeof(int32_t));
+}
+
+/* (a, b) in E(G), by binary search in a's sorted list */
+static int has_edge(const og* g, int32_t a, int32_t b) {
+    int64_t lo = g->off[a], hi = g->off[a + 1];
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (g->adj[mid] < b) lo = mid + 1; else hi = mid;
+    }
+    return lo < g->off[a + 1] && g->adj[lo] == b;
+}
+
+static int in_sorted(const int32_t* a, int64_t n, int32_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo < n && a[lo] == x;
+}
+
+/* ------------------------------------------------------------ search */
+
+#define OMAXK 64
+
+typedef struct {
+    const og* g;
+    int k;
+    const int32_t* ql;
+    int order[OMAXK];          /* position -> query vertex */
+    int par[OMAXK];            /* position -> position of the vertex we extend from */
+    int nb[OMAXK];             /* number of other earlier neighbours */
+    int bn[OMAXK][OMAXK];      /* their positions */
+    const int64_t* aoff;       /* allowed sets, per query vertex */
+    const int32_t* av;
+    const uint8_t* aon;
+    int64_t max_emb;
+    int32_t* emb;
+    int64_t* emb_slot;         /* shared slot counter */
+    int64_t budget;
+} sctx;
+
+typedef struct {
+    uint64_t count;
+    uint64_t depth[OMAXK];     /* valid partial results with d+1 positions mapped */
+    double balg;               /* list bytes read to extend them (see oracle_match) */
+    int64_t nodes;
+    int over;
+} sacc;
+
+static int allowed(const sctx* c, int u, int32_t v) {
+    if (!c->aon || !c->aon[u]) return 1;
+    return in_sorted(c->av + c->aoff[u], c->aoff[u + 1] - c->aoff[u], v);
+}
+
+/* |{w in N_G(x) : l(w) = l_q(u), w allowed for u}| -- the length of the list
+ * the candidate search tree holds for x towards u when the allowed sets are
+ * the tree's candidate sets. */
+static int64_t list_len(const sctx* c, int32_t x, int u) {
+    const og* g = c->g;
+    int64_t n = 0;
+    for (int64_t i = g->off[x]; i < g->off[x + 1]; i++) {
+        int32_t w = g->adj[i];
+        if (g->lab[w] == c->ql[u] && allowed(c, u, w)) n++;
+    }
+    return n;
+}
+
+static void emit(const sctx* c, const int32_t* M) {
+    if (!c->emb || c->max_emb <= 0) return;
+    int64_t s = __atomic_fetch_add(c->emb_slot, 1, __ATOMIC_RELAXED);
+    if (s >= c->max_emb) return;
+    for (int i = 0; i < c->k; i++) c->emb[s * c->k + c->order[i]] = M[i];
+}
+
+static void extend(const sctx* c, sacc* a, int32_t* M, int d, int want_balg) {
+    /* M[0..d) maps positions 0..d-1 and is a valid partial embedding */
+    a->depth[d - 1]++;
+    if (d == c->k) { a->count++; emit(c, M); return; }
+    if (a->over) return;
+    const og* g = c->g;
+    int u = c->order[d];
+    int32_t x = M[c->par[d]];
+    a->nodes += 1 + (g->off[x + 1] - g->off[x]);
+    if (c->budget > 0 && a->nodes > c->budget) { a->over = 1; return; }
+    if (want_balg) {
+        a->balg += 8.0 + 4.0 * (double)list_len(c, x, u);
+        for (int j = 0; j < c->nb[d]; j++)
+            a->balg += 8.0 + 4.0 * (double)list_len(c, M[c->bn[d][j]], u);
+    }
+    /* candidates: N_G(x), or the allowed set of u when that is shorter
+     * (then adjacency to x is tested by binary search) */
+    int64_t na = (c->aon && c->aon[u]) ? c->aoff[u + 1] - c->aoff[u] : -1;
+    int from_allow = na >= 0 && na < g->off[x + 1] - g->off[x];
+    int64_t lo = from_allow ? c->aoff[u] : g->off[x];
+    int64_t hi = from_allow ? c->aoff[u + 1] : g->off[x + 1];
+    for (int64_t i = lo; i < hi; i++) {
+        int32_t v = from_allow ? c->av[i] : g->adj[i];
+        if (g->lab[v] != c->ql[u]) continue;
+        if (from_allow && !has_edge(g, x, v)) continue;
+        int ok = 1;
+        for (int j = 0; j < d && ok; j++) if (M[j] == v) ok = 0;          /* injective */
+        for (int j = 0; j < c->nb[d] && ok; j++)
+            if (!has_edge(g, M[c->bn[d][j]], v)) ok = 0;                     /* edges */
+        if (!ok || (!from_allow && !allowed(c, u, v))) continue;
+        M[d] = v;
+        extend(c, a, M, d + 1, want_balg);
+        if (a->over) return;
+    }
+}
+
+/*
+ * Enumerate all embeddings of q in G (Definition 1).
+ *
+ * q: k vertices with labels ql[k], nqe undirected edges qe[nqe][2].
+ * order: position -> query vertex (NULL: breadth-first from query vertex 0,
+ *        neighbours in increasing id).  Every position after the first must
+ *        have an earlier neighbour; par[] (NULL: the earliest such neighbour)
+ *        names the position whose image's neighbours are scanned.
+ * allow_on[u] != 0 restricts M(u) to the sorted set
+ *        allow_v[allow_off[u] .. allow_off[u+1]).
+ * Outputs: *count_out = number of embeddings; up to max_emb of them in
+ *        emb_out[max_emb][k] indexed by query vertex id (any order);
+ *        depth_out[d] (nullable) = number of partial embeddings of the first
+ *        d+1 positions that satisfy labels, injectivity, every edge among
+ *        them and the allowed sets; *balg_out (nullable) = for every such
+ *        partial embedding of d = 1..k-1 positions, 8 + 4*|list| bytes for
+ *        the list it is extended from and for each other earlier neighbour's
+ *        list, where a list is N_G(x) restricted to the next query vertex's
+ *        label and allowed set.
+ * Returns 0, 1 when some thread exceeded node_budget (>0) work units (one
+ * per extended partial result plus one per neighbour scanned; the budget is
+ * per thread; counts are then partial), or a negative code on invalid input.
+ */
+int oracle_match(const og* g, int k, const int32_t* ql, int nqe, const int32_t* qe,
+                 const int32_t* order, const int32_t* par,
+                 const int64_t* allow_off, const int32_t* allow_v, const uint8_t* allow_on,
+                 int64_t max_emb, int32_t* emb_out, uint64_t* count_out, uint64_t* depth_out,
+                 double* balg_out, int64_t node_budget, int nthreads) {
+    if (k < 1 || k > OMAXK) return -1;
+    int A[OMAXK][OMAXK];
+    memset(A, 0, sizeof(A));
+    for (int e = 0; e < nqe; e++) {
+        int a = qe[2 * e], b = qe[2 * e + 1];
+        if (a < 0 || b < 0 || a >= k || b >= k || a == b) return -2;
+        A[a][b] = A[b][a] = 1;
+    }
+    sctx c;
+    memset(&c, 0, sizeof(c));
+    c.g = g; c.k = k; c.ql = ql;
+    if (order) {
+        for (int i = 0; i < k; i++) c.order[i] = order[i];
+    } else {
+        int seen[OMAXK] = {0}, qh = 0, qt = 0;
+        c.order[qt++] = 0; seen[0] = 1;
+        while (qh < qt) {
+            int u = c.order[qh++];
+            for (int w = 0; w < k; w++)
+                if (A[u][w] && !seen[w]) { seen[w] = 1; c.order[qt++] = w; }
+        }
+        if (qt != k) return -3;   /* disconnected query */
+    }
+    int pos[OMAXK];
+    for (int i = 0; i < k; i++) pos[i] = -1;
+    for (int i = 0; i < k; i++) {
+        if (c.order[i] < 0 || c.order[i] >= k || pos[c.order[i]] >= 0) return -4;
+        pos[c.order[i]] = i;
+    }
+    for (int d = 1; d < k; d++) {
+        int u = c.order[d];
+        int p = par ? par[d] : -1;
+        if (p < 0) {
+            for (int j = 0; j < d; j++) if (A[u][c.order[j]]) { p = j; break; }
+        }
+        if (p < 0 || p >= d || !A[u][c.order[p]]) return -3;
+        c.par[d] = p;
+        c.nb[d] = 0;
+        for (int j = 0; j < d; j++)
+            if (j != p && A[u][c.order[j]]) c.bn[d][c.nb[d]++] = j;
+    }
+    c.aoff = allow_off; c.av = allow_v; c.aon = allow_on;
+    c.max_emb = max_emb; c.emb = emb_out;
+    int64_t slot = 0;
+    c.emb_slot = &slot;
+    c.budget = node_budget;
+
+    /* root candidates: every vertex carrying the root's label */
+    int ur = c.order[0];
+    int64_t nr = 0;
+    int32_t* roots = (int32_t*)malloc((size_t)(g->n > 0 ? g->n : 1) * sizeof(int32_t));
+    for (int64_t v = 0; v < g->n; v++)
+        if (g->lab[v] == ql[ur] && allowed(&c, ur, (int32_t)v)) roots[nr++] = (int32_t)v;
+
+    int want_balg = balg_out != NULL;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+    sacc* acc = (sacc*)calloc((size_t)nt, sizeof(sacc));
+#pragma omp parallel num_threads(nt)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        int32_t M[OMAXK];
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t r = 0; r < nr; r++) {
+            if (acc[t].over) continue;
+            M[0] = roots[r];
+            extend(&c, &acc[t], M, 1, want_balg);
+        }
+    }
+    uint64_t cnt = 0;
+    double balg = want_balg ? 4.0 * (double)nr : 0.0;
+    int over = 0;
+    if (depth_out) memset(depth_out, 0, (size_t)k * sizeof(uint64_t));
+    for (int t = 0; t < nt; t++) {
+        cnt += acc[t].count;
+        balg += acc[t].balg;
+        over |= acc[t].over;
+        if (depth_out) for (int d = 0; d < k; d++) depth_out[d] += acc[t].depth[d];
+    }
+    *count_out = cnt;
+    if (balg_out) *balg_out = balg;
+    free(acc); free(roots);
+    return over ? 1 : 0;
+}

@@ -1,0 +1,391 @@
+"""Pins for the oracle: checks against what the paper and the mathematics fix
+(brute force, closed forms, automorphism and order invariants, the soundness
+theorem of Sec. IV-A, and the worked examples of Sec. IV-B, IV-C and V-A).
+CPU only."""
+import itertools
+import json
+import math
+import os
+
+import networkx as nx
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers
+
+def random_graph(rng, n, p, L):
+    edges = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
+    labels = rng.integers(0, L, size=n).astype(np.int32)
+    return np.array(edges, dtype=np.int32).reshape(-1, 2), labels
+
+
+def random_connected_query(rng, k, L, extra_p):
+    edges = set()
+    for v in range(1, k):
+        edges.add((int(rng.integers(0, v)), v))
+    for a in range(k):
+        for b in range(a + 1, k):
+            if rng.random() < extra_p:
+                edges.add((a, b))
+    labels = rng.integers(0, L, size=k).astype(np.int32)
+    return labels, np.array(sorted(edges), dtype=np.int32).reshape(-1, 2)
+
+
+def relabel_query(labels, edges, perm):
+    """query vertex u becomes perm[u]"""
+    nl = np.empty_like(labels)
+    nl[perm] = labels
+    ne = np.array([[perm[a], perm[b]] for a, b in edges], dtype=np.int32).reshape(-1, 2)
+    return nl, ne
+
+
+def aut_count(labels, edges):
+    k = len(labels)
+    E = {(min(a, b), max(a, b)) for a, b in edges}
+    n = 0
+    for p in itertools.permutations(range(k)):
+        if all(labels[p[u]] == labels[u] for u in range(k)) and \
+           all((min(p[a], p[b]), max(p[a], p[b])) in E for a, b in E):
+            n += 1
+    return n
+
+
+# ------------------------------------------------------------ brute force
+
+@pytest.mark.parametrize("seed", range(60))
+def test_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 9))
+    k = int(rng.integers(1, min(5, n) + 1))
+    L = int(rng.integers(1, 4))
+    edges, labels = random_graph(rng, n, float(rng.uniform(0.25, 0.8)), L)
+    ql, qe = random_connected_query(rng, k, L, float(rng.uniform(0.0, 0.6)))
+    want = oracle.brute_force(n, edges, labels, ql, qe)
+    g = oracle.Graph(n, edges, labels)
+    r = oracle.match(g, ql, qe, max_emb=100000, threads=1)
+    assert r["complete"]
+    assert r["count"] == len(want)
+    got = [tuple(int(x) for x in row) for row in r["emb"]]
+    assert got == want
+
+
+def test_duplicates_and_loops_are_dropped():
+    # the paper's graphs are simple (Sec. II-A): repeats and loops carry no edge
+    edges = np.array([[0, 1], [1, 0], [0, 1], [1, 1], [1, 2], [2, 2]], np.int32)
+    g = oracle.Graph(3, edges, np.zeros(3, np.int32))
+    off, adj = g.csr()
+    assert off.tolist() == [0, 1, 3, 4]
+    assert adj.tolist() == [1, 0, 2, 1]
+    assert oracle.count(g, [0, 0], [[0, 1]]) == 4   # 2 edges, both directions
+
+
+# ----------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("n,k", [(5, 1), (5, 2), (5, 3), (6, 4), (7, 5), (8, 3)])
+def test_clique_in_complete_graph(n, k):
+    edges = np.array(list(itertools.combinations(range(n), 2)), np.int32)
+    g = oracle.Graph(n, edges, np.zeros(n, np.int32))
+    qe = np.array(list(itertools.combinations(range(k), 2)), np.int32).reshape(-1, 2)
+    assert oracle.count(g, np.zeros(k, np.int32), qe) == math.perm(n, k)
+
+
+@pytest.mark.parametrize("n,L", [(3, 1), (5, 2), (6, 5), (9, 4), (12, 11), (40, 7)])
+def test_path_in_cycle(n, L):
+    edges = np.array([[i, (i + 1) % n] for i in range(n)], np.int32)
+    g = oracle.Graph(n, edges, np.zeros(n, np.int32))
+    qe = np.array([[i, i + 1] for i in range(L)], np.int32)
+    assert oracle.count(g, np.zeros(L + 1, np.int32), qe) == 2 * n
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_star_counts(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = 60
+    edges, labels = random_graph(rng, n, 0.15, 3)
+    g = oracle.Graph(n, edges, labels)
+    adj = [set() for _ in range(n)]
+    for a, b in edges:
+        adj[a].add(b); adj[b].add(a)
+    for s in (1, 2, 3):
+        for a_lab in range(3):
+            for b_lab in range(3):
+                want = sum(math.perm(sum(1 for w in adj[v] if labels[w] == b_lab), s)
+                           for v in range(n) if labels[v] == a_lab)
+                ql = np.array([a_lab] + [b_lab] * s, np.int32)
+                qe = np.array([[0, i] for i in range(1, s + 1)], np.int32)
+                assert oracle.count(g, ql, qe) == want
+
+
+def test_single_edge_counts():
+    rng = np.random.default_rng(7)
+    n = 80
+    edges, labels = random_graph(rng, n, 0.1, 3)
+    g = oracle.Graph(n, edges, labels)
+    for a in range(3):
+        for b in range(3):
+            m_ab = sum(1 for x, y in edges if {labels[x], labels[y]} == {a, b})
+            want = m_ab * (2 if a == b else 1)
+            assert oracle.count(g, [a, b], [[0, 1]]) == want
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_triangles_against_networkx(seed):
+    rng = np.random.default_rng(200 + seed)
+    n = 70
+    edges, labels = random_graph(rng, n, 0.12, 1)
+    G = nx.Graph(); G.add_nodes_from(range(n)); G.add_edges_from(edges.tolist())
+    tri = sum(nx.triangles(G).values()) // 3
+    g = oracle.Graph(n, edges, labels)
+    assert oracle.count(g, [0, 0, 0], [[0, 1], [1, 2], [0, 2]]) == 6 * tri
+
+
+# -------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("seed", range(10))
+def test_embeddings_equal_copies_times_automorphisms(seed):
+    rng = np.random.default_rng(300 + seed)
+    n = 9
+    edges, labels = random_graph(rng, n, 0.5, 2)
+    k = int(rng.integers(2, 5))
+    ql, qe = random_connected_query(rng, k, 2, 0.5)
+    g = oracle.Graph(n, edges, labels)
+    r = oracle.match(g, ql, qe, max_emb=1 << 16)
+    copies = set()
+    for M in r["emb"].tolist():
+        copies.add(frozenset((min(M[a], M[b]), max(M[a], M[b])) for a, b in qe) | frozenset((v,) for v in M))
+    assert r["count"] == len(copies) * aut_count(ql, qe)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_count_independent_of_order_and_vertex_ids(seed):
+    rng = np.random.default_rng(400 + seed)
+    n = 40
+    edges, labels = random_graph(rng, n, 0.15, 2)
+    k = 5
+    ql, qe = random_connected_query(rng, k, 2, 0.3)
+    g = oracle.Graph(n, edges, labels)
+    base = oracle.match(g, ql, qe, max_emb=1 << 18)
+    # another connected order: BFS from a different query vertex
+    qperm = rng.permutation(k)
+    ql2, qe2 = relabel_query(ql, qe, qperm)
+    r2 = oracle.match(g, ql2, qe2, max_emb=1 << 18)
+    assert r2["count"] == base["count"]
+    back = r2["emb"][:, qperm] if r2["count"] else r2["emb"]
+    assert sorted(map(tuple, back.tolist())) == sorted(map(tuple, base["emb"].tolist()))
+    # relabelling G's vertices permutes the embedding set
+    gp = rng.permutation(n)
+    g3 = oracle.Graph(n, gp[edges], labels[np.argsort(gp)])
+    r3 = oracle.match(g3, ql, qe, max_emb=1 << 18)
+    assert r3["count"] == base["count"]
+    inv = np.argsort(gp)
+    mapped = sorted(map(tuple, inv[r3["emb"]].tolist())) if r3["count"] else []
+    assert mapped == sorted(map(tuple, base["emb"].tolist()))
+
+
+# ------------------------------------------------------ CST (Algorithm 1)
+
+def _cst_case(seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(30, 120))
+    edges, labels = random_graph(rng, n, float(rng.uniform(0.05, 0.25)), int(rng.integers(1, 4)))
+    k = int(rng.integers(2, 7))
+    ql, qe = random_connected_query(rng, k, int(labels.max()) + 1, float(rng.uniform(0, 0.4)))
+    return n, edges, labels, ql, qe
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_cst_is_sound(seed):
+    """Soundness (Sec. IV-A): every embedding maps u into C(u), and every
+    query edge onto a CST edge; so the CST is a complete search space."""
+    n, edges, labels, ql, qe = _cst_case(seed)
+    g = oracle.Graph(n, edges, labels)
+    c = oracle.Cst(g, ql, qe)
+    r = oracle.match(g, ql, qe, max_emb=1 << 18)
+    k = len(ql)
+    cand = [set(c.cand(u).tolist()) for u in range(k)]
+    tree = {}
+    for u in range(k):
+        if c.parent[u] >= 0:
+            off, vals = c.tree(u)
+            cp = c.cand(int(c.parent[u]))
+            tree[u] = {int(cp[i]): set(vals[off[i]:off[i + 1]].tolist()) for i in range(len(cp))}
+    nts = {(a, b): (off, vals, c.cand(a)) for a, b, off, vals in c.nontree()}
+    for M in r["emb"].tolist():
+        for u in range(k):
+            assert M[u] in cand[u]
+            if c.parent[u] >= 0:
+                assert M[u] in tree[u][M[int(c.parent[u])]]
+        for (a, b), (off, vals, ca) in nts.items():
+            i = int(np.searchsorted(ca, M[a]))
+            assert M[b] in set(vals[off[i]:off[i + 1]].tolist())
+    # the tree's own counts: W bounds the embedding count (Sec. IV-C)
+    wf, wi, _, _ = c.workload()
+    assert wi >= r["count"] and wf >= r["count"]
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_cst_lists_follow_definition(seed):
+    """Each list is N_G(v) restricted to the other end's candidate set (the
+    CST definition of Sec. IV-A), candidates carry the query label, and every
+    candidate has its children (bottom-up validity)."""
+    n, edges, labels, ql, qe = _cst_case(seed)
+    g = oracle.Graph(n, edges, labels)
+    c = oracle.Cst(g, ql, qe)
+    off_g, adj_g = g.csr()
+    N = lambda v: set(adj_g[off_g[v]:off_g[v + 1]].tolist())
+    k = len(ql)
+    dq = np.bincount(qe.ravel(), minlength=k)
+    for u in range(k):
+        for v in c.cand(u).tolist():
+            assert labels[v] == ql[u] and len(N(v)) >= dq[u]
+    children = {u: [w for w in range(k) if c.parent[w] == u] for u in range(k)}
+    for u in range(k):
+        if c.parent[u] < 0:
+            continue
+        off, vals = c.tree(u)
+        cp, cu = c.cand(int(c.parent[u])), set(c.cand(u).tolist())
+        for i, vp in enumerate(cp.tolist()):
+            assert vals[off[i]:off[i + 1]].tolist() == sorted(N(vp) & cu)
+    for u in range(k):
+        for w in children[u]:
+            off, vals = c.tree(w)
+            assert np.all(np.diff(off) > 0)       # every survivor keeps each child
+    for a, b, off, vals in c.nontree():
+        cb = set(c.cand(b).tolist())
+        for i, v in enumerate(c.cand(a).tolist()):
+            assert vals[off[i]:off[i + 1]].tolist() == sorted(N(v) & cb)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_workload_equals_count_for_trees_with_distinct_labels(seed):
+    """W ignores injectivity and non-tree edges (Sec. IV-C); for a tree query
+    whose labels are pairwise distinct neither matters, so W is exact."""
+    rng = np.random.default_rng(600 + seed)
+    n = 150
+    L = 6
+    edges, labels = random_graph(rng, n, 0.06, L)
+    k = int(rng.integers(2, 6))
+    ql = rng.permutation(L)[:k].astype(np.int32)
+    qe = np.array([[int(rng.integers(0, v)), v] for v in range(1, k)], np.int32)
+    g = oracle.Graph(n, edges, labels)
+    c = oracle.Cst(g, ql, qe)
+    wf, wi, _, _ = c.workload()
+    cnt = oracle.count(g, ql, qe)
+    assert wi == cnt and wf == float(cnt)
+
+
+# ------------------------------------------------------- paper's examples
+
+def _fixture():
+    with open(os.path.join(GOLDEN, "paper_fig4_example.json")) as f:
+        return json.load(f)
+
+
+def test_paper_workload_example():
+    fx = _fixture()
+    g = oracle.Graph(fx["n"], fx["edges"], fx["labels"])
+    c = oracle.Cst(g, fx["query_labels"], fx["query_edges"])
+    ex = fx["expected"]
+    assert c.root == ex["root"]
+    assert c.parent.tolist() == ex["tree_parent"]
+    wf, wi, cf, ci = c.workload(dump_u=0)
+    assert wi == ex["W"] and wf == ex["W"]
+    cand0 = c.cand(0).tolist()
+    for v, want in ex["c_u0"].items():
+        assert int(ci[cand0.index(int(v))]) == want
+
+
+def test_paper_partition_example():
+    fx = _fixture()
+    ex = fx["expected"]
+    g = oracle.Graph(fx["n"], fx["edges"], fx["labels"])
+    c = oracle.Cst(g, fx["query_labels"], fx["query_edges"])
+    chunks = c.partition(ex["partition_delta_w"])
+    assert [(a, b, w) for (j, pre, a, b, w, i) in chunks] == [tuple(x) for x in ex["partition_chunks"]]
+    # parts are disjoint and complete: their counts add up to the whole
+    total = oracle.count(g, fx["query_labels"], fx["query_edges"])
+    parts = [oracle.count(g, fx["query_labels"], fx["query_edges"], allow=c.chunk_allow(j, pre, a, b))
+             for (j, pre, a, b, w, i) in chunks]
+    assert sum(parts) == total
+
+
+def test_paper_generator_validator_round():
+    fx = _fixture()
+    ex = fx["expected"]
+    g = oracle.Graph(fx["n"], fx["edges"], fx["labels"])
+    ql = np.array(fx["query_labels"], np.int32)
+    qe = np.array(fx["query_edges"], np.int32)
+    # partial results over (u0, u1), root fixed to v1: the round's input P
+    r2 = oracle.match(g, ql[:2], [[0, 1]], allow={0: [1]}, max_emb=100)
+    assert r2["emb"].tolist() == ex["round_P"]
+    # one more position, u2, with its tree edge (u0,u2) and non-tree edge (u1,u2)
+    sub_e = [[a, b] for a, b in qe.tolist() if a < 3 and b < 3]
+    r3 = oracle.match(g, ql[:3], sub_e, order=[0, 1, 2], allow={0: [1]}, max_emb=100)
+    assert r3["emb"].tolist() == ex["round_survivors"]
+    gen = ex["round_generated"]
+    bn = [1 if row in ex["round_survivors"] else 0 for row in gen]
+    assert bn == ex["round_B_n"]
+    # the order of the example reaches the same embeddings as any other
+    full = oracle.match(g, ql, qe, max_emb=100)
+    alt = oracle.match(g, ql, qe, order=ex["round_order"], max_emb=100)
+    assert full["emb"].tolist() == alt["emb"].tolist() and full["count"] == 3
+
+
+# ------------------------------------------------------------- partition
+
+@pytest.mark.parametrize("seed", range(10))
+def test_partition_disjoint_and_complete(seed):
+    n, edges, labels, ql, qe = _cst_case(700 + seed)
+    g = oracle.Graph(n, edges, labels)
+    c = oracle.Cst(g, ql, qe)
+    wf, wi, _, _ = c.workload()
+    total = oracle.match(g, ql, qe, max_emb=1 << 18)
+    delta = max(1, wi // 7)
+    chunks = c.partition(delta)
+    seen = set()
+    s = 0
+    for (j, pre, a, b, w, i) in chunks:
+        assert 0 < w <= delta or (b - a == 1 and j == len(ql) - 1)
+        assert c.chunk_w(j, pre, c.chunk_list(j, pre)[a:b]) == w
+        r = oracle.match(g, ql, qe, allow=c.chunk_allow(j, pre, a, b), max_emb=1 << 18)
+        assert r["count"] <= w
+        rows = set(map(tuple, r["emb"].tolist()))
+        assert len(rows) == min(r["count"], 1 << 18) and not (rows & seen)
+        seen |= rows
+        s += r["count"]
+    assert s == total["count"]
+    if total["count"] <= 1 << 18:
+        assert seen == set(map(tuple, total["emb"].tolist()))
+
+
+def test_partition_sampling_keeps_a_subset():
+    n, edges, labels, ql, qe = _cst_case(801)
+    g = oracle.Graph(n, edges, labels)
+    c = oracle.Cst(g, ql, qe)
+    wf, wi, _, _ = c.workload()
+    full = c.partition(max(1, wi // 20))
+    samp = c.partition(max(1, wi // 20), c_root=2.0, c_deep=1.0, seed=5)
+    ids = {ch[-1] for ch in full}
+    assert len(samp) <= len(full) and all(ch[-1] in ids for ch in samp)
+
+
+# ------------------------------------------------------ algorithmic bytes
+
+def test_balg_counts_lists_of_extended_partials():
+    """The list-byte count of the enumerator, on a path a-b-c where every
+    list is known by hand."""
+    # 0(a)-1(b)-2(c), 0-3(b), 3-4(c), 3-5(c)
+    edges = [[0, 1], [1, 2], [0, 3], [3, 4], [3, 5]]
+    labels = [0, 1, 2, 1, 2, 2]
+    g = oracle.Graph(6, edges, labels)
+    r = oracle.match(g, [0, 1, 2], [[0, 1], [1, 2]], want_balg=True, want_depth=True)
+    assert r["count"] == 3
+    # root list: 1 candidate (4 B); extend {0}: list of 0 towards b = {1,3} (8+8);
+    # extend {0,1}: list of 1 towards c = {2} (8+4); extend {0,3}: {4,5} (8+8)
+    assert r["balg"] == 4 + (8 + 8) + (8 + 4) + (8 + 8)
+    assert r["depth"].tolist() == [1, 2, 3]
