@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark: per-query subgraph matching on the power-law workload.
+
+Workload (synthetic stand-in for the paper's LDBC-SNB graphs and query set):
+Chung-Lu graph, exponent 2.1, 1,000,000 vertices, 16,000,000 undirected
+edges, 16 labels Zipf(1.0); 200 connected random-walk queries, 50 each of
+(8 vertices, dense), (8, sparse), (16, dense), (16, sparse).  Every query's
+embedding count is astronomical on this graph (workload estimates 1e20 to
+1e53), so each query is matched on a seeded sample of its CST partition:
+chunks with workload estimate <= delta_w, about `sample_root` sampled runs
+of root candidates and one sampled run per deeper split.  Counts on the
+sampled chunks are exact.
+
+One step = for every query: fast_build_cst + fast_partition + fast_match,
+with the data graph resident on the device.  value = embeddings enumerated
+per second; queries/s and per-query latency percentiles ride along.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "embeddings/sec"
+UNIT = "embeddings/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--queries", type=int, default=50, help="queries per (size, kind) class")
+    p.add_argument("--delta-w", type=int, default=1 << 20)
+    p.add_argument("--sample-root", type=float, default=16.0)
+    p.add_argument("--sample-deep", type=float, default=1.0)
+    p.add_argument("--seed", type=int, default=2000)
+    p.add_argument("--emb-k", type=int, default=1024, help="embeddings copied to the host per query (e2e)")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    return p.parse_args()
+
+
+def workload(args, rank: int):
+    import synth
+    n, e, lab = synth.powerlaw_graph(seed=args.seed)
+    qs = []
+    for k in (8, 16):
+        for kind in ("dense", "sparse"):
+            stream0 = 100_000 * rank + 1000 * k + (0 if kind == "dense" else 500)
+            qs += synth.walk_queries(n, e, lab, k, args.queries, kind, seed=args.seed, stream0=stream0)
+    desc = (f"Chung-Lu gamma=2.1, n=1,000,000, m=16,000,000, 16 Zipf(1.0) labels; "
+            f"{len(qs)} random-walk queries (8/16 vertices x dense/sparse); CST partition sampled: "
+            f"delta_w={args.delta_w}, sample_root={args.sample_root}, sample_deep={args.sample_deep}, "
+            f"seed={args.seed}")
+    return n, e, lab, qs, desc
+
+
+class Clocks:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0])); smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(args, n, e, lab, qs, budget_s):
+    """The oracle as it stands: its own CST and partition restatements, then
+    its enumerator on the sampled chunks, until budget_s of enumeration."""
+    import oracle
+    og = oracle.Graph(n, e, lab)
+    emb = 0
+    t_enum = 0.0
+    chunks_done = 0
+    queries = 0
+    for q in qs:
+        c = oracle.Cst(og, q.labels, q.edges)
+        chunks = c.partition(args.delta_w, args.sample_root, args.sample_deep, args.seed)
+        queries += 1
+        for (j, pre, a, b, w, i) in chunks:
+            t0 = time.perf_counter()
+            r = oracle.match(og, q.labels, q.edges, allow=c.chunk_allow(j, pre, a, b))
+            t_enum += time.perf_counter() - t0
+            emb += r["count"]
+            chunks_done += 1
+            if t_enum > budget_s:
+                break
+        c.close()
+        if t_enum > budget_s:
+            break
+    cores = os.cpu_count() or 1
+    return {"value": emb / t_enum if t_enum > 0 else 0.0, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{chunks_done} sampled chunks of the first {queries} queries "
+                      f"({emb} embeddings in {t_enum:.1f} s of enumeration, OpenMP over root candidates)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n, e, lab, qs, desc = workload(args, 0)
+    import oracle
+    og = oracle.Graph(n, e, lab)
+    c = oracle.Cst(og, qs[0].labels, qs[0].edges)
+    chunks = c.partition(args.delta_w, args.sample_root, args.sample_deep, args.seed)
+    per_step = max(1.0, args.cpu_seconds / 2)
+
+    def step(start):
+        emb, t = 0, 0.0
+        i = start
+        while t < per_step:
+            (j, pre, a, b, w, cid) = chunks[i % len(chunks)]
+            t0 = time.perf_counter()
+            emb += oracle.match(og, qs[0].labels, qs[0].edges, allow=c.chunk_allow(j, pre, a, b))["count"]
+            t += time.perf_counter() - t0
+            i += 1
+        return emb, t, i
+
+    pos = 0
+    for _ in range(args.warmup):
+        _, _, pos = step(pos)
+    tot_e, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        em, t, pos = step(pos)
+        tot_e += em
+        tot_t += t
+    v = tot_e / tot_t if tot_t else 0.0
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": desc, "sample": "chunks of query 0, in order"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                             "sample": f"{per_step:.0f} s of oracle enumeration per step over the sampled "
+                                       f"chunks of query 0"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2102_10768_gb300 as F
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    F.build()
+    F.lib()
+    n, e, lab, qs, desc = workload(args, rank)
+    stream = torch.cuda.current_stream()
+    g = F.Graph(n, e, lab)
+    cfg = F.default_config(delta_w=args.delta_w, sample_root=args.sample_root, sample_deep=args.sample_deep,
+                           sample_seed=args.seed, time_budget_s=30.0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+
+    def one_query(q, k=0, emb=None):
+        cst = F.Cst(g, q.labels, q.edges, cfg)
+        ch = F.Chunks(cst, cfg)
+        r = F.match(cst, ch, k=k, emb_out=emb, cfg=cfg, check=False)
+        if r["status"] not in (F.FAST_OK,):
+            raise F.FastError(r["status"], F.lib().fast_last_error().decode())
+        ms = F.last_match_ms()
+        nch = ch.n
+        ch.close(); cst.close()
+        return r["count"], ms, nch
+
+    # algorithmic bytes of the matcher per query (counting pass, untimed)
+    balg = 0
+    nchunks = 0
+    for q in qs:
+        cst = F.Cst(g, q.labels, q.edges, cfg)
+        ch = F.Chunks(cst, cfg)
+        b, _ = F.match_stats(cst, ch, cfg)
+        balg += b
+        nchunks += ch.n
+        ch.close(); cst.close()
+
+    def step():
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        lat = []
+        emb, kms = 0, 0.0
+        ev0.record(stream)
+        for q in qs:
+            t0 = time.perf_counter()
+            c, ms, _ = one_query(q)
+            lat.append(1000 * (time.perf_counter() - t0))
+            emb += c
+            kms += ms
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return emb, ev0.elapsed_time(ev1), kms, lat
+
+    for _ in range(args.warmup):
+        step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = F.kernel_launches()
+    tot_emb, tot_ms, tot_kms, lats = 0, 0.0, 0.0, []
+    for _ in range(args.steps):
+        em, ms, kms, lat = step()
+        tot_emb += em
+        tot_ms += ms
+        tot_kms += kms
+        lats += lat
+    torch.cuda.synchronize()
+    launches = F.kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    # end to end through the C ABI with host buffers: query arrays in, counts
+    # and the first emb_k embeddings of each query out to pinned host memory
+    pinned = {k: torch.empty((args.emb_k, k), dtype=torch.int32, pin_memory=True) for k in (8, 16)}
+    h2d = sum(q.labels.nbytes + q.edges.nbytes for q in qs)
+    e2e_emb, d2h, t_e2e = 0, 0, 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        for q in qs:
+            buf = pinned[q.k]
+            cst = F.Cst(g, q.labels, q.edges, cfg)
+            ch = F.Chunks(cst, cfg)
+            r = F.match(cst, ch, k=args.emb_k, emb_out=buf.numpy(), cfg=cfg)
+            e2e_emb += r["count"]
+            d2h += 8 + 4 * q.k * r["written"]
+            ch.close(); cst.close()
+        t_e2e += time.perf_counter() - ts
+
+    steps = max(args.steps, 1)
+    t_s = tot_ms / 1000.0
+    stats = torch.tensor([t_s, float(tot_emb), t_e2e, float(e2e_emb)], dtype=torch.float64, device="cuda")
+    if dist:
+        mx = stats.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = stats.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        t_s, tot_all, t_e2e_max, e2e_all = float(mx[0]), float(sm[1]), float(mx[2]), float(sm[3])
+    else:
+        tot_all, t_e2e_max, e2e_all = float(tot_emb), t_e2e, float(e2e_emb)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    achieved = (balg * steps) / (tot_kms / 1000.0) / 1e9 if tot_kms > 0 else 0.0
+    lat_sorted = sorted(lats)
+    cpu = cpu_baseline(args, n, e, lab, qs, args.cpu_seconds) if world == 1 else None
+    line = {
+        "metric": METRIC, "value": tot_all / t_s, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_s / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": desc, "queries_per_step": len(qs), "chunks_per_step": nchunks,
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}, queries per rank"},
+        "queries_per_sec": len(qs) * steps * world / t_s,
+        "latency_ms": {"p50": lat_sorted[len(lat_sorted) // 2], "p99": lat_sorted[int(0.99 * (len(lat_sorted) - 1))]},
+        "embeddings_per_step": tot_emb / steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_match", "algorithmic_bytes_per_step": balg,
+                     "kernel_ms_per_step": tot_kms / steps},
+        "e2e": {"value": e2e_all / t_e2e_max if t_e2e_max else 0.0, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // steps},
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,269 @@
+/*
+ * fast.h -- C ABI of a GB300 (sm_103a) implementation of candidate-search-tree
+ * subgraph matching, after "FAST: FPGA-based Subgraph Matching on Massive
+ * Graphs" (Jin, Yang, Lin, Yang, Qin, Peng; arXiv 2102.10768).
+ *
+ * Problem (Sec. II-A, Definition 1 and the problem statement): given a
+ * labelled query graph q and a labelled data graph G, both undirected and
+ * simple, enumerate every embedding -- every injective map M: V(q) -> V(G)
+ * with l_q(u) = l_G(M(u)) for every u and (M(u), M(u')) in E(G) for every
+ * query edge (u, u').  Embeddings are maps, not subgraphs: a copy of q in G is
+ * reached once per automorphism of q.
+ *
+ * Pipeline (each step is CUDA on the device; the host only sequences them):
+ *   fast_load_graph  -- CSR of G plus a label index (the data model of
+ *                       Sec. II-A).
+ *   fast_build_cst   -- the candidate search tree CST of Sec. IV-A
+ *                       (Algorithm 1): candidate filter, top-down
+ *                       construction over a BFS tree t_q of q, bottom-up
+ *                       refinement, non-tree candidate edges, and the
+ *                       workload estimate of Sec. IV-C.
+ *   fast_partition   -- the CST partition of Sec. IV-B (Algorithm 2) into
+ *                       chunks whose workload estimate is bounded.
+ *   fast_match       -- enumeration over the CST (the semantics of
+ *                       Algorithms 4-8, Sec. V-A): a uint64 count and,
+ *                       optionally, the first k embeddings found.
+ *
+ * Conventions for every entry point:
+ *   - Return value: FAST_OK (0) or one of the FAST_ERR_* codes below; the
+ *     thread-local fast_last_error() then describes the failure.  Outputs
+ *     are undefined after an error unless stated otherwise.
+ *   - `stream` is a cudaStream_t passed as void* (NULL: the legacy default
+ *     stream).  Work is enqueued on it; calls that must report sizes or
+ *     counts to the host synchronise it before returning.
+ *   - Handles (fast_graph, fast_cst, fast_chunks) are opaque, owned by the
+ *     library and released with their fast_free_* function.  Input arrays
+ *     are copied; the caller keeps ownership of everything it passes in.
+ *   - All device memory the library needs is allocated stream-ordered
+ *     (cudaMallocAsync) on the current CUDA device.
+ */
+#ifndef FAST_GB300_H
+#define FAST_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define FAST_OK 0
+#define FAST_ERR_INVALID 1   /* bad argument: ids out of range, q.n > 32, disconnected q, ... */
+#define FAST_ERR_OOM 2       /* a device allocation failed */
+#define FAST_ERR_TIMEOUT 3   /* fast_match ran past config.time_budget_s; the count is partial */
+#define FAST_ERR_OVERFLOW 4  /* the embedding count reached 2^64 - 1 (saturated) */
+#define FAST_ERR_CUDA 5      /* a CUDA call or kernel launch failed */
+#define FAST_ERR_LIMIT 6     /* fast_partition would exceed config.max_chunks */
+
+#define FAST_MAX_QUERY 32    /* query vertices per query (one warp lane each) */
+
+/* flags for fast_load_graph */
+#define FAST_PTR_DEVICE 1    /* edges and labels are device pointers */
+
+typedef struct fast_graph fast_graph;
+typedef struct fast_cst fast_cst;
+typedef struct fast_chunks fast_chunks;
+
+/* A query graph q (Sec. II-A).  Host arrays; vertices are 0..n-1. */
+typedef struct {
+    int32_t n;               /* |V(q)|, 1..FAST_MAX_QUERY */
+    int32_t m;               /* number of entries in edges */
+    const int32_t* labels;   /* [n] vertex labels, >= 0 */
+    const int32_t* edges;    /* [m][2] undirected edges; repeats are ignored, loops rejected */
+} fast_query_desc;
+
+/* Tunables.  fast_config_default() fills documented defaults. */
+typedef struct {
+    /* Partition (Sec. IV-B, Algorithm 2): a chunk holds a workload estimate
+     * W' <= delta_w (Sec. IV-C).  The split factor of a part is
+     * k = min(ceil(W'/delta_w), |C'(u)|). */
+    uint64_t delta_w;
+    /* Optional seeded sampling of the partition: a part produced by a split
+     * into k parts is kept iff u01(id) < min(1, c/k), c = sample_root for a
+     * split of the root's candidates and sample_deep deeper (c <= 0 keeps
+     * every part, i.e. the chunks cover the whole search space). */
+    double sample_root;
+    double sample_deep;
+    uint64_t sample_seed;
+    int64_t max_chunks;      /* fast_partition fails with FAST_ERR_LIMIT beyond this */
+    /* Matcher launch shape: warps per CTA and CTAs per SM (persistent). */
+    int32_t warps_per_block;
+    int32_t blocks_per_sm;
+    /* Wall-clock budget for one fast_match call, seconds (<= 0: none). */
+    double time_budget_s;
+} fast_config;
+
+/* Default tunables: delta_w = 2^20, no sampling, max_chunks = 2^22,
+ * 8 warps per CTA, 4 CTAs per SM, no time budget. */
+void fast_config_default(fast_config* cfg);
+
+/* Thread-local message for the last failing call ("" if none). */
+const char* fast_last_error(void);
+
+/* ----------------------------------------------------------- data graph */
+
+/*
+ * Build the device-resident data graph G (Sec. II-A: undirected, labelled,
+ * simple).  edges: [m][2] vertex ids in 0..n-1; both directions are stored,
+ * self loops and repeated edges are dropped, every neighbour list is sorted
+ * ascending.  labels: [n], >= 0 and below 2^23.  Host pointers unless flags
+ * has FAST_PTR_DEVICE.  n <= 2^31 - 1 and 2m < 2^32.  Layout on the device:
+ * int64 row offsets [n+1], int32 neighbour ids, int32 labels, and a label
+ * index (vertices grouped by label, ascending id within a label).
+ * Errors: FAST_ERR_INVALID for ids or labels out of range.
+ */
+int fast_load_graph(int64_t n, int64_t m, const int32_t* edges, const int32_t* labels, int flags,
+                    void* stream, fast_graph** out);
+
+/* n, number of stored (directed) adjacency entries = 2|E(G)|, label count
+ * (max label + 1) and maximum degree D_G. */
+int fast_graph_info(const fast_graph* g, int64_t* n, int64_t* nadj, int32_t* num_labels, int64_t* max_degree);
+
+/* Copy the CSR to host arrays row_ptr[n+1] and col[nadj] (a test aid). */
+int fast_graph_copy_csr(const fast_graph* g, int64_t* row_ptr, int32_t* col, void* stream);
+
+void fast_free_graph(fast_graph* g);
+
+/* ----------------------------------------------------------------- CST */
+
+/*
+ * Build the candidate search tree of q over G (Sec. IV-A, Algorithm 1) and
+ * its workload estimate (Sec. IV-C), entirely on the device:
+ *   filter:    C0(u) = { v : l(v) = l_q(u), d_G(v) >= d_q(u) }.
+ *   root:      argmin_u |C0(u)| / d_q(u), ties to the smaller id; t_q is the
+ *              BFS tree from it (neighbours in increasing id).
+ *   top-down:  in BFS order, C(u) = vertices of C0(u) adjacent to some
+ *              candidate of the parent, and N^{u_p}_u(v_p) = N_G(v_p) n C(u).
+ *   bottom-up: in reverse BFS order, child lists are cut to the refined
+ *              child sets and v leaves C(u) when one of them is empty.
+ *   order:     the matching order O is the depth-first preorder of t_q with
+ *              children taken by increasing (|C|, id) -- whole root-to-leaf
+ *              paths in turn.
+ *   non-tree:  for each query edge outside t_q, from its earlier endpoint
+ *              u_j to its later endpoint u_i in O: N^{u_j}_{u_i}(v) =
+ *              N_G(v) n C(u_i), for v in C(u_j).
+ *   workload:  c_u(v) = 1 at leaves, c_u(v) = prod over children u' of
+ *              sum_{v' in N^u_{u'}(v)} c_{u'}(v'), W = sum over C(root); in
+ *              saturating uint64 and in float64.
+ * Lists are stored as sorted candidate-local indices.  The call synchronises
+ * `stream` a few times (candidate counts decide the root and the order).
+ * An empty candidate set is not an error: the CST then has no embeddings.
+ * Errors: FAST_ERR_INVALID for a bad or disconnected query.
+ */
+int fast_build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* cfg, void* stream,
+                   fast_cst** out);
+
+/*
+ * Shape of a CST: k = |V(q)|; root; order[k] (position -> query vertex);
+ * parent[k] (query vertex -> parent in t_q, -1 for the root); cand[k]
+ * (query vertex -> |C(u)|); W as saturating uint64 and float64.  Any output
+ * pointer may be NULL.
+ */
+int fast_cst_info(const fast_cst* c, int32_t* k, int32_t* root, int32_t* order, int32_t* parent,
+                  int64_t* cand, uint64_t* w_u64, double* w_f64);
+
+/* Copy C(u) (sorted data-vertex ids, |C(u)| entries) to host memory. */
+int fast_cst_candidates(const fast_cst* c, int32_t u, int32_t* out, void* stream);
+
+/* Number of list entries of the tree edge into u (0 for the root). */
+int fast_cst_tree_size(const fast_cst* c, int32_t u, int64_t* entries);
+
+/* Copy the tree lists into u: off[|C(parent(u))|+1] and idx[entries]
+ * (candidate-local indices into C(u)); row i belongs to C(parent(u))[i]. */
+int fast_cst_tree_lists(const fast_cst* c, int32_t u, int64_t* off, uint32_t* idx, void* stream);
+
+/* Number of non-tree CST edges, and the endpoints (query vertices, earlier
+ * then later in O) and list size of edge e. */
+int fast_cst_nontree_count(const fast_cst* c, int32_t* count);
+int fast_cst_nontree_edge(const fast_cst* c, int32_t e, int32_t* from_u, int32_t* to_u, int64_t* entries);
+
+/* Copy the lists of non-tree edge e: off[|C(from)|+1], idx[entries]. */
+int fast_cst_nontree_lists(const fast_cst* c, int32_t e, int64_t* off, uint32_t* idx, void* stream);
+
+/* Copy c_u(v) for u's candidates (saturating uint64, |C(u)| entries). */
+int fast_cst_workload(const fast_cst* c, int32_t u, uint64_t* out, void* stream);
+
+void fast_free_cst(fast_cst* c);
+
+/* ------------------------------------------------------------ partition */
+
+/*
+ * Partition the CST (Sec. IV-B, Algorithm 2).  Since every position before
+ * the split position is then a single candidate, a chunk is
+ * (j, the candidates of positions 0..j-1, a run [a, b) of the list L_j),
+ * where L_j is C(root) when j = 0 and otherwise the tree list, towards
+ * position j, of the candidate at position j's parent position.  Runs are
+ * even contiguous slices; a run with W' <= delta_w is a chunk (W' = 0 runs
+ * hold no embedding and are dropped); a run of one candidate moves on to the
+ * next position; longer runs split again.  With sampling off the chunks are
+ * disjoint and cover every embedding.  Level-synchronous on the device; the
+ * host reads one queue size per level.
+ * Errors: FAST_ERR_LIMIT when more than cfg->max_chunks chunks arise.
+ */
+int fast_partition(const fast_cst* c, const fast_config* cfg, void* stream, fast_chunks** out);
+
+/* Number of chunks, and their summed workload estimate (saturating). */
+int fast_chunks_info(const fast_chunks* ch, int64_t* count, uint64_t* w_sum);
+
+/*
+ * Copy the chunk descriptors to host arrays of `count` entries: j[i],
+ * prefix[i][k] (candidate-local indices of positions 0..j-1; -1 beyond),
+ * a[i], b[i], w[i] (W', saturating uint64), id[i] (sampling id).
+ */
+int fast_chunks_copy(const fast_chunks* ch, int32_t* j, int32_t* prefix, int64_t* a, int64_t* b,
+                     uint64_t* w, uint64_t* id, void* stream);
+
+void fast_free_chunks(fast_chunks* ch);
+
+/* ---------------------------------------------------------------- match */
+
+/*
+ * Enumerate the embeddings in `chunks` (NULL: the whole CST as one chunk)
+ * -- the semantics of Algorithms 4-8 (Sec. V-A): every partial result is
+ * extended by the tree list of its parent position's candidate (Generator),
+ * kept only if the new vertex is not already used (VisitedValidator) and is
+ * adjacent to the images of its earlier non-tree neighbours in the CST
+ * (EdgeValidator), and reported once complete (Synchronizer).
+ *   k:           embeddings to write (0: count only).
+ *   emb_out:     device buffer of k rows x |V(q)| uint32 data-vertex ids,
+ *                column u = M(u) (query vertex id order); any k embeddings
+ *                of the enumerated set, each once.  NULL iff k == 0.
+ *   count_out:   host; total number of embeddings in the chunks.
+ *   written_out: host; rows written = min(k, count).
+ *   chunk_counts: optional device buffer of one uint64 per chunk.
+ * The call synchronises `stream`.  FAST_ERR_TIMEOUT (time budget spent)
+ * and FAST_ERR_OVERFLOW leave a partial or saturated count in *count_out.
+ */
+int fast_match(const fast_cst* c, const fast_chunks* chunks, uint64_t k, uint32_t* emb_out,
+               uint64_t* count_out, uint64_t* written_out, void* stream);
+
+/* fast_match with an explicit launch configuration and per-chunk counts. */
+int fast_match_ex(const fast_cst* c, const fast_chunks* chunks, const fast_config* cfg, uint64_t k,
+                  uint32_t* emb_out, uint64_t* count_out, uint64_t* written_out, uint64_t* chunk_counts,
+                  void* stream);
+
+/*
+ * Counting pass over the same search: out[0] = algorithmic bytes (list
+ * offsets 8 B and list entries 4 B for every list a partial result is
+ * extended from or checked against, plus 4 B per candidate of a root run),
+ * out[1 + d] for d < k = partial results with d+1 positions mapped that pass
+ * every check.  out has k + 1 entries; host memory.
+ */
+int fast_match_stats(const fast_cst* c, const fast_chunks* chunks, const fast_config* cfg, uint64_t* out,
+                     void* stream);
+
+/* ---------------------------------------------------------- measurement */
+
+/* Duration in milliseconds of the last matcher kernel launched by this host
+ * thread, measured with CUDA events recorded on the launching stream around
+ * the kernel (0 if none ran). */
+double fast_last_match_ms(void);
+
+/* Kernels launched by the library since the process started (all threads). */
+uint64_t fast_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FAST_GB300_H */

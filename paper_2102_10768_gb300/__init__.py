@@ -1,0 +1,345 @@
+"""GB300 candidate-search-tree subgraph matching (after arXiv 2102.10768).
+
+A thin binding of the C ABI in ``include/fast.h`` (``_build/libfast.so``):
+argument marshalling only -- every step of the computation runs in the
+library's CUDA kernels.  PyTorch, when present, only supplies the current
+CUDA stream and device buffers.  The library must be built (``build()``);
+importing this module without it raises.
+
+Low-level functions keep the C names (``fast_load_graph`` ...); the classes
+``Graph``, ``Cst`` and ``Chunks`` own the corresponding handles.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+FAST_OK = 0
+FAST_ERR_INVALID = 1
+FAST_ERR_OOM = 2
+FAST_ERR_TIMEOUT = 3
+FAST_ERR_OVERFLOW = 4
+FAST_ERR_CUDA = 5
+FAST_ERR_LIMIT = 6
+FAST_PTR_DEVICE = 1
+FAST_MAX_QUERY = 32
+
+_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "TIMEOUT", 4: "OVERFLOW", 5: "CUDA", 6: "LIMIT"}
+
+
+class FastError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"FAST_ERR_{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("delta_w", ctypes.c_uint64), ("sample_root", ctypes.c_double),
+                ("sample_deep", ctypes.c_double), ("sample_seed", ctypes.c_uint64),
+                ("max_chunks", ctypes.c_int64), ("warps_per_block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("time_budget_s", ctypes.c_double)]
+
+
+class QueryDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("labels", ctypes.POINTER(ctypes.c_int32)), ("edges", ctypes.POINTER(ctypes.c_int32))]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64, _i32, _u64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+
+_SIGS = {
+    "fast_config_default": (None, [_vp]),
+    "fast_last_error": (ctypes.c_char_p, []),
+    "fast_load_graph": (ctypes.c_int, [_i64, _i64, _vp, _vp, ctypes.c_int, _vp, _vp]),
+    "fast_graph_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fast_graph_copy_csr": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "fast_free_graph": (None, [_vp]),
+    "fast_build_cst": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fast_cst_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fast_cst_candidates": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+    "fast_cst_tree_size": (ctypes.c_int, [_vp, _i32, _vp]),
+    "fast_cst_tree_lists": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "fast_cst_nontree_count": (ctypes.c_int, [_vp, _vp]),
+    "fast_cst_nontree_edge": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "fast_cst_nontree_lists": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "fast_cst_workload": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+    "fast_free_cst": (None, [_vp]),
+    "fast_partition": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "fast_chunks_info": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fast_chunks_copy": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fast_free_chunks": (None, [_vp]),
+    "fast_match": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp, _vp, _vp]),
+    "fast_match_ex": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp]),
+    "fast_match_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fast_last_match_ms": (ctypes.c_double, []),
+    "fast_kernel_launches": (ctypes.c_uint64, []),
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library (sm_103a) in-tree."""
+    return _build.build(force=force)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libfast.so; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing: build the CUDA library first "
+                               "(paper_2102_10768_gb300.build())")
+        L = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(rc: int):
+    if rc != FAST_OK:
+        raise FastError(rc, lib().fast_last_error().decode())
+
+
+def _p(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a
+
+
+def default_stream():
+    """cudaStream_t of torch's current stream (None = legacy default)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def default_config(**kw) -> Config:
+    c = Config()
+    lib().fast_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+# ------------------------------------------------------------------ handles
+
+class Graph:
+    """Device-resident data graph (fast_load_graph)."""
+
+    def __init__(self, n: int, edges, labels, stream=None, device: bool = False):
+        self.n = int(n)
+        self._keep = None
+        if device:
+            e, lab = edges, labels
+            m = int(edges.shape[0])
+        else:
+            e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+            lab = np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+            m = e.shape[0]
+        h = _vp()
+        st = stream if stream is not None else default_stream()
+        _check(lib().fast_load_graph(self.n, m, _p(e), _p(lab), FAST_PTR_DEVICE if device else 0, st,
+                                     ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        n, nadj, ml = _i64(), _i64(), _i64()
+        nl = _i32()
+        _check(lib().fast_graph_info(self._h, ctypes.byref(n), ctypes.byref(nadj), ctypes.byref(nl), ctypes.byref(ml)))
+        return {"n": n.value, "nadj": nadj.value, "num_labels": nl.value, "max_degree": ml.value}
+
+    def csr(self, stream=None):
+        inf = self.info()
+        off = np.empty(inf["n"] + 1, np.int64)
+        col = np.empty(max(inf["nadj"], 1), np.int32)
+        _check(lib().fast_graph_copy_csr(self._h, _p(off), _p(col), stream if stream is not None else default_stream()))
+        return off, col[:inf["nadj"]]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fast_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Cst:
+    """Candidate search tree of one query (fast_build_cst)."""
+
+    def __init__(self, graph: Graph, qlabels, qedges, cfg: Config | None = None, stream=None):
+        ql = np.ascontiguousarray(np.asarray(qlabels, dtype=np.int32))
+        qe = np.ascontiguousarray(np.asarray(qedges, dtype=np.int32).reshape(-1, 2))
+        self.graph = graph
+        self.k = int(ql.shape[0])
+        self._ql, self._qe = ql, qe
+        q = QueryDesc(self.k, qe.shape[0], ql.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                      qe.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        h = _vp()
+        self.stream = stream if stream is not None else default_stream()
+        _check(lib().fast_build_cst(graph.handle, ctypes.byref(q), ctypes.byref(cfg) if cfg else None,
+                                    self.stream, ctypes.byref(h)))
+        self._h = h
+        k = self.k
+        kk, root = _i32(), _i32()
+        order = np.empty(k, np.int32); parent = np.empty(k, np.int32); cand = np.empty(k, np.int64)
+        wu, wf = _u64(), ctypes.c_double()
+        _check(lib().fast_cst_info(h, ctypes.byref(kk), ctypes.byref(root), _p(order), _p(parent), _p(cand),
+                                   ctypes.byref(wu), ctypes.byref(wf)))
+        self.root, self.order, self.parent, self.ncand = root.value, order, parent, cand
+        self.W, self.Wf = wu.value, wf.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def candidates(self, u: int) -> np.ndarray:
+        out = np.empty(max(int(self.ncand[u]), 1), np.int32)
+        _check(lib().fast_cst_candidates(self._h, u, _p(out), self.stream))
+        return out[:int(self.ncand[u])]
+
+    def tree_lists(self, u: int):
+        """(offsets over C(parent(u)), candidate-local indices into C(u))."""
+        ent = _i64()
+        _check(lib().fast_cst_tree_size(self._h, u, ctypes.byref(ent)))
+        rows = int(self.ncand[int(self.parent[u])])
+        off = np.empty(rows + 1, np.int64)
+        idx = np.empty(max(ent.value, 1), np.uint32)
+        _check(lib().fast_cst_tree_lists(self._h, u, _p(off), _p(idx), self.stream))
+        return off, idx[:ent.value]
+
+    def nontree(self):
+        """[(from_u, to_u, offsets, candidate-local indices into C(to_u))]."""
+        cnt = _i32()
+        _check(lib().fast_cst_nontree_count(self._h, ctypes.byref(cnt)))
+        out = []
+        for e in range(cnt.value):
+            a, b, ent = _i32(), _i32(), _i64()
+            _check(lib().fast_cst_nontree_edge(self._h, e, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ent)))
+            rows = int(self.ncand[a.value])
+            off = np.empty(rows + 1, np.int64)
+            idx = np.empty(max(ent.value, 1), np.uint32)
+            _check(lib().fast_cst_nontree_lists(self._h, e, _p(off), _p(idx), self.stream))
+            out.append((a.value, b.value, off, idx[:ent.value]))
+        return out
+
+    def workload(self, u: int) -> np.ndarray:
+        out = np.empty(max(int(self.ncand[u]), 1), np.uint64)
+        _check(lib().fast_cst_workload(self._h, u, _p(out), self.stream))
+        return out[:int(self.ncand[u])]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fast_free_cst(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Chunks:
+    """Partition of a CST (fast_partition)."""
+
+    def __init__(self, cst: Cst, cfg: Config | None = None, stream=None):
+        self.cst = cst
+        h = _vp()
+        self.stream = stream if stream is not None else cst.stream
+        _check(lib().fast_partition(cst.handle, ctypes.byref(cfg) if cfg else None, self.stream, ctypes.byref(h)))
+        self._h = h
+        n, ws = _i64(), _u64()
+        _check(lib().fast_chunks_info(h, ctypes.byref(n), ctypes.byref(ws)))
+        self.n, self.w_sum = n.value, ws.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def copy(self):
+        """List of (j, prefix tuple of candidate-local indices, a, b, W', id)."""
+        n, k = self.n, self.cst.k
+        j = np.empty(max(n, 1), np.int32); pre = np.empty((max(n, 1), k), np.int32)
+        a = np.empty(max(n, 1), np.int64); b = np.empty(max(n, 1), np.int64)
+        w = np.empty(max(n, 1), np.uint64); ids = np.empty(max(n, 1), np.uint64)
+        _check(lib().fast_chunks_copy(self._h, _p(j), _p(pre), _p(a), _p(b), _p(w), _p(ids), self.stream))
+        return [(int(j[i]), tuple(int(x) for x in pre[i, :j[i]]), int(a[i]), int(b[i]), int(w[i]), int(ids[i]))
+                for i in range(n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fast_free_chunks(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def match(cst: Cst, chunks: Chunks | None = None, k: int = 0, emb_out=None, cfg: Config | None = None,
+          chunk_counts=None, stream=None, check: bool = True):
+    """fast_match_ex.  emb_out: device tensor / host array with >= k rows of
+    cst.k uint32 (allocated on the host here when None and k > 0).
+    chunk_counts: optional device buffer of one uint64 per chunk.
+    Returns dict(count, written, status, emb)."""
+    if k > 0 and emb_out is None:
+        emb_out = np.zeros((k, cst.k), np.uint32)
+    cnt, wr = _u64(), _u64()
+    rc = lib().fast_match_ex(cst.handle, chunks.handle if chunks else None, ctypes.byref(cfg) if cfg else None,
+                             k, _p(emb_out), ctypes.byref(cnt), ctypes.byref(wr), _p(chunk_counts),
+                             stream if stream is not None else cst.stream)
+    if check and rc not in (FAST_OK,):
+        _check(rc)
+    return {"count": cnt.value, "written": wr.value, "status": rc, "emb": emb_out}
+
+
+def match_stats(cst: Cst, chunks: Chunks | None = None, cfg: Config | None = None, stream=None):
+    """fast_match_stats: (algorithmic bytes, partial results per depth)."""
+    out = np.zeros(cst.k + 1, np.uint64)
+    _check(lib().fast_match_stats(cst.handle, chunks.handle if chunks else None, ctypes.byref(cfg) if cfg else None,
+                                  _p(out), stream if stream is not None else cst.stream))
+    return int(out[0]), out[1:].astype(np.int64)
+
+
+def last_match_ms() -> float:
+    """Event-timed duration of the last matcher kernel on this thread."""
+    return float(lib().fast_last_match_ms())
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(lib().fast_kernel_launches())

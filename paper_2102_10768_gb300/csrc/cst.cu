@@ -1,0 +1,736 @@
+// Candidate search tree construction (Sec. IV-A, Algorithm 1) and the
+// workload estimate (Sec. IV-C), on the device.
+//
+// Steps (each a handful of kernels; the host only sequences them and reads
+// candidate counts, which decide the root and the matching order):
+//   filter     |C0(u)| for every u in one launch over the label buckets.
+//   top-down   per tree edge (u_p -> u): the neighbour lists of C(u_p) are
+//              flattened into one edge space (prefix sum of degrees); an
+//              ordered compaction keeps neighbours that pass u's filter,
+//              writing N^{u_p}_u(v_p) in place and marking the reached
+//              vertices in a bitmap, whose compaction is C(u).
+//   bottom-up  per u, children first: one warp per candidate counts the
+//              list entries still alive in each child's bitmap; candidates
+//              with an empty child list are dropped; the surviving lists are
+//              rewritten as candidate-local indices (bitmap rank).
+//   non-tree   per non-tree edge (earlier u_j -> later u_i in the order):
+//              the same edge-space compaction over C(u_j) with the bitmap of
+//              C(u_i) as predicate and its rank as output.
+//   workload   one warp per candidate, children first: the saturating sum of
+//              c over each child list, and their product.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+#include "prims.cuh"
+
+using namespace fast;
+
+namespace {
+
+// ------------------------------------------------------------ small kernels
+
+__global__ void k_filter_count(const int32_t* __restrict__ lab_vtx, const int32_t* __restrict__ key,
+                               const int64_t* __restrict__ lo, const int64_t* __restrict__ hi,
+                               const int32_t* __restrict__ dq, unsigned long long* __restrict__ cnt) {
+    int u = blockIdx.y;
+    int64_t a = lo[u], b = hi[u];
+    int want = dq[u];
+    unsigned long long c = 0;
+    for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x)
+        c += ((key[lab_vtx[i]] & 255) >= want) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt[u], c);
+}
+
+// C0(root): the label bucket filtered by degree (bucket order = id order)
+struct FilterF {
+    using value_type = int32_t;
+    const int32_t* bucket;
+    const int32_t* key;
+    int dq;
+    __device__ void begin(int64_t) {}
+    __device__ bool eval(int64_t i, int32_t& v) const {
+        v = bucket[i];
+        return (key[v] & 255) >= dq;
+    }
+    __device__ int64_t tag(int64_t) const { return -1; }
+    __device__ void at(int64_t, int64_t) const {}
+};
+
+__global__ void k_cand_degree(const int32_t* __restrict__ cand, int64_t nc, const int64_t* __restrict__ row_ptr,
+                              int64_t* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc) out[i] = row_ptr[cand[i] + 1] - row_ptr[cand[i]];
+}
+
+__device__ __forceinline__ int64_t row_of(const int64_t* e_off, int64_t rows, int64_t i) {
+    // last r with e_off[r] <= i
+    int64_t lo = 0, hi = rows;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (e_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Top-down: flattened neighbour lists of C(u_p); keeps neighbours passing
+// u's filter (label and degree), marks them reached, writes list offsets.
+struct TopDownF {
+    using value_type = int32_t;
+    const int64_t* e_off;      // [rows+1]
+    int64_t rows;
+    const int32_t* cp;         // C(u_p)
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const int32_t* key;
+    int32_t want_key_hi;       // label
+    int32_t want_dq;
+    uint32_t* reached;         // bitmap over V(G)
+    int64_t* t_off;            // out: [rows+1]
+    int64_t row;
+    int64_t nbase;
+    __device__ void begin(int64_t i0) {
+        row = row_of(e_off, rows, i0);
+        nbase = row_ptr[cp[row]] - e_off[row];
+    }
+    __device__ bool eval(int64_t i, int32_t& v) {
+        while (i >= e_off[row + 1]) { row++; nbase = row_ptr[cp[row]] - e_off[row]; }
+        int32_t x = col[nbase + i];
+        v = x;
+        int32_t kk = key[x];
+        bool hit = (kk >> 8) == want_key_hi && (kk & 255) >= want_dq;
+        if (hit) atomicOr(&reached[x >> 5], 1u << (x & 31));
+        return hit;
+    }
+    __device__ int64_t tag(int64_t i) const { return (i == e_off[row]) ? row : -1; }
+    __device__ void at(int64_t r, int64_t rank) const { t_off[r] = rank; }
+};
+
+// Non-tree: flattened neighbour lists of C(u_j); keeps members of C(u_i)
+// (bitmap) and writes their rank in C(u_i).
+struct NonTreeF {
+    using value_type = uint32_t;
+    const int64_t* e_off;
+    int64_t rows;
+    const int32_t* cj;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const uint32_t* alive;     // bitmap of C(u_i)
+    const uint32_t* rank;      // prefix popcounts of alive
+    int64_t* n_off;
+    int64_t row;
+    int64_t nbase;
+    __device__ void begin(int64_t i0) {
+        row = row_of(e_off, rows, i0);
+        nbase = row_ptr[cj[row]] - e_off[row];
+    }
+    __device__ bool eval(int64_t i, uint32_t& v) {
+        while (i >= e_off[row + 1]) { row++; nbase = row_ptr[cj[row]] - e_off[row]; }
+        int32_t x = col[nbase + i];
+        uint32_t w = alive[x >> 5], bit = 1u << (x & 31);
+        v = rank[x >> 5] + __popc(w & (bit - 1));
+        return (w & bit) != 0;
+    }
+    __device__ int64_t tag(int64_t i) const { return (i == e_off[row]) ? row : -1; }
+    __device__ void at(int64_t r, int64_t rank_) const { n_off[r] = rank_; }
+};
+
+// candidate ids from a bitmap, in id order
+struct BitsF {
+    using value_type = int32_t;
+    const uint32_t* bits;
+    __device__ void begin(int64_t) {}
+    __device__ bool eval(int64_t i, int32_t& v) const {
+        v = (int32_t)i;
+        return (bits[i >> 5] >> (i & 31)) & 1u;
+    }
+    __device__ int64_t tag(int64_t) const { return -1; }
+    __device__ void at(int64_t, int64_t) const {}
+};
+
+// rows kept by a validity mask
+struct KeepRowsF {
+    using value_type = int32_t;
+    const int32_t* ids;
+    const uint8_t* valid;
+    __device__ void begin(int64_t) {}
+    __device__ bool eval(int64_t i, int32_t& v) const {
+        v = ids[i];
+        return valid[i] != 0;
+    }
+    __device__ int64_t tag(int64_t) const { return -1; }
+    __device__ void at(int64_t, int64_t) const {}
+};
+
+__global__ void k_set_bits(const int32_t* __restrict__ ids, int64_t n, uint32_t* __restrict__ bits) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicOr(&bits[ids[i] >> 5], 1u << (ids[i] & 31));
+}
+
+__global__ void k_popc_words(const uint32_t* __restrict__ bits, int64_t nw, uint32_t* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nw) out[i] = __popc(bits[i]);
+}
+
+// per row: entries of the list whose id is alive in the child's bitmap
+__global__ void k_count_alive(const int64_t* __restrict__ off, const int32_t* __restrict__ list, int64_t rows,
+                              const uint32_t* __restrict__ alive, int64_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < rows; r += nw) {
+        int64_t lo = off[r], hi = off[r + 1];
+        int64_t c = 0;
+        for (int64_t e = lo + lane; e < hi; e += 32) {
+            int32_t x = list[e];
+            c += (alive[x >> 5] >> (x & 31)) & 1u;
+        }
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) cnt[r] = c;
+    }
+}
+
+struct ChildCounts {
+    const int64_t* cnt[kMaxK];
+    int nch;
+};
+
+__global__ void k_valid_rows(ChildCounts cc, int64_t rows, uint8_t* __restrict__ valid, int64_t* __restrict__ vflag) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    uint8_t ok = 1;
+    for (int c = 0; c < cc.nch; c++) ok &= (cc.cnt[c][r] > 0) ? 1 : 0;
+    valid[r] = ok;
+    vflag[r] = ok;
+}
+
+__global__ void k_gather_counts(const int64_t* __restrict__ cnt, const uint8_t* __restrict__ valid,
+                                const int64_t* __restrict__ newrow, int64_t rows, int64_t* __restrict__ out) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < rows && valid[r]) out[newrow[r]] = cnt[r];
+}
+
+// rewrite the alive entries of valid rows as candidate-local indices
+__global__ void k_write_alive(const int64_t* __restrict__ off, const int32_t* __restrict__ list, int64_t rows,
+                              const uint8_t* __restrict__ valid, const int64_t* __restrict__ newrow,
+                              const uint32_t* __restrict__ alive, const uint32_t* __restrict__ rank,
+                              const int64_t* __restrict__ new_off, uint32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < rows; r += nw) {
+        if (!valid[r]) continue;
+        int64_t lo = off[r], hi = off[r + 1];
+        int64_t dst = new_off[newrow[r]];
+        for (int64_t base = lo; base < hi; base += 32) {
+            int64_t e = base + lane;
+            bool ok = false;
+            uint32_t v = 0;
+            if (e < hi) {
+                int32_t x = list[e];
+                uint32_t wd = alive[x >> 5], bit = 1u << (x & 31);
+                ok = (wd & bit) != 0;
+                v = rank[x >> 5] + __popc(wd & (bit - 1));
+            }
+            uint32_t m = __ballot_sync(0xffffffffu, ok);
+            if (ok) out[dst + __popc(m & lanemask_lt())] = v;
+            dst += __popc(m);
+        }
+    }
+}
+
+struct ChildLists {
+    const int64_t* off[kMaxK];
+    const uint32_t* idx[kMaxK];
+    const uint64_t* cval[kMaxK];
+    const double* cvalf[kMaxK];
+    uint64_t* ssum[kMaxK];
+    int nch;
+};
+
+__device__ __forceinline__ uint64_t warp_sat_sum(uint64_t v) {
+    for (int o = 16; o > 0; o >>= 1) v = sat_add(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_f(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// c_u(v) = prod over children of the sum of c over v's list (Sec. IV-C)
+__global__ void k_workload(ChildLists cl, int64_t rows, uint64_t* __restrict__ cval, double* __restrict__ cvalf) {
+    const int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < rows; r += nw) {
+        uint64_t prod = 1;
+        double prodf = 1.0;
+        for (int c = 0; c < cl.nch; c++) {
+            int64_t lo = cl.off[c][r], hi = cl.off[c][r + 1];
+            uint64_t s = 0;
+            double sf = 0.0;
+            for (int64_t e = lo + lane; e < hi; e += 32) {
+                uint32_t x = cl.idx[c][e];
+                s = sat_add(s, cl.cval[c][x]);
+                sf += cl.cvalf[c][x];
+            }
+            s = warp_sat_sum(s);
+            sf = warp_sum_f(sf);
+            if (lane == 0) cl.ssum[c][r] = s;
+            prod = sat_mul(prod, s);
+            prodf *= sf;
+        }
+        if (lane == 0) { cval[r] = prod; cvalf[r] = prodf; }
+    }
+}
+
+__global__ void k_total_w(const uint64_t* __restrict__ cval, const double* __restrict__ cvalf, int64_t n,
+                          uint64_t* __restrict__ out, double* __restrict__ outf) {
+    __shared__ uint64_t sh[32];
+    __shared__ double shf[32];
+    uint64_t s = 0;
+    double sf = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) { s = sat_add(s, cval[i]); sf += cvalf[i]; }
+    s = warp_sat_sum(s);
+    sf = warp_sum_f(sf);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { sh[warp] = s; shf[warp] = sf; }
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        s = lane < nw ? sh[lane] : 0;
+        sf = lane < nw ? shf[lane] : 0.0;
+        s = warp_sat_sum(s);
+        sf = warp_sum_f(sf);
+        if (lane == 0) { *out = s; *outf = sf; }
+    }
+}
+
+__global__ void k_fill_u64(uint64_t* p, int64_t n, uint64_t v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+__global__ void k_fill_f64(double* p, int64_t n, double v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+    int64_t b = ceil_div(n, threads);
+    return (unsigned)(b < 1 ? 1 : (b > 0x7FFFFFFF ? 0x7FFFFFFF : b));
+}
+
+inline unsigned warp_grid(int64_t rows) {
+    // one warp per row up to a persistent cap
+    int64_t blocks = ceil_div(rows, 8);
+    int64_t cap = (int64_t)num_sms() * 32;
+    if (blocks > cap) blocks = cap;
+    return (unsigned)(blocks < 1 ? 1 : blocks);
+}
+
+// ----------------------------------------------------------------- build
+
+struct Bits {
+    uint32_t* alive = nullptr;
+    uint32_t* rank = nullptr;
+};
+
+void cst_release(fast_cst* c) {
+    if (!c) return;
+    cudaStream_t s = c->stream;
+    for (int u = 0; u < kMaxK; u++) {
+        dfree(c->cand[u], s); dfree(c->t_off[u], s); dfree(c->t_idx[u], s);
+        dfree(c->cval[u], s); dfree(c->cvalf[u], s); dfree(c->ssum[u], s);
+    }
+    for (int e = 0; e < c->nnt; e++) { dfree(c->n_off[e], s); dfree(c->n_idx[e], s); }
+    delete c;
+}
+
+int validate_query(const fast_query_desc* q, int A[kMaxK][kMaxK], int* dq) {
+    if (!q) return set_error(FAST_ERR_INVALID, "query is NULL");
+    int k = q->n;
+    if (k < 1 || k > kMaxK) return set_error(FAST_ERR_INVALID, "query has %d vertices (1..%d)", k, kMaxK);
+    if (!q->labels || (q->m > 0 && !q->edges) || q->m < 0) return set_error(FAST_ERR_INVALID, "query arrays are NULL");
+    memset(A, 0, sizeof(int) * kMaxK * kMaxK);
+    for (int u = 0; u < k; u++) {
+        dq[u] = 0;
+        if (q->labels[u] < 0) return set_error(FAST_ERR_INVALID, "query label < 0");
+    }
+    for (int e = 0; e < q->m; e++) {
+        int a = q->edges[2 * e], b = q->edges[2 * e + 1];
+        if (a < 0 || b < 0 || a >= k || b >= k) return set_error(FAST_ERR_INVALID, "query edge (%d,%d) out of range", a, b);
+        if (a == b) return set_error(FAST_ERR_INVALID, "query edge (%d,%d) is a loop", a, b);
+        if (!A[a][b]) { A[a][b] = A[b][a] = 1; dq[a]++; dq[b]++; }
+    }
+    // connected?
+    int seen[kMaxK] = {0}, st[kMaxK], sp = 0, cnt = 1;
+    st[sp++] = 0; seen[0] = 1;
+    while (sp) {
+        int u = st[--sp];
+        for (int w = 0; w < k; w++) if (A[u][w] && !seen[w]) { seen[w] = 1; st[sp++] = w; cnt++; }
+    }
+    if (cnt != k) return set_error(FAST_ERR_INVALID, "query graph is disconnected");
+    return FAST_OK;
+}
+
+int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* cfg_in, cudaStream_t s,
+              fast_cst** out) {
+    if (!out) return set_error(FAST_ERR_INVALID, "fast_build_cst: out is NULL");
+    *out = nullptr;
+    if (!g) return set_error(FAST_ERR_INVALID, "fast_build_cst: graph is NULL");
+    int A[kMaxK][kMaxK], dq[kMaxK];
+    FAST_TRY(validate_query(q, A, dq));
+    const int k = q->n;
+    fast_cst* c = new fast_cst();
+    memset(c->cand, 0, sizeof(c->cand)); memset(c->t_off, 0, sizeof(c->t_off)); memset(c->t_idx, 0, sizeof(c->t_idx));
+    memset(c->cval, 0, sizeof(c->cval)); memset(c->cvalf, 0, sizeof(c->cvalf)); memset(c->ssum, 0, sizeof(c->ssum));
+    memset(c->n_off, 0, sizeof(c->n_off)); memset(c->n_idx, 0, sizeof(c->n_idx));
+    memset(c->t_entries, 0, sizeof(c->t_entries)); memset(c->ncand, 0, sizeof(c->ncand));
+    c->g = g; c->k = k; c->stream = s;
+    if (cfg_in) c->cfg = *cfg_in; else fast_config_default(&c->cfg);
+    for (int u = 0; u < k; u++) { c->qlabel[u] = q->labels[u]; c->dq[u] = dq[u]; }
+
+    const int64_t n = g->n;
+    const int64_t nw = n / 32 + 1;
+    // temporaries
+    int32_t* td_list[kMaxK] = {nullptr};    // top-down lists (data-vertex ids)
+    int64_t* td_off[kMaxK] = {nullptr};
+    int32_t* td_cand[kMaxK] = {nullptr};    // top-down candidate sets
+    int64_t td_n[kMaxK] = {0};
+    Bits bits[kMaxK];
+    int64_t* e_off = nullptr;
+    int64_t* dev_i64 = nullptr;
+    unsigned long long* cnt_d = nullptr;
+    int32_t* dq_d = nullptr;
+    int64_t* lo_d = nullptr;
+    int rc = FAST_OK;
+
+    do {
+        // ---------------------------------------------------- filter counts
+        int64_t lo[kMaxK], hi[kMaxK], c0[kMaxK];
+        int64_t maxb = 1;
+        for (int u = 0; u < k; u++) {
+            int32_t l = q->labels[u];
+            if (l < g->num_labels) { lo[u] = g->lab_ptr_host[l]; hi[u] = g->lab_ptr_host[l + 1]; }
+            else { lo[u] = hi[u] = 0; }
+            maxb = std::max<int64_t>(maxb, hi[u] - lo[u]);
+        }
+        rc = dalloc(&cnt_d, k, s); if (rc) break;
+        rc = dalloc(&dq_d, k, s); if (rc) break;
+        rc = dalloc(&lo_d, 2 * k, s); if (rc) break;
+        cudaMemsetAsync(cnt_d, 0, k * sizeof(unsigned long long), s);
+        cudaMemcpyAsync(dq_d, dq, k * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(lo_d, lo, k * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(lo_d + k, hi, k * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        {
+            dim3 grid((unsigned)std::min<int64_t>(ceil_div(maxb, 256), 1024), (unsigned)k);
+            k_filter_count<<<grid, 256, 0, s>>>(g->lab_vtx, g->key, lo_d, lo_d + k, dq_d, cnt_d);
+            note_launch();
+        }
+        unsigned long long hc[kMaxK];
+        if (cudaMemcpyAsync(hc, cnt_d, k * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "filter count"); break; }
+        for (int u = 0; u < k; u++) c0[u] = (int64_t)hc[u];
+
+        // ------------------------------------------------- root and t_q
+        int r = 0;
+        for (int u = 1; u < k; u++)
+            if ((unsigned __int128)c0[u] * (unsigned)dq[r] < (unsigned __int128)c0[r] * (unsigned)dq[u]) r = u;
+        c->root = r;
+        {
+            int seen[kMaxK] = {0}, qh = 0, qt = 0;
+            c->bfs[qt++] = r; seen[r] = 1; c->parent[r] = -1;
+            while (qh < qt) {
+                int u = c->bfs[qh++];
+                for (int w = 0; w < k; w++)
+                    if (A[u][w] && !seen[w]) { seen[w] = 1; c->parent[w] = u; c->bfs[qt++] = w; }
+            }
+        }
+
+        // ------------------------------------------------ C(root) = C0(root)
+        {
+            FilterF f{g->lab_vtx + lo[r], g->key, dq[r]};
+            rc = compact_alloc(f, hi[r] - lo[r], &td_cand[r], &td_n[r], s); if (rc) break;
+        }
+
+        // ----------------------------------------------------- top-down
+        for (int t = 1; t < k && rc == FAST_OK; t++) {
+            int u = c->bfs[t], p = c->parent[u];
+            int64_t rows = td_n[p];
+            rc = dalloc(&e_off, rows + 1, s); if (rc) break;
+            if (rows > 0) { k_cand_degree<<<grid_for(rows, 256), 256, 0, s>>>(td_cand[p], rows, g->row_ptr, e_off); note_launch(); }
+            rc = scan_exclusive<int64_t>(e_off, e_off, rows, e_off + rows, s); if (rc) break;
+            int64_t E = 0;
+            if (cudaMemcpyAsync(&E, e_off + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "edge space size"); break; }
+            rc = dalloc(&bits[u].alive, nw, s); if (rc) break;
+            cudaMemsetAsync(bits[u].alive, 0, nw * sizeof(uint32_t), s);
+            rc = dalloc(&td_off[u], rows + 1, s); if (rc) break;
+            TopDownF f{};
+            f.e_off = e_off; f.rows = rows; f.cp = td_cand[p]; f.row_ptr = g->row_ptr; f.col = g->col; f.key = g->key;
+            f.want_key_hi = q->labels[u]; f.want_dq = dq[u]; f.reached = bits[u].alive; f.t_off = td_off[u];
+            int64_t kept = 0;
+            rc = compact_alloc(f, E, &td_list[u], &kept, s); if (rc) break;
+            if (cudaMemcpyAsync(td_off[u] + rows, &kept, sizeof(int64_t), cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "offset tail"); break; }
+            dfree(e_off, s);
+            BitsF bf{bits[u].alive};
+            rc = compact_alloc(bf, n, &td_cand[u], &td_n[u], s); if (rc) break;
+            // (a pageable-source async copy has consumed `kept` on return;
+            //  the bitmap is rebuilt from the refined set during bottom-up)
+        }
+        if (rc) break;
+
+        // ---------------------------------------------------- bottom-up
+        for (int t = k - 1; t >= 0 && rc == FAST_OK; t--) {
+            int u = c->bfs[t];
+            int64_t rows = td_n[u];
+            int ch[kMaxK], nch = 0;
+            for (int w = 0; w < k; w++) if (c->parent[w] == u) ch[nch++] = w;
+            int64_t* cnt[kMaxK] = {nullptr};
+            uint8_t* valid = nullptr;
+            int64_t* newrow = nullptr;
+            do {
+                ChildCounts cc{};
+                cc.nch = nch;
+                for (int i = 0; i < nch; i++) {
+                    int w = ch[i];
+                    rc = dalloc(&cnt[i], rows, s); if (rc) break;
+                    if (rows > 0) {
+                        k_count_alive<<<warp_grid(rows), 256, 0, s>>>(td_off[w], td_list[w], rows, bits[w].alive, cnt[i]);
+                        note_launch();
+                    }
+                    cc.cnt[i] = cnt[i];
+                }
+                if (rc) break;
+                rc = dalloc(&valid, rows, s); if (rc) break;
+                rc = dalloc(&newrow, rows + 1, s); if (rc) break;
+                if (rows > 0) { k_valid_rows<<<grid_for(rows, 256), 256, 0, s>>>(cc, rows, valid, newrow); note_launch(); }
+                rc = scan_exclusive<int64_t>(newrow, newrow, rows, newrow + rows, s); if (rc) break;
+                KeepRowsF kf{td_cand[u], valid};
+                rc = compact_alloc(kf, rows, &c->cand[u], &c->ncand[u], s); if (rc) break;
+                int64_t nu = c->ncand[u];
+                for (int i = 0; i < nch && rc == FAST_OK; i++) {
+                    int w = ch[i];
+                    rc = dalloc(&c->t_off[w], nu + 1, s); if (rc) break;
+                    if (rows > 0) { k_gather_counts<<<grid_for(rows, 256), 256, 0, s>>>(cnt[i], valid, newrow, rows, c->t_off[w]); note_launch(); }
+                    rc = scan_exclusive<int64_t>(c->t_off[w], c->t_off[w], nu, c->t_off[w] + nu, s); if (rc) break;
+                    int64_t ent = 0;
+                    if (cudaMemcpyAsync(&ent, c->t_off[w] + nu, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "list size"); break; }
+                    c->t_entries[w] = ent;
+                    rc = dalloc(&c->t_idx[w], ent, s); if (rc) break;
+                    if (rows > 0) {
+                        k_write_alive<<<warp_grid(rows), 256, 0, s>>>(td_off[w], td_list[w], rows, valid, newrow,
+                                                                      bits[w].alive, bits[w].rank, c->t_off[w], c->t_idx[w]);
+                        note_launch();
+                    }
+                    dfree(td_list[w], s); dfree(td_off[w], s);
+                }
+                if (rc) break;
+                // bitmap + rank of the refined C(u)
+                if (!bits[u].alive) { rc = dalloc(&bits[u].alive, nw, s); if (rc) break; }
+                cudaMemsetAsync(bits[u].alive, 0, nw * sizeof(uint32_t), s);
+                if (nu > 0) { k_set_bits<<<grid_for(nu, 256), 256, 0, s>>>(c->cand[u], nu, bits[u].alive); note_launch(); }
+                rc = dalloc(&bits[u].rank, nw, s); if (rc) break;
+                k_popc_words<<<grid_for(nw, 256), 256, 0, s>>>(bits[u].alive, nw, bits[u].rank);
+                note_launch();
+                rc = scan_exclusive<uint32_t>(bits[u].rank, bits[u].rank, nw, (uint32_t*)nullptr, s);
+            } while (0);
+            for (int i = 0; i < nch; i++) dfree(cnt[i], s);
+            dfree(valid, s); dfree(newrow, s);
+            dfree(td_cand[u], s);
+        }
+        if (rc) break;
+
+        // ------------------------------------------------ matching order
+        {
+            int stack[kMaxK], sp = 0, no = 0;
+            stack[sp++] = r;
+            while (sp) {
+                int u = stack[--sp];
+                c->order[no++] = u;
+                int chl[kMaxK], nc = 0;
+                for (int w = 0; w < k; w++) if (c->parent[w] == u) chl[nc++] = w;
+                std::sort(chl, chl + nc, [&](int a, int b) {
+                    return c->ncand[a] != c->ncand[b] ? c->ncand[a] < c->ncand[b] : a < b;
+                });
+                for (int i = nc - 1; i >= 0; i--) stack[sp++] = chl[i];
+            }
+            for (int i = 0; i < k; i++) c->pos[c->order[i]] = i;
+        }
+
+        // ------------------------------------------------------ non-tree
+        c->nnt = 0;
+        for (int i = 0; i < k && rc == FAST_OK; i++) {
+            int ui = c->order[i];
+            for (int j = 0; j < i && rc == FAST_OK; j++) {
+                int uj = c->order[j];
+                if (!A[ui][uj] || c->parent[ui] == uj || c->parent[uj] == ui) continue;
+                int e = c->nnt++;
+                c->nt_from[e] = uj; c->nt_to[e] = ui;
+                int64_t rows = c->ncand[uj];
+                rc = dalloc(&e_off, rows + 1, s); if (rc) break;
+                if (rows > 0) { k_cand_degree<<<grid_for(rows, 256), 256, 0, s>>>(c->cand[uj], rows, g->row_ptr, e_off); note_launch(); }
+                rc = scan_exclusive<int64_t>(e_off, e_off, rows, e_off + rows, s); if (rc) break;
+                int64_t E = 0;
+                if (cudaMemcpyAsync(&E, e_off + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "edge space size"); break; }
+                rc = dalloc(&c->n_off[e], rows + 1, s); if (rc) break;
+                NonTreeF f{};
+                f.e_off = e_off; f.rows = rows; f.cj = c->cand[uj]; f.row_ptr = g->row_ptr; f.col = g->col;
+                f.alive = bits[ui].alive; f.rank = bits[ui].rank; f.n_off = c->n_off[e];
+                int64_t kept = 0;
+                rc = compact_alloc(f, E, &c->n_idx[e], &kept, s); if (rc) break;
+                c->n_entries[e] = kept;
+                if (cudaMemcpyAsync(c->n_off[e] + rows, &c->n_entries[e], sizeof(int64_t), cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "offset tail"); break; }
+                dfree(e_off, s);
+            }
+        }
+        if (rc) break;
+
+        // ------------------------------------------------------ workload
+        for (int t = k - 1; t >= 0 && rc == FAST_OK; t--) {
+            int u = c->bfs[t];
+            int64_t rows = c->ncand[u];
+            rc = dalloc(&c->cval[u], rows, s); if (rc) break;
+            rc = dalloc(&c->cvalf[u], rows, s); if (rc) break;
+            ChildLists cl{};
+            cl.nch = 0;
+            for (int w = 0; w < k && rc == FAST_OK; w++) {
+                if (c->parent[w] != u) continue;
+                rc = dalloc(&c->ssum[w], rows, s); if (rc) break;
+                cl.off[cl.nch] = c->t_off[w]; cl.idx[cl.nch] = c->t_idx[w];
+                cl.cval[cl.nch] = c->cval[w]; cl.cvalf[cl.nch] = c->cvalf[w]; cl.ssum[cl.nch] = c->ssum[w];
+                cl.nch++;
+            }
+            if (rc) break;
+            if (rows > 0) {
+                if (cl.nch == 0) {
+                    k_fill_u64<<<grid_for(rows, 256), 256, 0, s>>>(c->cval[u], rows, 1);
+                    note_launch();
+                    k_fill_f64<<<grid_for(rows, 256), 256, 0, s>>>(c->cvalf[u], rows, 1.0);
+                    note_launch();
+                } else {
+                    k_workload<<<warp_grid(rows), 256, 0, s>>>(cl, rows, c->cval[u], c->cvalf[u]);
+                    note_launch();
+                }
+            }
+        }
+        if (rc) break;
+        {
+            uint64_t* w_d = nullptr;
+            rc = dalloc(&w_d, 2, s); if (rc) break;
+            k_total_w<<<1, 1024, 0, s>>>(c->cval[r], c->cvalf[r], c->ncand[r], w_d, (double*)(w_d + 1));
+            note_launch();
+            uint64_t hw[2];
+            cudaError_t e1 = cudaMemcpyAsync(hw, w_d, sizeof(hw), cudaMemcpyDeviceToHost, s);
+            cudaError_t e2 = cudaStreamSynchronize(s);
+            dfree(w_d, s);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) { rc = cuda_status(e2 != cudaSuccess ? e2 : e1, "fast_build_cst", __FILE__, __LINE__); break; }
+            c->W = hw[0];
+            memcpy(&c->Wf, &hw[1], sizeof(double));
+        }
+    } while (0);
+
+    for (int u = 0; u < kMaxK; u++) {
+        dfree(td_list[u], s); dfree(td_off[u], s); dfree(td_cand[u], s);
+        dfree(bits[u].alive, s); dfree(bits[u].rank, s);
+    }
+    dfree(e_off, s); dfree(dev_i64, s); dfree(cnt_d, s); dfree(dq_d, s); dfree(lo_d, s);
+    if (rc != FAST_OK) {
+        cst_release(c);
+        return rc;
+    }
+    *out = c;
+    return FAST_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- C ABI
+
+extern "C" int fast_build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* cfg, void* stream,
+                              fast_cst** out) {
+    return build_cst(g, q, cfg, (cudaStream_t)stream, out);
+}
+
+extern "C" int fast_cst_info(const fast_cst* c, int32_t* k, int32_t* root, int32_t* order, int32_t* parent,
+                             int64_t* cand, uint64_t* w_u64, double* w_f64) {
+    if (!c) return set_error(FAST_ERR_INVALID, "fast_cst_info: NULL cst");
+    if (k) *k = c->k;
+    if (root) *root = c->root;
+    for (int i = 0; i < c->k; i++) {
+        if (order) order[i] = c->order[i];
+        if (parent) parent[i] = c->parent[i];
+        if (cand) cand[i] = c->ncand[i];
+    }
+    if (w_u64) *w_u64 = c->W;
+    if (w_f64) *w_f64 = c->Wf;
+    return FAST_OK;
+}
+
+extern "C" int fast_cst_candidates(const fast_cst* c, int32_t u, int32_t* out, void* stream) {
+    if (!c || u < 0 || u >= c->k || (!out && c->ncand[u])) return set_error(FAST_ERR_INVALID, "fast_cst_candidates: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->ncand[u]) FAST_CUDA(cudaMemcpyAsync(out, c->cand[u], c->ncand[u] * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FAST_CUDA(cudaStreamSynchronize(s));
+    return FAST_OK;
+}
+
+extern "C" int fast_cst_tree_size(const fast_cst* c, int32_t u, int64_t* entries) {
+    if (!c || u < 0 || u >= c->k || !entries) return set_error(FAST_ERR_INVALID, "fast_cst_tree_size: bad argument");
+    *entries = c->parent[u] < 0 ? 0 : c->t_entries[u];
+    return FAST_OK;
+}
+
+extern "C" int fast_cst_tree_lists(const fast_cst* c, int32_t u, int64_t* off, uint32_t* idx, void* stream) {
+    if (!c || u < 0 || u >= c->k || c->parent[u] < 0 || !off) return set_error(FAST_ERR_INVALID, "fast_cst_tree_lists: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t rows = c->ncand[c->parent[u]];
+    FAST_CUDA(cudaMemcpyAsync(off, c->t_off[u], (rows + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (c->t_entries[u]) FAST_CUDA(cudaMemcpyAsync(idx, c->t_idx[u], c->t_entries[u] * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    FAST_CUDA(cudaStreamSynchronize(s));
+    return FAST_OK;
+}
+
+extern "C" int fast_cst_nontree_count(const fast_cst* c, int32_t* count) {
+    if (!c || !count) return set_error(FAST_ERR_INVALID, "fast_cst_nontree_count: bad argument");
+    *count = c->nnt;
+    return FAST_OK;
+}
+
+extern "C" int fast_cst_nontree_edge(const fast_cst* c, int32_t e, int32_t* from_u, int32_t* to_u, int64_t* entries) {
+    if (!c || e < 0 || e >= c->nnt) return set_error(FAST_ERR_INVALID, "fast_cst_nontree_edge: bad argument");
+    if (from_u) *from_u = c->nt_from[e];
+    if (to_u) *to_u = c->nt_to[e];
+    if (entries) *entries = c->n_entries[e];
+    return FAST_OK;
+}
+
+extern "C" int fast_cst_nontree_lists(const fast_cst* c, int32_t e, int64_t* off, uint32_t* idx, void* stream) {
+    if (!c || e < 0 || e >= c->nnt || !off) return set_error(FAST_ERR_INVALID, "fast_cst_nontree_lists: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t rows = c->ncand[c->nt_from[e]];
+    FAST_CUDA(cudaMemcpyAsync(off, c->n_off[e], (rows + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (c->n_entries[e]) FAST_CUDA(cudaMemcpyAsync(idx, c->n_idx[e], c->n_entries[e] * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    FAST_CUDA(cudaStreamSynchronize(s));
+    return FAST_OK;
+}
+
+extern "C" int fast_cst_workload(const fast_cst* c, int32_t u, uint64_t* out, void* stream) {
+    if (!c || u < 0 || u >= c->k || (!out && c->ncand[u])) return set_error(FAST_ERR_INVALID, "fast_cst_workload: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->ncand[u]) FAST_CUDA(cudaMemcpyAsync(out, c->cval[u], c->ncand[u] * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    FAST_CUDA(cudaStreamSynchronize(s));
+    return FAST_OK;
+}
+
+extern "C" void fast_free_cst(fast_cst* c) {
+    if (!c) return;
+    cudaStream_t s = c->stream;
+    cst_release(c);
+    cudaStreamSynchronize(s);
+}

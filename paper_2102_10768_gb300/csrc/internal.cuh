@@ -1,0 +1,77 @@
+// Definitions of the library's opaque handles (device-resident data graph,
+// candidate search tree and partition) and of the chunk descriptor shared by
+// the partitioner and the matcher.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+constexpr int kMaxK = FAST_MAX_QUERY;
+constexpr int kMaxNT = kMaxK * (kMaxK - 1) / 2;
+
+// Data graph G (Sec. II-A) on the device.
+struct fast_graph {
+    int64_t n = 0;
+    int64_t nadj = 0;          // stored adjacency entries (2|E|)
+    int32_t num_labels = 0;
+    int64_t max_degree = 0;
+    int64_t* row_ptr = nullptr;   // [n+1]
+    int32_t* col = nullptr;       // [nadj], each row sorted ascending
+    int32_t* label = nullptr;     // [n]
+    int32_t* key = nullptr;       // [n] (label << 8) | min(degree, 255): one load per filter test
+    int64_t* lab_ptr = nullptr;   // [num_labels+1]
+    int32_t* lab_vtx = nullptr;   // [n] vertices grouped by label, ascending id
+    std::vector<int64_t> lab_ptr_host;
+};
+
+// Candidate search tree (Sec. IV-A) of one query.  Indexed by query vertex
+// unless noted; lists hold candidate-local indices.
+struct fast_cst {
+    const fast_graph* g = nullptr;
+    int k = 0;
+    int root = 0;
+    int order[kMaxK];          // position -> query vertex (matching order O)
+    int pos[kMaxK];            // query vertex -> position
+    int parent[kMaxK];         // query vertex -> parent in t_q (-1: root)
+    int bfs[kMaxK];            // BFS order of t_q
+    int32_t qlabel[kMaxK];
+    int32_t dq[kMaxK];         // query degree
+    int64_t ncand[kMaxK];      // |C(u)|
+    int32_t* cand[kMaxK];      // C(u): sorted data-vertex ids
+    int64_t* t_off[kMaxK];     // tree lists into u: offsets over rows of C(parent(u))
+    uint32_t* t_idx[kMaxK];    //   entries: indices into C(u)
+    int64_t t_entries[kMaxK];
+    int nnt = 0;
+    int nt_from[kMaxNT], nt_to[kMaxNT];   // query vertices, earlier -> later in O
+    int64_t* n_off[kMaxNT];
+    uint32_t* n_idx[kMaxNT];
+    int64_t n_entries[kMaxNT];
+    uint64_t* cval[kMaxK];     // c_u(v), saturating uint64 (Sec. IV-C)
+    double* cvalf[kMaxK];      // c_u(v), float64
+    uint64_t* ssum[kMaxK];     // per row of C(parent(u)): sum of c_u over its list into u
+    uint64_t W = 0;
+    double Wf = 0.0;
+    fast_config cfg;
+    cudaStream_t stream = nullptr;
+};
+
+// One chunk of a partitioned CST (Sec. IV-B): positions 0..j-1 fixed to one
+// candidate each (prefix, candidate-local indices), position j restricted to
+// entries [a, b) of its list L_j.
+struct alignas(16) Chunk {
+    int32_t j;
+    uint32_t a, b;
+    uint32_t pad;
+    uint64_t w;                // workload estimate W' (saturating)
+    uint64_t id;               // sampling id
+    uint32_t prefix[kMaxK];
+};
+
+struct fast_chunks {
+    const fast_cst* c = nullptr;
+    int64_t n = 0;
+    Chunk* d = nullptr;        // device [n]
+    uint64_t w_sum = 0;
+    cudaStream_t stream = nullptr;
+};

@@ -1,0 +1,335 @@
+// CST partition (Sec. IV-B, Algorithm 2) driven by the workload estimate of
+// Sec. IV-C, level-synchronous on the device.
+//
+// A pending part is a Chunk: positions 0..j-1 fixed (prefix), position j
+// restricted to the run [a, b) of its list L_j.  Its estimate is
+//   W' = F(prefix) * sum_{x in L_j[a..b)} c_{u_j}(x),
+//   F(prefix) = prod over prefix positions p, over children c of p placed
+//               after j, of the per-row child sum s_{p->c}(prefix[p]),
+// which equals the workload DP evaluated on the partitioned tree: restricting
+// a candidate set to the part leaves c unchanged for every candidate still
+// reachable, and every position after j hangs below a prefix position.
+// One level = three kernels (decide and count parts, write parts, sum the
+// parts' estimates); the host reads two sizes per level.
+#include <vector>
+
+#include "internal.cuh"
+#include "prims.cuh"
+
+using namespace fast;
+
+namespace {
+
+struct PartPlan {
+    int k;
+    int par_pos[kMaxK];            // position -> parent position (-1 at 0)
+    uint32_t child_mask[kMaxK];    // position -> bitmask of child positions
+    const int64_t* t_off[kMaxK];   // by position (tree edge into it)
+    const uint32_t* t_idx[kMaxK];
+    const uint64_t* cval[kMaxK];   // by position
+    const uint64_t* ssum[kMaxK];   // by position: per row of C(parent position)
+    uint64_t delta_w;
+    double c_root, c_deep;
+};
+
+struct PartRec {
+    uint32_t item;
+    uint32_t a, b;
+    uint32_t pad;
+    uint64_t id;
+    uint64_t f;                    // F(prefix)
+};
+
+__device__ __forceinline__ uint32_t list_at(const PartPlan& P, const Chunk& c, uint64_t x) {
+    if (c.j == 0) return (uint32_t)x;
+    int64_t base = P.t_off[c.j][c.prefix[P.par_pos[c.j]]];
+    return P.t_idx[c.j][base + (int64_t)x];
+}
+
+__device__ __forceinline__ uint32_t list_len(const PartPlan& P, const Chunk& c, uint32_t root_n) {
+    if (c.j == 0) return root_n;
+    uint32_t m = c.prefix[P.par_pos[c.j]];
+    return (uint32_t)(P.t_off[c.j][m + 1] - P.t_off[c.j][m]);
+}
+
+__device__ __forceinline__ bool keep_part(const PartPlan& P, int j, uint64_t kk, uint64_t id) {
+    double cs = j == 0 ? P.c_root : P.c_deep;
+    if (cs <= 0.0) return true;
+    double tau = cs / (double)kk;
+    if (!(tau < 1.0)) return true;
+    return (double)(id >> 11) * (1.0 / 9007199254740992.0) < tau;
+}
+
+// Advance single-candidate runs to the next position (same estimate), then
+// classify: 0 drop, 1 emit as a chunk, 2 split.  Writes the advanced item
+// back.  Returns the split factor in *kk_out.
+__device__ int classify(const PartPlan& P, Chunk& c, uint32_t root_n, uint64_t* kk_out) {
+    for (;;) {
+        if (c.w == 0) return 0;
+        if (c.w <= P.delta_w) return 1;
+        uint32_t n = c.b - c.a;
+        if (n == 1) {
+            if (c.j + 1 >= P.k) return 1;
+            c.prefix[c.j] = list_at(P, c, c.a);
+            c.j += 1;
+            c.a = 0;
+            c.b = list_len(P, c, root_n);
+            continue;
+        }
+        uint64_t kk = c.w / P.delta_w + (c.w % P.delta_w != 0);
+        if (kk > n) kk = n;
+        *kk_out = kk;
+        return 2;
+    }
+}
+
+// one thread per pending item: classify and count the kept parts
+__global__ void k_part_count(const PartPlan P, Chunk* __restrict__ items, int64_t nitems, uint32_t root_n,
+                             int64_t* __restrict__ nparts, int64_t* __restrict__ nemit) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nitems) return;
+    Chunk c = items[t];
+    uint64_t kk = 0;
+    int act = classify(P, c, root_n, &kk);
+    items[t] = c;
+    int64_t np = 0;
+    if (act == 2) {
+        for (uint64_t i = 0; i < kk; i++)
+            np += keep_part(P, c.j, kk, mix64(c.id + (i + 1) * 0x9E3779B97F4A7C15ull)) ? 1 : 0;
+    }
+    nparts[t] = np;
+    nemit[t] = act == 1 ? 1 : 0;
+}
+
+__device__ uint64_t prefix_factor(const PartPlan& P, const Chunk& c) {
+    uint64_t f = 1;
+    for (int p = 0; p < c.j; p++) {
+        uint32_t m = P.child_mask[p];
+        while (m) {
+            int ch = __ffs(m) - 1;
+            m &= m - 1;
+            if (ch > c.j) f = sat_mul(f, P.ssum[ch][c.prefix[p]]);
+        }
+    }
+    return f;
+}
+
+// one thread per pending item: write emitted chunks and part records
+__global__ void k_part_write(const PartPlan P, const Chunk* __restrict__ items, int64_t nitems,
+                             const int64_t* __restrict__ part_off, const int64_t* __restrict__ emit_off,
+                             PartRec* __restrict__ parts, Chunk* __restrict__ emitted) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nitems) return;
+    Chunk c = items[t];
+    int64_t np = part_off[t + 1] - part_off[t];
+    int64_t ne = emit_off[t + 1] - emit_off[t];
+    if (ne) emitted[emit_off[t]] = c;
+    if (!np) return;
+    uint32_t n = c.b - c.a;
+    uint64_t kk = c.w / P.delta_w + (c.w % P.delta_w != 0);
+    if (kk > n) kk = n;
+    uint64_t f = prefix_factor(P, c);
+    int64_t o = part_off[t];
+    for (uint64_t i = 0; i < kk; i++) {
+        uint64_t id = mix64(c.id + (i + 1) * 0x9E3779B97F4A7C15ull);
+        if (!keep_part(P, c.j, kk, id)) continue;
+        PartRec r;
+        r.item = (uint32_t)t;
+        r.a = c.a + (uint32_t)((i * (uint64_t)n) / kk);
+        r.b = c.a + (uint32_t)(((i + 1) * (uint64_t)n) / kk);
+        r.pad = 0;
+        r.id = id;
+        r.f = f;
+        parts[o++] = r;
+    }
+}
+
+// one warp per part: W' = F * (saturating sum of c over the run)
+__global__ void k_part_sum(const PartPlan P, const Chunk* __restrict__ items, const PartRec* __restrict__ parts,
+                           int64_t nparts, Chunk* __restrict__ next) {
+    const int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = w; p < nparts; p += nw) {
+        PartRec r = parts[p];
+        const Chunk& it = items[r.item];
+        int j = it.j;
+        const uint64_t* cv = P.cval[j];
+        uint64_t s = 0;
+        if (j == 0) {
+            for (uint64_t x = r.a + lane; x < r.b; x += 32) s = sat_add(s, cv[x]);
+        } else {
+            int64_t base = P.t_off[j][it.prefix[P.par_pos[j]]];
+            for (uint64_t x = r.a + lane; x < r.b; x += 32) s = sat_add(s, cv[P.t_idx[j][base + (int64_t)x]]);
+        }
+        for (int o = 16; o > 0; o >>= 1) s = sat_add(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if (lane < kMaxK) {
+            uint32_t* dst = next[p].prefix;
+            dst[lane] = lane < j ? it.prefix[lane] : 0u;
+        }
+        if (lane == 0) {
+            next[p].j = j;
+            next[p].a = r.a;
+            next[p].b = r.b;
+            next[p].pad = 0;
+            next[p].w = sat_mul(r.f, s);
+            next[p].id = r.id;
+        }
+    }
+}
+
+PartPlan make_plan(const fast_cst* c, const fast_config* cfg) {
+    PartPlan P;
+    memset(&P, 0, sizeof(P));
+    P.k = c->k;
+    for (int i = 0; i < c->k; i++) {
+        int u = c->order[i];
+        P.par_pos[i] = c->parent[u] < 0 ? -1 : c->pos[c->parent[u]];
+        P.t_off[i] = c->t_off[u];
+        P.t_idx[i] = c->t_idx[u];
+        P.cval[i] = c->cval[u];
+        P.ssum[i] = c->ssum[u];
+        P.child_mask[i] = 0;
+    }
+    for (int i = 1; i < c->k; i++) P.child_mask[P.par_pos[i]] |= 1u << i;
+    P.delta_w = cfg->delta_w ? cfg->delta_w : 1;
+    P.c_root = cfg->sample_root;
+    P.c_deep = cfg->sample_deep;
+    return P;
+}
+
+int partition(const fast_cst* c, const fast_config* cfg_in, cudaStream_t s, fast_chunks** out) {
+    if (!out) return set_error(FAST_ERR_INVALID, "fast_partition: out is NULL");
+    *out = nullptr;
+    if (!c) return set_error(FAST_ERR_INVALID, "fast_partition: cst is NULL");
+    fast_config cfg;
+    if (cfg_in) cfg = *cfg_in; else cfg = c->cfg;
+    PartPlan P = make_plan(c, &cfg);
+    uint32_t root_n = (uint32_t)c->ncand[c->root];
+    std::vector<std::pair<Chunk*, int64_t>> levels;
+    int64_t total = 0;
+    Chunk* items = nullptr;
+    int64_t nitems = 0;
+    int rc = FAST_OK;
+    int64_t* cnt = nullptr;
+    PartRec* parts = nullptr;
+    Chunk* next = nullptr;
+    const int64_t cap = cfg.max_chunks > 0 ? cfg.max_chunks : (1ll << 22);
+
+    if (root_n > 0 && c->W > 0) {
+        Chunk r0;
+        memset(&r0, 0, sizeof(r0));
+        r0.j = 0; r0.a = 0; r0.b = root_n; r0.w = c->W; r0.id = mix64(cfg.sample_seed);
+        rc = dalloc(&items, 1, s);
+        if (rc == FAST_OK) {
+            cudaError_t e = cudaMemcpyAsync(items, &r0, sizeof(Chunk), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) rc = cuda_status(e, "partition seed", __FILE__, __LINE__);
+            nitems = 1;
+        }
+    }
+    while (rc == FAST_OK && nitems > 0) {
+        // counts: [0, nitems] part offsets, [nitems+1, 2 nitems+1] emit offsets
+        rc = dalloc(&cnt, 2 * (nitems + 1), s); if (rc) break;
+        int64_t* part_off = cnt;
+        int64_t* emit_off = cnt + nitems + 1;
+        k_part_count<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(P, items, nitems, root_n, part_off, emit_off);
+        note_launch();
+        rc = scan_exclusive<int64_t>(part_off, part_off, nitems, part_off + nitems, s); if (rc) break;
+        rc = scan_exclusive<int64_t>(emit_off, emit_off, nitems, emit_off + nitems, s); if (rc) break;
+        int64_t np = 0, ne = 0;
+        cudaError_t e = cudaMemcpyAsync(&np, part_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ne, emit_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { rc = cuda_status(e, "partition level sizes", __FILE__, __LINE__); break; }
+        if (total + ne > cap || np > 4 * cap) {
+            rc = set_error(FAST_ERR_LIMIT, "fast_partition: more than max_chunks=%lld chunks", (long long)cap);
+            break;
+        }
+        Chunk* em = nullptr;
+        if (ne) { rc = dalloc(&em, ne, s); if (rc) break; levels.push_back({em, ne}); total += ne; }
+        rc = dalloc(&parts, np, s); if (rc) break;
+        k_part_write<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(P, items, nitems, part_off, emit_off, parts, em);
+        note_launch();
+        rc = dalloc(&next, np, s); if (rc) break;
+        if (np) {
+            int64_t blocks = std::min<int64_t>(ceil_div(np, 8), (int64_t)num_sms() * 32);
+            k_part_sum<<<(unsigned)blocks, 256, 0, s>>>(P, items, parts, np, next);
+            note_launch();
+        }
+        if (cudaGetLastError() != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "partition kernel launch"); break; }
+        dfree(cnt, s); dfree(parts, s); dfree(items, s);
+        items = next; next = nullptr;
+        nitems = np;
+    }
+    dfree(cnt, s); dfree(parts, s); dfree(next, s); dfree(items, s);
+    fast_chunks* ch = nullptr;
+    if (rc == FAST_OK) {
+        ch = new fast_chunks();
+        ch->c = c; ch->n = total; ch->stream = s;
+        rc = dalloc(&ch->d, total, s);
+        int64_t o = 0;
+        for (auto& lv : levels) {
+            if (rc != FAST_OK) break;
+            cudaError_t e = cudaMemcpyAsync(ch->d + o, lv.first, lv.second * sizeof(Chunk), cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) rc = cuda_status(e, "partition gather", __FILE__, __LINE__);
+            o += lv.second;
+        }
+    }
+    for (auto& lv : levels) dfree(lv.first, s);
+    if (rc == FAST_OK) {
+        // summed estimate (host side; chunk counts are modest)
+        std::vector<Chunk> h(total);
+        cudaError_t e = total ? cudaMemcpyAsync(h.data(), ch->d, total * sizeof(Chunk), cudaMemcpyDeviceToHost, s) : cudaSuccess;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_status(e, "partition readback", __FILE__, __LINE__);
+        uint64_t ws = 0;
+        for (auto& x : h) ws = sat_add(ws, x.w);
+        if (ch) ch->w_sum = ws;
+    }
+    if (rc != FAST_OK) {
+        if (ch) { dfree(ch->d, s); delete ch; }
+        return rc;
+    }
+    *out = ch;
+    return FAST_OK;
+}
+
+}  // namespace
+
+extern "C" int fast_partition(const fast_cst* c, const fast_config* cfg, void* stream, fast_chunks** out) {
+    return partition(c, cfg, (cudaStream_t)stream, out);
+}
+
+extern "C" int fast_chunks_info(const fast_chunks* ch, int64_t* count, uint64_t* w_sum) {
+    if (!ch) return set_error(FAST_ERR_INVALID, "fast_chunks_info: NULL chunks");
+    if (count) *count = ch->n;
+    if (w_sum) *w_sum = ch->w_sum;
+    return FAST_OK;
+}
+
+extern "C" int fast_chunks_copy(const fast_chunks* ch, int32_t* j, int32_t* prefix, int64_t* a, int64_t* b,
+                                uint64_t* w, uint64_t* id, void* stream) {
+    if (!ch) return set_error(FAST_ERR_INVALID, "fast_chunks_copy: NULL chunks");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Chunk> h(ch->n);
+    if (ch->n) FAST_CUDA(cudaMemcpyAsync(h.data(), ch->d, ch->n * sizeof(Chunk), cudaMemcpyDeviceToHost, s));
+    FAST_CUDA(cudaStreamSynchronize(s));
+    int k = ch->c->k;
+    for (int64_t i = 0; i < ch->n; i++) {
+        if (j) j[i] = h[i].j;
+        if (prefix) for (int t = 0; t < k; t++) prefix[i * k + t] = t < h[i].j ? (int32_t)h[i].prefix[t] : -1;
+        if (a) a[i] = h[i].a;
+        if (b) b[i] = h[i].b;
+        if (w) w[i] = h[i].w;
+        if (id) id[i] = h[i].id;
+    }
+    return FAST_OK;
+}
+
+extern "C" void fast_free_chunks(fast_chunks* ch) {
+    if (!ch) return;
+    cudaStream_t s = ch->stream;
+    dfree(ch->d, s);
+    delete ch;
+    cudaStreamSynchronize(s);
+}

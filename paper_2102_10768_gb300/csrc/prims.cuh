@@ -1,0 +1,359 @@
+// Device-wide building blocks written for this library: exclusive scan,
+// ordered predicate compaction over an index space, and a stable LSD radix
+// sort of 64-bit keys.  All are stream-ordered and allocate their scratch
+// with cudaMallocAsync on the caller's stream.
+#pragma once
+
+#include "common.cuh"
+
+namespace fast {
+
+constexpr int kScanBlock = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+// Block-wide exclusive scan of ITEMS values per thread (blocked layout:
+// thread t holds tile positions t*ITEMS .. t*ITEMS+ITEMS-1).  Returns the
+// block total.  `warp_tmp` needs BLOCK/32 entries of shared memory.
+template <class T, int BLOCK, int ITEMS>
+__device__ __forceinline__ T block_exclusive_scan(T (&v)[ITEMS], T* warp_tmp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T local = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) { T x = v[i]; v[i] = local; local += x; }
+    T incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        T t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) warp_tmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NW = BLOCK / 32;
+        T x = lane < NW ? warp_tmp[lane] : T(0);
+        T y = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            T t = __shfl_up_sync(0xffffffffu, y, off);
+            if (lane >= off) y += t;
+        }
+        if (lane < NW) warp_tmp[lane] = y - x;       // exclusive
+        if (lane == NW - 1) warp_tmp[NW] = y;         // total
+    }
+    __syncthreads();
+    T base = warp_tmp[warp] + (incl - local);
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) v[i] += base;
+    T total = warp_tmp[BLOCK / 32];
+    __syncthreads();
+    return total;
+}
+
+template <class T>
+__global__ void k_scan_partials(const T* __restrict__ in, int64_t n, T* __restrict__ partials) {
+    __shared__ T tmp[kScanBlock / 32 + 1];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    T v[kScanItems];
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) v[i] = (base + i < n) ? in[base + i] : T(0);
+    T tot = block_exclusive_scan<T, kScanBlock, kScanItems>(v, tmp);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ void k_scan_apply(const T* __restrict__ in, T* __restrict__ out, int64_t n,
+                             const T* __restrict__ partials, T* __restrict__ total) {
+    __shared__ T tmp[kScanBlock / 32 + 1];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    T v[kScanItems];
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) v[i] = (base + i < n) ? in[base + i] : T(0);
+    T tot = block_exclusive_scan<T, kScanBlock, kScanItems>(v, tmp);
+    T off = partials ? partials[blockIdx.x] : T(0);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++)
+        if (base + i < n) out[base + i] = v[i] + off;
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = off + tot;
+}
+
+// out[i] = in[0] + ... + in[i-1]; *total (device, nullable) = sum of all.
+// in and out may alias.
+template <class T>
+int scan_exclusive(const T* in, T* out, int64_t n, T* total, cudaStream_t s) {
+    if (n <= 0) {
+        if (total) FAST_CUDA(cudaMemsetAsync(total, 0, sizeof(T), s));
+        return FAST_OK;
+    }
+    int64_t nb = ceil_div(n, kScanTile);
+    if (nb == 1) {
+        k_scan_apply<T><<<1, kScanBlock, 0, s>>>(in, out, n, (const T*)nullptr, total);
+        note_launch();
+        FAST_CUDA(cudaGetLastError());
+        return FAST_OK;
+    }
+    T* part = nullptr;
+    FAST_TRY(dalloc(&part, nb, s));
+    k_scan_partials<T><<<(unsigned)nb, kScanBlock, 0, s>>>(in, n, part);
+    note_launch();
+    int rc = cudaGetLastError() == cudaSuccess ? FAST_OK : set_error(FAST_ERR_CUDA, "scan partials launch");
+    if (rc == FAST_OK) rc = scan_exclusive<T>(part, part, nb, (T*)nullptr, s);
+    if (rc == FAST_OK) {
+        k_scan_apply<T><<<(unsigned)nb, kScanBlock, 0, s>>>(in, out, n, part, total);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "scan apply launch");
+    }
+    dfree(part, s);
+    return rc;
+}
+
+// ---------------------------------------------------------------- compaction
+//
+// Ordered compaction over indices [0, n): F::eval(i, val) says whether index
+// i is kept and what to write; kept values land in out[] in index order.
+// F::begin(i0) is called once per thread before it evaluates indices i0,
+// i0+1, ... in increasing order.  In the write pass F::tag(i), called right
+// after eval(i), may return a non-negative tag (e.g. the row that index i
+// starts); F::at(tag, rank) then receives the number of kept indices before
+// i (used to write list offsets).
+
+constexpr int kCompBlock = 256;
+constexpr int kCompItems = 8;
+constexpr int kCompTile = kCompBlock * kCompItems;
+
+template <class F>
+__global__ void k_compact_count(F f, int64_t n, int64_t* __restrict__ counts) {
+    __shared__ int64_t tmp[kCompBlock / 32 + 1];
+    int64_t base = (int64_t)blockIdx.x * kCompTile + (int64_t)threadIdx.x * kCompItems;
+    int64_t v[kCompItems];
+    F g = f;
+    g.begin(base);
+#pragma unroll
+    for (int i = 0; i < kCompItems; i++) {
+        typename F::value_type x;
+        v[i] = (base + i < n && g.eval(base + i, x)) ? 1 : 0;
+    }
+    int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kCompItems>(v, tmp);
+    if (threadIdx.x == 0) counts[blockIdx.x] = tot;
+}
+
+template <class F>
+__global__ void k_compact_write(F f, int64_t n, const int64_t* __restrict__ offs,
+                                typename F::value_type* __restrict__ out, int64_t* __restrict__ count) {
+    __shared__ int64_t tmp[kCompBlock / 32 + 1];
+    int64_t base = (int64_t)blockIdx.x * kCompTile + (int64_t)threadIdx.x * kCompItems;
+    int64_t v[kCompItems];
+    typename F::value_type val[kCompItems];
+    int64_t tg[kCompItems];
+    F g = f;
+    g.begin(base);
+#pragma unroll
+    for (int i = 0; i < kCompItems; i++) {
+        v[i] = (base + i < n && g.eval(base + i, val[i])) ? 1 : 0;
+        tg[i] = (base + i < n) ? g.tag(base + i) : -1;
+    }
+    int64_t hit[kCompItems];
+#pragma unroll
+    for (int i = 0; i < kCompItems; i++) hit[i] = v[i];
+    int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kCompItems>(v, tmp);
+    int64_t off = offs[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kCompItems; i++) {
+        if (tg[i] >= 0) g.at(tg[i], off + v[i]);
+        if (hit[i]) out[off + v[i]] = val[i];
+    }
+    if (count && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *count = off + tot;
+}
+
+// Runs the two passes; *count_dev receives the kept count (device memory).
+template <class F>
+int compact(const F& f, int64_t n, typename F::value_type* out, int64_t* count_dev, cudaStream_t s) {
+    if (n <= 0) {
+        if (count_dev) FAST_CUDA(cudaMemsetAsync(count_dev, 0, sizeof(int64_t), s));
+        return FAST_OK;
+    }
+    int64_t nb = ceil_div(n, kCompTile);
+    int64_t* offs = nullptr;
+    FAST_TRY(dalloc(&offs, nb, s));
+    k_compact_count<F><<<(unsigned)nb, kCompBlock, 0, s>>>(f, n, offs);
+    note_launch();
+    int rc = cudaGetLastError() == cudaSuccess ? FAST_OK : set_error(FAST_ERR_CUDA, "compact count launch");
+    if (rc == FAST_OK) rc = scan_exclusive<int64_t>(offs, offs, nb, (int64_t*)nullptr, s);
+    if (rc == FAST_OK) {
+        k_compact_write<F><<<(unsigned)nb, kCompBlock, 0, s>>>(f, n, offs, out, count_dev);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "compact write launch");
+    }
+    dfree(offs, s);
+    return rc;
+}
+
+// Size query for a compaction whose output size is not known in advance:
+// runs the counting pass only and returns the kept count on the host.
+template <class F>
+int compact_size(const F& f, int64_t n, int64_t* kept_host, cudaStream_t s) {
+    *kept_host = 0;
+    if (n <= 0) return FAST_OK;
+    int64_t nb = ceil_div(n, kCompTile);
+    int64_t* offs = nullptr;
+    int64_t* tot = nullptr;
+    FAST_TRY(dalloc(&offs, nb, s));
+    int rc = dalloc(&tot, 1, s);
+    if (rc == FAST_OK) {
+        k_compact_count<F><<<(unsigned)nb, kCompBlock, 0, s>>>(f, n, offs);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "compact count launch");
+    }
+    if (rc == FAST_OK) rc = scan_exclusive<int64_t>(offs, offs, nb, tot, s);
+    if (rc == FAST_OK) {
+        cudaError_t e = cudaMemcpyAsync(kept_host, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_status(e, "compact_size readback", __FILE__, __LINE__);
+    }
+    dfree(offs, s);
+    dfree(tot, s);
+    return rc;
+}
+
+// Count, allocate the output (stream-ordered), then write: one host sync to
+// learn the size.  *out is left null when nothing is kept.
+template <class F>
+int compact_alloc(const F& f, int64_t n, typename F::value_type** out, int64_t* kept_host, cudaStream_t s) {
+    *out = nullptr;
+    *kept_host = 0;
+    if (n <= 0) return FAST_OK;
+    int64_t nb = ceil_div(n, kCompTile);
+    int64_t* offs = nullptr;
+    int64_t* tot = nullptr;
+    FAST_TRY(dalloc(&offs, nb + 1, s));
+    tot = offs + nb;
+    int rc = FAST_OK;
+    k_compact_count<F><<<(unsigned)nb, kCompBlock, 0, s>>>(f, n, offs);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "compact count launch");
+    if (rc == FAST_OK) rc = scan_exclusive<int64_t>(offs, offs, nb, tot, s);
+    if (rc == FAST_OK) {
+        cudaError_t e = cudaMemcpyAsync(kept_host, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_status(e, "compaction size readback", __FILE__, __LINE__);
+    }
+    if (rc == FAST_OK) rc = dalloc(out, (size_t)(*kept_host), s);
+    if (rc == FAST_OK) {
+        k_compact_write<F><<<(unsigned)nb, kCompBlock, 0, s>>>(f, n, offs, *out, (int64_t*)nullptr);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "compact write launch");
+    }
+    dfree(offs, s);
+    if (rc != FAST_OK) dfree(*out, s);
+    return rc;
+}
+
+// --------------------------------------------------------------- radix sort
+//
+// Stable LSD radix sort of uint64 keys, 8-bit digits, over the digit
+// positions listed in `shifts`.  Three kernels per pass: per-tile digit
+// histograms, a digit-major exclusive scan of them, and a stable scatter that
+// ranks keys inside a tile warp by warp with __match_any_sync.
+
+constexpr int kSortBlock = 256;
+constexpr int kSortRounds = 16;
+constexpr int kSortTile = kSortBlock * kSortRounds;
+
+static __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int64_t nblocks,
+                             uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; r++) {
+        int64_t i = base + (int64_t)r * kSortBlock + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+static __global__ void k_radix_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n,
+                                int shift, int64_t nblocks, const uint32_t* __restrict__ offs) {
+    constexpr int NW = kSortBlock / 32;
+    __shared__ uint32_t goff[256];        // global start of this tile's digit run
+    __shared__ uint32_t run[256];         // keys of each digit already placed
+    __shared__ uint32_t wcnt[NW][256];    // per-round per-warp counts -> offsets
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    goff[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    run[threadIdx.x] = 0;
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; r++) {
+#pragma unroll
+        for (int w = 0; w < NW; w++) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        int64_t i = base + (int64_t)r * kSortBlock + threadIdx.x;
+        bool valid = i < n;
+        uint64_t key = valid ? in[i] : 0;
+        uint32_t d = valid ? (uint32_t)((key >> shift) & 255u) : 256u + lane;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lanemask_lt());
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t b = run[threadIdx.x];
+#pragma unroll
+            for (int w = 0; w < NW; w++) {
+                uint32_t c = wcnt[w][threadIdx.x];
+                wcnt[w][threadIdx.x] = b;
+                b += c;
+            }
+            run[threadIdx.x] = b;
+        }
+        __syncthreads();
+        if (valid) out[goff[d] + wcnt[warp][d] + rank] = key;
+        __syncthreads();
+    }
+}
+
+// Sorts keys[0..n) in place (tmp: caller scratch of n keys, or null to
+// allocate).  n must be below 2^32.
+inline int radix_sort_u64(uint64_t* keys, int64_t n, const int* shifts, int npass, cudaStream_t s) {
+    if (n <= 1 || npass == 0) return FAST_OK;
+    if (n >= (int64_t)0xFFFFFFFFll) return set_error(FAST_ERR_INVALID, "radix sort: too many keys (%lld)", (long long)n);
+    int64_t nb = ceil_div(n, kSortTile);
+    uint64_t* tmp = nullptr;
+    uint32_t* hist = nullptr;
+    FAST_TRY(dalloc(&tmp, n, s));
+    int rc = dalloc(&hist, 256 * nb, s);
+    uint64_t* a = keys;
+    uint64_t* b = tmp;
+    for (int p = 0; p < npass && rc == FAST_OK; p++) {
+        k_radix_hist<<<(unsigned)nb, kSortBlock, 0, s>>>(a, n, shifts[p], nb, hist);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "radix hist launch"); break; }
+        rc = scan_exclusive<uint32_t>(hist, hist, 256 * nb, (uint32_t*)nullptr, s);
+        if (rc != FAST_OK) break;
+        k_radix_scatter<<<(unsigned)nb, kSortBlock, 0, s>>>(a, b, n, shifts[p], nb, hist);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "radix scatter launch"); break; }
+        uint64_t* t = a; a = b; b = t;
+    }
+    if (rc == FAST_OK && a != keys) {
+        cudaError_t e = cudaMemcpyAsync(keys, a, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) rc = cuda_status(e, "radix copy back", __FILE__, __LINE__);
+    }
+    dfree(tmp, s);
+    dfree(hist, s);
+    return rc;
+}
+
+// Digit shifts covering bits [lo, hi) in 8-bit steps.
+inline int digit_shifts(int lo, int hi, int* out, int max_out) {
+    int n = 0;
+    for (int sft = lo; sft < hi && n < max_out; sft += 8) out[n++] = sft;
+    return n;
+}
+
+inline int bits_for(int64_t maxval) {
+    int b = 0;
+    while (b < 63 && (maxval >> b) > 0) b++;
+    return b;
+}
+
+}  // namespace fast

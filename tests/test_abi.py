@@ -1,0 +1,38 @@
+"""The C ABI library builds for sm_103a, loads, and exports every function
+include/fast.h declares; the binding covers them.  No GPU calls."""
+import ctypes
+import os
+import re
+
+import paper_2102_10768_gb300 as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fast.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fast_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_pipeline():
+    names = declared_functions()
+    for f in ("fast_load_graph", "fast_build_cst", "fast_partition", "fast_match"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol():
+    F.build()
+    lib = ctypes.CDLL(F.library_path())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert sorted(F.exported_symbols()) == declared_functions()
+
+
+def test_config_default_without_gpu():
+    c = F.default_config()
+    assert c.delta_w == 1 << 20 and c.warps_per_block == 8 and c.max_chunks == 1 << 22
+    assert F.lib().fast_last_error() == b""
