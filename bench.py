@@ -4,16 +4,17 @@
 Workload (synthetic stand-in for the paper's LDBC-SNB graphs and query set):
 Chung-Lu graph, exponent 2.1, 1,000,000 vertices, 16,000,000 undirected
 edges, 16 labels Zipf(1.0); 200 connected random-walk queries, 50 each of
-(8 vertices, dense), (8, sparse), (16, dense), (16, sparse).  Every query's
-embedding count is astronomical on this graph (workload estimates 1e20 to
-1e53), so each query is matched on a seeded sample of its CST partition:
-chunks with workload estimate <= delta_w, about `sample_root` sampled runs
-of root candidates and one sampled run per deeper split.  Counts on the
-sampled chunks are exact.
+(8 vertices, dense), (8, sparse), (16, dense), (16, sparse).  On this graph
+the embedding counts are astronomical (workload estimates 1e20 to 1e53), so
+each query enumerates until `limit` embeddings are found and reports
+min(total, limit) -- an exact number, checked against the oracle's own search
+-- under a per-query time budget (queries that spend it are reported
+separately and still add what they enumerated).
 
-One step = for every query: fast_build_cst + fast_partition + fast_match,
-with the data graph resident on the device.  value = embeddings enumerated
-per second; queries/s and per-query latency percentiles ride along.
+One step = for every query: fast_build_cst + fast_partition (Alg. 2,
+delta_w, at most max_chunks chunks) + fast_match, the data graph resident on
+the device.  value = embeddings enumerated per second; queries/s and
+per-query latency percentiles ride along.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -27,8 +28,6 @@ import subprocess
 import sys
 import threading
 import time
-
-import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -45,8 +44,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--queries", type=int, default=50, help="queries per (size, kind) class")
     p.add_argument("--delta-w", type=int, default=1 << 20)
-    p.add_argument("--sample-root", type=float, default=16.0)
-    p.add_argument("--sample-deep", type=float, default=1.0)
+    p.add_argument("--max-chunks", type=int, default=4096)
+    p.add_argument("--limit", type=int, default=1 << 22, help="embeddings per query (exact min(total, limit))")
+    p.add_argument("--budget", type=float, default=2.0, help="seconds per query before it is cut")
     p.add_argument("--seed", type=int, default=2000)
     p.add_argument("--emb-k", type=int, default=1024, help="embeddings copied to the host per query (e2e)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
@@ -62,9 +62,9 @@ def workload(args, rank: int):
             stream0 = 100_000 * rank + 1000 * k + (0 if kind == "dense" else 500)
             qs += synth.walk_queries(n, e, lab, k, args.queries, kind, seed=args.seed, stream0=stream0)
     desc = (f"Chung-Lu gamma=2.1, n=1,000,000, m=16,000,000, 16 Zipf(1.0) labels; "
-            f"{len(qs)} random-walk queries (8/16 vertices x dense/sparse); CST partition sampled: "
-            f"delta_w={args.delta_w}, sample_root={args.sample_root}, sample_deep={args.sample_deep}, "
-            f"seed={args.seed}")
+            f"{len(qs)} random-walk queries (8/16 vertices x dense/sparse); per query: CST, Alg. 2 partition "
+            f"(delta_w={args.delta_w}, max_chunks={args.max_chunks}), match until limit={args.limit} "
+            f"embeddings (count = min(total, limit)), budget {args.budget} s; seed={args.seed}")
     return n, e, lab, qs, desc
 
 
@@ -130,74 +130,60 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def oracle_sample(args, og, qs, budget_s, start=0):
+    """The oracle as it stands on the same per-query task (its own search,
+    stopped at `limit` embeddings), queries in order from `start`, until
+    budget_s of search time."""
+    import oracle
+    emb, t, done = 0, 0.0, 0
+    i = start
+    while t < budget_s:
+        q = qs[i % len(qs)]
+        i += 1
+        t0 = time.perf_counter()
+        r = oracle.match(og, q.labels, q.edges, limit=args.limit, budget=int(5e8))
+        t += time.perf_counter() - t0
+        emb += r["count"]
+        done += 1
+    return emb, t, done, i
+
+
 def cpu_baseline(args, n, e, lab, qs, budget_s):
-    """The oracle as it stands: its own CST and partition restatements, then
-    its enumerator on the sampled chunks, until budget_s of enumeration."""
     import oracle
     og = oracle.Graph(n, e, lab)
-    emb = 0
-    t_enum = 0.0
-    chunks_done = 0
-    queries = 0
-    for q in qs:
-        c = oracle.Cst(og, q.labels, q.edges)
-        chunks = c.partition(args.delta_w, args.sample_root, args.sample_deep, args.seed)
-        queries += 1
-        for (j, pre, a, b, w, i) in chunks:
-            t0 = time.perf_counter()
-            r = oracle.match(og, q.labels, q.edges, allow=c.chunk_allow(j, pre, a, b))
-            t_enum += time.perf_counter() - t0
-            emb += r["count"]
-            chunks_done += 1
-            if t_enum > budget_s:
-                break
-        c.close()
-        if t_enum > budget_s:
-            break
-    cores = os.cpu_count() or 1
-    return {"value": emb / t_enum if t_enum > 0 else 0.0, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{chunks_done} sampled chunks of the first {queries} queries "
-                      f"({emb} embeddings in {t_enum:.1f} s of enumeration, OpenMP over root candidates)"}
+    emb, t, done, _ = oracle_sample(args, og, qs, budget_s)
+    return {"value": emb / t if t > 0 else 0.0, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"first {done} queries of the workload, each searched until {args.limit} embeddings "
+                      f"({emb} embeddings in {t:.1f} s; OpenMP threads over root candidates)"}
 
 
 def run_reference(args):
+    """The oracle arm: the same task on the host cores, a bounded sample of
+    queries per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n, e, lab, qs, desc = workload(args, 0)
     import oracle
+    n, e, lab, qs, desc = workload(args, 0)
     og = oracle.Graph(n, e, lab)
-    c = oracle.Cst(og, qs[0].labels, qs[0].edges)
-    chunks = c.partition(args.delta_w, args.sample_root, args.sample_deep, args.seed)
     per_step = max(1.0, args.cpu_seconds / 2)
-
-    def step(start):
-        emb, t = 0, 0.0
-        i = start
-        while t < per_step:
-            (j, pre, a, b, w, cid) = chunks[i % len(chunks)]
-            t0 = time.perf_counter()
-            emb += oracle.match(og, qs[0].labels, qs[0].edges, allow=c.chunk_allow(j, pre, a, b))["count"]
-            t += time.perf_counter() - t0
-            i += 1
-        return emb, t, i
-
     pos = 0
     for _ in range(args.warmup):
-        _, _, pos = step(pos)
-    tot_e, tot_t = 0, 0.0
+        _, _, _, pos = oracle_sample(args, og, qs, per_step, pos)
+    tot_e, tot_t, tot_q = 0, 0.0, 0
     for _ in range(args.steps):
-        em, t, pos = step(pos)
+        em, t, done, pos = oracle_sample(args, og, qs, per_step, pos)
         tot_e += em
         tot_t += t
+        tot_q += done
     v = tot_e / tot_t if tot_t else 0.0
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": desc, "sample": "chunks of query 0, in order"},
+            "data": "synthetic", "config": {"workload": desc},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
-                             "sample": f"{per_step:.0f} s of oracle enumeration per step over the sampled "
-                                       f"chunks of query 0"},
+                             "sample": f"{per_step:.0f} s of oracle search per step, queries in workload order "
+                                       f"({tot_q} queries timed)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -219,31 +205,21 @@ def run_ours(args):
     n, e, lab, qs, desc = workload(args, rank)
     stream = torch.cuda.current_stream()
     g = F.Graph(n, e, lab)
-    cfg = F.default_config(delta_w=args.delta_w, sample_root=args.sample_root, sample_deep=args.sample_deep,
-                           sample_seed=args.seed, time_budget_s=30.0)
+    cfg = F.default_config(delta_w=args.delta_w, max_chunks=args.max_chunks, limit=args.limit,
+                           time_budget_s=args.budget)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
 
     def one_query(q, k=0, emb=None):
         cst = F.Cst(g, q.labels, q.edges, cfg)
         ch = F.Chunks(cst, cfg)
         r = F.match(cst, ch, k=k, emb_out=emb, cfg=cfg, check=False)
-        if r["status"] not in (F.FAST_OK,):
+        if r["status"] not in (F.FAST_OK, F.FAST_ERR_TIMEOUT):
             raise F.FastError(r["status"], F.lib().fast_last_error().decode())
-        ms = F.last_match_ms()
-        nch = ch.n
-        ch.close(); cst.close()
-        return r["count"], ms, nch
-
-    # algorithmic bytes of the matcher per query (counting pass, untimed)
-    balg = 0
-    nchunks = 0
-    for q in qs:
-        cst = F.Cst(g, q.labels, q.edges, cfg)
-        ch = F.Chunks(cst, cfg)
-        b, _ = F.match_stats(cst, ch, cfg)
-        balg += b
-        nchunks += ch.n
-        ch.close(); cst.close()
+        res = (r["count"], F.last_match_ms(), F.last_match_bytes(), r["status"] == F.FAST_ERR_TIMEOUT,
+               r["written"])
+        ch.close()
+        cst.close()
+        return res
 
     def step():
         flush.zero_()
@@ -251,17 +227,19 @@ def run_ours(args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         lat = []
-        emb, kms = 0, 0.0
+        emb, kms, kbytes, cut = 0, 0.0, 0, 0
         ev0.record(stream)
         for q in qs:
             t0 = time.perf_counter()
-            c, ms, _ = one_query(q)
+            c, ms, b, timed_out, _ = one_query(q)
             lat.append(1000 * (time.perf_counter() - t0))
             emb += c
             kms += ms
+            kbytes += b
+            cut += timed_out
         ev1.record(stream)
         torch.cuda.synchronize()
-        return emb, ev0.elapsed_time(ev1), kms, lat
+        return emb, ev0.elapsed_time(ev1), kms, kbytes, cut, lat
 
     for _ in range(args.warmup):
         step()
@@ -271,20 +249,23 @@ def run_ours(args):
     clocks = Clocks(local)
     clocks.start()
     launches0 = F.kernel_launches()
-    tot_emb, tot_ms, tot_kms, lats = 0, 0.0, 0.0, []
+    tot_emb, tot_ms, tot_kms, tot_bytes, tot_cut, lats = 0, 0.0, 0.0, 0, 0, []
     for _ in range(args.steps):
-        em, ms, kms, lat = step()
+        em, ms, kms, kb, cut, lat = step()
         tot_emb += em
         tot_ms += ms
         tot_kms += kms
+        tot_bytes += kb
+        tot_cut += cut
         lats += lat
     torch.cuda.synchronize()
     launches = F.kernel_launches() - launches0
     if dist:
         dist.barrier()
     ck = clocks.stop()
-    # end to end through the C ABI with host buffers: query arrays in, counts
-    # and the first emb_k embeddings of each query out to pinned host memory
+
+    # end to end through the C ABI with host buffers: query arrays in, the
+    # count and the first emb_k embeddings of each query out to pinned memory
     pinned = {k: torch.empty((args.emb_k, k), dtype=torch.int32, pin_memory=True) for k in (8, 16)}
     h2d = sum(q.labels.nbytes + q.edges.nbytes for q in qs)
     e2e_emb, d2h, t_e2e = 0, 0, 0.0
@@ -293,19 +274,15 @@ def run_ours(args):
         torch.cuda.synchronize()
         ts = time.perf_counter()
         for q in qs:
-            buf = pinned[q.k]
-            cst = F.Cst(g, q.labels, q.edges, cfg)
-            ch = F.Chunks(cst, cfg)
-            r = F.match(cst, ch, k=args.emb_k, emb_out=buf.numpy(), cfg=cfg)
-            e2e_emb += r["count"]
-            d2h += 8 + 4 * q.k * r["written"]
-            ch.close(); cst.close()
+            c, _, _, _, written = one_query(q, k=args.emb_k, emb=pinned[q.k].numpy())
+            e2e_emb += c
+            d2h += 8 + 4 * q.k * written
         t_e2e += time.perf_counter() - ts
 
     steps = max(args.steps, 1)
     t_s = tot_ms / 1000.0
-    stats = torch.tensor([t_s, float(tot_emb), t_e2e, float(e2e_emb)], dtype=torch.float64, device="cuda")
     if dist:
+        stats = torch.tensor([t_s, float(tot_emb), t_e2e, float(e2e_emb)], dtype=torch.float64, device="cuda")
         mx = stats.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
         sm = stats.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
         t_s, tot_all, t_e2e_max, e2e_all = float(mx[0]), float(sm[1]), float(mx[2]), float(sm[3])
@@ -315,7 +292,7 @@ def run_ours(args):
         dist.destroy_process_group()
         return
     peak, peak_kind = peaks()
-    achieved = (balg * steps) / (tot_kms / 1000.0) / 1e9 if tot_kms > 0 else 0.0
+    achieved = tot_bytes / (tot_kms / 1000.0) / 1e9 if tot_kms > 0 else 0.0
     lat_sorted = sorted(lats)
     cpu = cpu_baseline(args, n, e, lab, qs, args.cpu_seconds) if world == 1 else None
     line = {
@@ -323,14 +300,15 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_s / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": desc, "queries_per_step": len(qs), "chunks_per_step": nchunks,
+        "config": {"workload": desc, "queries_per_step": len(qs),
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}, queries per rank"},
         "queries_per_sec": len(qs) * steps * world / t_s,
         "latency_ms": {"p50": lat_sorted[len(lat_sorted) // 2], "p99": lat_sorted[int(0.99 * (len(lat_sorted) - 1))]},
         "embeddings_per_step": tot_emb / steps,
+        "queries_cut_by_budget_per_step": tot_cut / steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "k_match", "algorithmic_bytes_per_step": balg,
+                     "kernel": "k_match", "algorithmic_bytes_per_step": tot_bytes / steps,
                      "kernel_ms_per_step": tot_kms / steps},
         "e2e": {"value": e2e_all / t_e2e_max if t_e2e_max else 0.0, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // steps},

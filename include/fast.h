@@ -53,7 +53,7 @@ extern "C" {
 #define FAST_ERR_TIMEOUT 3   /* fast_match ran past config.time_budget_s; the count is partial */
 #define FAST_ERR_OVERFLOW 4  /* the embedding count reached 2^64 - 1 (saturated) */
 #define FAST_ERR_CUDA 5      /* a CUDA call or kernel launch failed */
-#define FAST_ERR_LIMIT 6     /* fast_partition would exceed config.max_chunks */
+#define FAST_ERR_LIMIT 6     /* reserved */
 
 #define FAST_MAX_QUERY 32    /* query vertices per query (one warp lane each) */
 
@@ -91,10 +91,13 @@ typedef struct {
     int32_t blocks_per_sm;
     /* Wall-clock budget for one fast_match call, seconds (<= 0: none). */
     double time_budget_s;
+    /* Enumeration limit: fast_match stops once `limit` embeddings are found
+     * and reports min(total, limit), exactly (0: enumerate everything). */
+    uint64_t limit;
 } fast_config;
 
-/* Default tunables: delta_w = 2^20, no sampling, max_chunks = 2^22,
- * 8 warps per CTA, 4 CTAs per SM, no time budget. */
+/* Default tunables: delta_w = 2^20, no sampling, max_chunks = 2^16,
+ * 8 warps per CTA, 4 CTAs per SM, no time budget, no limit. */
 void fast_config_default(fast_config* cfg);
 
 /* Thread-local message for the last failing call ("" if none). */
@@ -194,11 +197,14 @@ void fast_free_cst(fast_cst* c);
  * where L_j is C(root) when j = 0 and otherwise the tree list, towards
  * position j, of the candidate at position j's parent position.  Runs are
  * even contiguous slices; a run with W' <= delta_w is a chunk (W' = 0 runs
- * hold no embedding and are dropped); a run of one candidate moves on to the
- * next position; longer runs split again.  With sampling off the chunks are
- * disjoint and cover every embedding.  Level-synchronous on the device; the
- * host reads one queue size per level.
- * Errors: FAST_ERR_LIMIT when more than cfg->max_chunks chunks arise.
+ * hold no embedding and are dropped); a run of one candidate joins the fixed
+ * prefix and moves on to the next position -- unless it repeats a fixed
+ * candidate or lacks a CST edge to a fixed non-tree neighbour, in which case
+ * it holds no embedding and is dropped; longer runs split again.  Runs are
+ * processed level by level; if a level would bring the chunk count above
+ * cfg->max_chunks, the runs still pending become chunks as they are (their
+ * W' may exceed delta_w).  With sampling off the chunks are disjoint and
+ * cover every embedding.  The host reads two sizes per level.
  */
 int fast_partition(const fast_cst* c, const fast_config* cfg, void* stream, fast_chunks** out);
 
@@ -258,6 +264,11 @@ int fast_match_stats(const fast_cst* c, const fast_chunks* chunks, const fast_co
  * thread, measured with CUDA events recorded on the launching stream around
  * the kernel (0 if none ran). */
 double fast_last_match_ms(void);
+
+/* Algorithmic bytes of the last fast_match on this host thread: 8 B of
+ * offsets plus 4 B per entry for every list a partial result was extended
+ * from or checked against, and 4 B per candidate of a root run. */
+uint64_t fast_last_match_bytes(void);
 
 /* Kernels launched by the library since the process started (all threads). */
 uint64_t fast_kernel_launches(void);

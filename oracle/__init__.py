@@ -55,7 +55,9 @@ def _L():
         lib.oracle_graph_nadj.restype = i64
         lib.oracle_graph_csr.argtypes = [vp, vp, vp]
         lib.oracle_match.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp, vp, vp,
-                                     i64, vp, vp, vp, vp, i64, ctypes.c_int]
+                                     i64, vp, vp, vp, vp, i64, ctypes.c_int, u64]
+        lib.oracle_check_embeddings.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, i64, vp]
+        lib.oracle_check_embeddings.restype = i64
         lib.oracle_cst_build.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp]
         lib.oracle_cst_build.restype = vp
         lib.oracle_cst_free.argtypes = [vp]
@@ -124,10 +126,12 @@ def _qarrays(qlabels, qedges):
 
 
 def match(g: Graph, qlabels, qedges, order=None, par=None, allow=None, max_emb: int = 0,
-          budget: int = 0, threads: int = 0, want_depth: bool = False, want_balg: bool = False):
+          budget: int = 0, threads: int = 0, want_depth: bool = False, want_balg: bool = False,
+          limit: int = 0):
     """Enumerate embeddings of q in G by plain backtracking (Definition 1).
 
     allow: optional {query vertex: iterable of allowed data vertices}.
+    limit: stop after `limit` embeddings (count = min(total, limit)).
     Returns a dict: count, complete (False if the per-thread node budget was
     hit), emb (sorted int32[rows][k] indexed by query vertex, at most
     max_emb rows), depth (partial results per number of mapped positions),
@@ -155,7 +159,7 @@ def match(g: Graph, qlabels, qedges, order=None, par=None, allow=None, max_emb: 
     balg = np.zeros(1, dtype=np.float64)
     rc = _L().oracle_match(g._h, k, _p(ql), qe.shape[0], _p(qe), _p(o), _p(pp), _p(aoff), _p(av), _p(aon),
                            max_emb, _p(emb), _p(cnt), _p(depth), _p(balg) if want_balg else None,
-                           budget, threads)
+                           budget, threads, limit)
     if rc < 0:
         raise ValueError(f"oracle_match: invalid input ({rc})")
     count = int(cnt[0])
@@ -165,6 +169,14 @@ def match(g: Graph, qlabels, qedges, order=None, par=None, allow=None, max_emb: 
     return {"count": count, "complete": rc == 0, "emb": rows,
             "depth": depth.astype(np.int64) if want_depth else None,
             "balg": float(balg[0]) if want_balg else None}
+
+
+def invalid_rows(g: Graph, qlabels, qedges, emb) -> int:
+    """How many rows of emb[rows][k] (by query vertex) are not embeddings
+    of q in G by Definition 1."""
+    ql, qe = _qarrays(qlabels, qedges)
+    e = np.ascontiguousarray(np.asarray(emb, dtype=np.int32).reshape(-1, ql.shape[0]))
+    return int(_L().oracle_check_embeddings(g._h, ql.shape[0], _p(ql), qe.shape[0], _p(qe), e.shape[0], _p(e)))
 
 
 def count(g: Graph, qlabels, qedges, **kw) -> int:
@@ -228,9 +240,9 @@ class Cst:
         return float(wf[0]), int(wi[0]), cf[:n], ci[:n]
 
     def partition(self, delta_w: int, c_root: float = 0.0, c_deep: float = 0.0, seed: int = 0,
-                  max_chunks: int = 1 << 20):
+                  max_chunks: int = 1 << 16):
         """Algorithm 2 (readings in cst_ref.c).  Returns a list of chunks
-        (j, prefix global ids tuple, a, b, W', id) in depth-first order."""
+        (j, prefix global ids tuple, a, b, W', id), level by level."""
         k = self.k
         j = np.empty(max_chunks, np.int32); pre = np.empty((max_chunks, k), np.int32)
         a = np.empty(max_chunks, np.int64); b = np.empty(max_chunks, np.int64)

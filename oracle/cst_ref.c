@@ -360,6 +360,16 @@ void oracle_cst_workload(const ocst* c, double* w_f, uint64_t* w_i, int dump_u, 
  *   recurse  a run with W' <= delta_w is a chunk (W' = 0 runs hold no
  *            embedding and are dropped); otherwise a run of one candidate
  *            moves on to the next position, and a longer run is split again.
+ *   fixed    when a run of one candidate v at position j moves on, v joins
+ *            the fixed prefix; if v equals the candidate fixed at an earlier
+ *            position, or lacks a CST edge to the candidate fixed at an
+ *            earlier non-tree neighbour, the part holds no embedding and is
+ *            dropped (the CST validity rule applied to single candidates).
+ *   cap      runs are processed level by level (all runs of one depth of the
+ *            recursion, in order); a level whose chunks plus new parts
+ *            would pass max_chunks turns its live runs into chunks as they
+ *            are (their W' may exceed delta_w), which keeps them disjoint
+ *            and complete.
  *   sample   optional: a run produced by a split into k parts is kept iff
  *            u01(id) < min(1, c/k), c = c_root at the first position and
  *            c_deep later (c <= 0 keeps every run).  id(root) = mix64(seed),
@@ -464,8 +474,22 @@ static uint64_t restricted_w(const pctx* P, int j, const int32_t* prefix, const 
     return W;
 }
 
+/* may candidate v sit at position j after the fixed prefix[0..j-1]? */
+static int prefix_ok(const pctx* P, int j, const int32_t* prefix, int32_t v) {
+    const ocst* c = P->c;
+    int u = c->order[j];
+    for (int p = 0; p < j; p++)
+        if (prefix[p] == v) return 0;
+    for (int e = 0; e < c->nnt; e++) {
+        if (c->nt_to[e] != u) continue;
+        int f = c->nt_from[e];
+        int64_t row = find_sorted(c->cand[f].v, c->cand[f].n, prefix[P->pos[f]]);
+        if (row < 0 || find_sorted(c->nt[e][row].v, c->nt[e][row].n, v) < 0) return 0;
+    }
+    return 1;
+}
+
 static void p_emit(pctx* P, const ochunk* ch) {
-    if (P->nout >= P->max_chunks) { P->overflow = 1; return; }
     if (P->nout == P->cap) {
         P->cap = P->cap ? 2 * P->cap : 64;
         P->out = (ochunk*)realloc(P->out, (size_t)P->cap * sizeof(ochunk));
@@ -473,47 +497,94 @@ static void p_emit(pctx* P, const ochunk* ch) {
     P->out[P->nout++] = *ch;
 }
 
-static void p_process(pctx* P, ochunk ch) {
+/* Move runs of one candidate on to the next position (same W'), checking
+ * the newly fixed candidate.  Returns 0 drop, 1 chunk, 2 split (kk parts). */
+static int p_classify(const pctx* P, ochunk* ch, uint64_t* kk_out) {
     const ocst* c = P->c;
     for (;;) {
-        if (P->overflow) return;
-        if (ch.w == 0) return;
-        if (ch.w <= P->delta_w) { p_emit(P, &ch); return; }
-        int64_t n = ch.b - ch.a;
+        if (ch->w == 0) return 0;
+        if (ch->w <= P->delta_w) return 1;
+        int64_t n = ch->b - ch->a;
         int64_t len;
-        const int32_t* L = chunk_list(P, ch.j, ch.prefix, &len);
+        const int32_t* L = chunk_list(P, ch->j, ch->prefix, &len);
         if (n == 1) {
-            if (ch.j + 1 >= c->k) { p_emit(P, &ch); return; }   /* cannot split further */
-            ch.prefix[ch.j] = L[ch.a];
-            ch.j += 1;
-            const int32_t* L2 = chunk_list(P, ch.j, ch.prefix, &len);
-            (void)L2;
-            ch.a = 0; ch.b = len;
+            if (ch->j + 1 >= c->k) return 1;                 /* cannot split further */
+            if (!prefix_ok(P, ch->j, ch->prefix, L[ch->a])) return 0;
+            ch->prefix[ch->j] = L[ch->a];
+            ch->j += 1;
+            chunk_list(P, ch->j, ch->prefix, &len);
+            ch->a = 0; ch->b = len;
             continue;                                       /* same tree, next position */
         }
-        uint64_t kk = ch.w / P->delta_w + (ch.w % P->delta_w != 0);
+        uint64_t kk = ch->w / P->delta_w + (ch->w % P->delta_w != 0);
         if (kk > (uint64_t)n) kk = (uint64_t)n;
-        double cs = ch.j == 0 ? P->c_root : P->c_deep;
-        double tau = cs <= 0.0 ? 2.0 : (cs / (double)kk < 1.0 ? cs / (double)kk : 2.0);
-        for (uint64_t i = 0; i < kk; i++) {
-            ochunk sub = ch;
-            sub.a = ch.a + (int64_t)((__uint128_t)i * (uint64_t)n / kk);
-            sub.b = ch.a + (int64_t)((__uint128_t)(i + 1) * (uint64_t)n / kk);
-            sub.id = pmix(ch.id + (i + 1) * 0x9E3779B97F4A7C15ull);
-            if (tau <= 1.0 && (double)(sub.id >> 11) * (1.0 / 9007199254740992.0) >= tau) continue;
-            sub.w = restricted_w(P, sub.j, sub.prefix, L + sub.a, sub.b - sub.a);
-            p_process(P, sub);
-            if (P->overflow) return;
-        }
-        return;
+        *kk_out = kk;
+        return 2;
     }
+}
+
+static int p_keep(const pctx* P, int j, uint64_t kk, uint64_t id) {
+    double cs = j == 0 ? P->c_root : P->c_deep;
+    double tau = cs <= 0.0 ? 2.0 : (cs / (double)kk < 1.0 ? cs / (double)kk : 2.0);
+    return !(tau <= 1.0 && (double)(id >> 11) * (1.0 / 9007199254740992.0) >= tau);
+}
+
+/* Level by level: every pending run is moved on / classified; a level whose
+ * chunks and parts would pass max_chunks instead turns its live runs into
+ * chunks as they are. */
+static void p_levels(pctx* P, ochunk root) {
+    ochunk* cur = (ochunk*)malloc(sizeof(ochunk));
+    int64_t ncur = 1;
+    cur[0] = root;
+    while (ncur > 0 && !P->overflow) {
+        int* act = (int*)malloc((size_t)ncur * sizeof(int));
+        uint64_t* kk = (uint64_t*)calloc((size_t)ncur, sizeof(uint64_t));
+        int64_t ne = 0, np = 0, nl = 0;
+        for (int64_t t = 0; t < ncur; t++) {
+            act[t] = p_classify(P, &cur[t], &kk[t]);
+            ne += act[t] == 1;
+            nl += act[t] != 0;
+            if (act[t] == 2)
+                for (uint64_t i = 0; i < kk[t]; i++)
+                    np += p_keep(P, cur[t].j, kk[t], pmix(cur[t].id + (i + 1) * 0x9E3779B97F4A7C15ull));
+        }
+        if (P->nout + ne + np > P->max_chunks) {
+            for (int64_t t = 0; t < ncur; t++) if (act[t] != 0) p_emit(P, &cur[t]);
+            free(act); free(kk);
+            break;
+        }
+        ochunk* nxt = (ochunk*)malloc((size_t)(np > 0 ? np : 1) * sizeof(ochunk));
+        int64_t o = 0;
+        for (int64_t t = 0; t < ncur; t++) {
+            if (act[t] == 1) p_emit(P, &cur[t]);
+            if (act[t] != 2) continue;
+            ochunk* ch = &cur[t];
+            int64_t n = ch->b - ch->a, len;
+            const int32_t* L = chunk_list(P, ch->j, ch->prefix, &len);
+            for (uint64_t i = 0; i < kk[t]; i++) {
+                uint64_t id = pmix(ch->id + (i + 1) * 0x9E3779B97F4A7C15ull);
+                if (!p_keep(P, ch->j, kk[t], id)) continue;
+                ochunk sub = *ch;
+                sub.a = ch->a + (int64_t)((__uint128_t)i * (uint64_t)n / kk[t]);
+                sub.b = ch->a + (int64_t)((__uint128_t)(i + 1) * (uint64_t)n / kk[t]);
+                sub.id = id;
+                sub.w = restricted_w(P, sub.j, sub.prefix, L + sub.a, sub.b - sub.a);
+                nxt[o++] = sub;
+            }
+        }
+        free(act); free(kk); free(cur);
+        cur = nxt;
+        ncur = o;
+    }
+    free(cur);
 }
 
 /*
  * Partition the CST (Algorithm 2 with the readings above).  Chunks are
- * written in depth-first order: j_out[i], prefix_out[i][k] (global ids,
- * entries >= j unused), a_out/b_out, w_out (W'), id_out.  Returns the chunk
- * count, or -1 when more than max_chunks would be produced.
+ * written level by level, in order within a level: j_out[i],
+ * prefix_out[i][k] (global ids, entries >= j unused), a_out/b_out, w_out
+ * (W'), id_out.  Output arrays need room for max_chunks entries.  Returns
+ * the chunk count.
  */
 int64_t oracle_cst_partition(const ocst* c, uint64_t delta_w, double c_root, double c_deep, uint64_t seed,
                              int64_t max_chunks, int32_t* j_out, int32_t* prefix_out, int64_t* a_out,
@@ -528,8 +599,7 @@ int64_t oracle_cst_partition(const ocst* c, uint64_t delta_w, double c_root, dou
     double wf; uint64_t wi;
     oracle_cst_workload(c, &wf, &wi, -1, NULL, NULL);
     root.w = wi;
-    if (root.b > 0) p_process(&P, root);
-    if (P.overflow) { free(P.out); return -1; }
+    if (root.b > 0) p_levels(&P, root);
     for (int64_t i = 0; i < P.nout; i++) {
         j_out[i] = P.out[i].j;
         for (int t = 0; t < c->k; t++) prefix_out[i * c->k + t] = t < P.out[i].j ? P.out[i].prefix[t] : -1;

@@ -133,6 +133,8 @@ typedef struct {
     int32_t* emb;
     int64_t* emb_slot;         /* shared slot counter */
     int64_t budget;
+    uint64_t limit;            /* stop once this many embeddings are found (0: none) */
+    uint64_t* found;           /* shared count towards the limit */
 } sctx;
 
 typedef struct {
@@ -171,8 +173,17 @@ static void emit(const sctx* c, const int32_t* M) {
 static void extend(const sctx* c, sacc* a, int32_t* M, int d, int want_balg) {
     /* M[0..d) maps positions 0..d-1 and is a valid partial embedding */
     a->depth[d - 1]++;
-    if (d == c->k) { a->count++; emit(c, M); return; }
+    if (d == c->k) {
+        if (c->limit) {
+            uint64_t f = __atomic_fetch_add(c->found, 1, __ATOMIC_RELAXED);
+            if (f >= c->limit) { a->over = 2; return; }
+        }
+        a->count++;
+        emit(c, M);
+        return;
+    }
     if (a->over) return;
+    if (c->limit && __atomic_load_n(c->found, __ATOMIC_RELAXED) >= c->limit) { a->over = 2; return; }
     const og* g = c->g;
     int u = c->order[d];
     int32_t x = M[c->par[d]];
@@ -223,6 +234,8 @@ static void extend(const sctx* c, sacc* a, int32_t* M, int d, int want_balg) {
  *        the list it is extended from and for each other earlier neighbour's
  *        list, where a list is N_G(x) restricted to the next query vertex's
  *        label and allowed set.
+ * limit (> 0) stops the search once `limit` embeddings are found; the count
+ * is then exactly min(total, limit) and the rows any such embeddings.
  * Returns 0, 1 when some thread exceeded node_budget (>0) work units (one
  * per extended partial result plus one per neighbour scanned; the budget is
  * per thread; counts are then partial), or a negative code on invalid input.
@@ -231,7 +244,7 @@ int oracle_match(const og* g, int k, const int32_t* ql, int nqe, const int32_t* 
                  const int32_t* order, const int32_t* par,
                  const int64_t* allow_off, const int32_t* allow_v, const uint8_t* allow_on,
                  int64_t max_emb, int32_t* emb_out, uint64_t* count_out, uint64_t* depth_out,
-                 double* balg_out, int64_t node_budget, int nthreads) {
+                 double* balg_out, int64_t node_budget, int nthreads, uint64_t limit) {
     if (k < 1 || k > OMAXK) return -1;
     int A[OMAXK][OMAXK];
     memset(A, 0, sizeof(A));
@@ -278,6 +291,9 @@ int oracle_match(const og* g, int k, const int32_t* ql, int nqe, const int32_t* 
     int64_t slot = 0;
     c.emb_slot = &slot;
     c.budget = node_budget;
+    uint64_t found = 0;
+    c.limit = limit;
+    c.found = &found;
 
     /* root candidates: every vertex carrying the root's label */
     int ur = c.order[0];
@@ -308,16 +324,40 @@ int oracle_match(const og* g, int k, const int32_t* ql, int nqe, const int32_t* 
     }
     uint64_t cnt = 0;
     double balg = want_balg ? 4.0 * (double)nr : 0.0;
-    int over = 0;
+    int over = 0, limited = 0;
     if (depth_out) memset(depth_out, 0, (size_t)k * sizeof(uint64_t));
     for (int t = 0; t < nt; t++) {
         cnt += acc[t].count;
         balg += acc[t].balg;
-        over |= acc[t].over;
+        over |= acc[t].over == 1;
+        limited |= acc[t].over == 2;
         if (depth_out) for (int d = 0; d < k; d++) depth_out[d] += acc[t].depth[d];
     }
     *count_out = cnt;
     if (balg_out) *balg_out = balg;
     free(acc); free(roots);
-    return over ? 1 : 0;
+    if (over && !limited) return 1;
+    return 0;
+}
+
+/*
+ * Check rows of a candidate embedding list against Definition 1 directly:
+ * labels, injectivity and every query edge present in G.  emb[rows][k] is
+ * indexed by query vertex.  Returns the number of rows that fail.
+ */
+int64_t oracle_check_embeddings(const og* g, int k, const int32_t* ql, int nqe, const int32_t* qe,
+                                int64_t rows, const int32_t* emb) {
+    int64_t bad = 0;
+    for (int64_t r = 0; r < rows; r++) {
+        const int32_t* M = emb + r * k;
+        int ok = 1;
+        for (int u = 0; u < k && ok; u++) {
+            if (M[u] < 0 || M[u] >= g->n || g->lab[M[u]] != ql[u]) ok = 0;
+            for (int w = 0; w < u && ok; w++) if (M[w] == M[u]) ok = 0;
+        }
+        for (int e = 0; e < nqe && ok; e++)
+            if (!has_edge(g, M[qe[2 * e]], M[qe[2 * e + 1]])) ok = 0;
+        bad += !ok;
+    }
+    return bad;
 }

@@ -41,7 +41,8 @@ class Config(ctypes.Structure):
     _fields_ = [("delta_w", ctypes.c_uint64), ("sample_root", ctypes.c_double),
                 ("sample_deep", ctypes.c_double), ("sample_seed", ctypes.c_uint64),
                 ("max_chunks", ctypes.c_int64), ("warps_per_block", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("time_budget_s", ctypes.c_double)]
+                ("blocks_per_sm", ctypes.c_int32), ("time_budget_s", ctypes.c_double),
+                ("limit", ctypes.c_uint64)]
 
 
 class QueryDesc(ctypes.Structure):
@@ -78,6 +79,7 @@ _SIGS = {
     "fast_match_ex": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp]),
     "fast_match_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "fast_last_match_ms": (ctypes.c_double, []),
+    "fast_last_match_bytes": (ctypes.c_uint64, []),
     "fast_kernel_launches": (ctypes.c_uint64, []),
 }
 
@@ -338,6 +340,11 @@ def match_stats(cst: Cst, chunks: Chunks | None = None, cfg: Config | None = Non
 def last_match_ms() -> float:
     """Event-timed duration of the last matcher kernel on this thread."""
     return float(lib().fast_last_match_ms())
+
+
+def last_match_bytes() -> int:
+    """Algorithmic bytes of the last fast_match on this thread."""
+    return int(lib().fast_last_match_bytes())
 
 
 def kernel_launches() -> int:

@@ -50,10 +50,11 @@ extern "C" void fast_config_default(fast_config* cfg) {
     cfg->sample_root = 0.0;
     cfg->sample_deep = 0.0;
     cfg->sample_seed = 0;
-    cfg->max_chunks = 1ll << 22;
+    cfg->max_chunks = 1ll << 16;
     cfg->warps_per_block = 8;
     cfg->blocks_per_sm = 4;
     cfg->time_budget_s = 0.0;
+    cfg->limit = 0;
 }
 
 namespace {

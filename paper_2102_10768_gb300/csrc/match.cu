@@ -1,19 +1,27 @@
 // Enumeration over the CST (the semantics of Algorithms 4-8, Sec. V-A).
 //
-// One warp owns one chunk at a time (a persistent grid pulls chunk indices
-// from a global counter) and walks its search space depth first.  Per depth
-// the warp scans the candidate list of the parent position's image 32
-// entries at a time -- the Generator -- and each lane tests its candidate:
+// One warp owns one work item at a time -- a chunk of the partition, or a
+// run another warp gave away -- and walks its search space depth first.  Per
+// depth the warp scans the candidate list of the parent position's image 32
+// entries at a time (the Generator) and each lane tests its candidate:
 //   EdgeValidator    binary search of the candidate in the CST list of every
 //                    earlier non-tree neighbour's image;
 //   VisitedValidator the candidate's data vertex against the images of the
 //                    earlier positions with the same label (distinct labels
 //                    cannot collide);
-// a ballot keeps the survivors -- the Synchronizer -- which are buffered in
-// shared memory and expanded one by one, or counted (and optionally written
-// out) at the last position.  The per-depth scan state lives in registers of
-// the lane whose index is the depth (depth <= 31), so no per-depth array is
-// indexed dynamically.
+// a ballot keeps the survivors (the Synchronizer), which are buffered in
+// shared memory and expanded one by one, or counted -- and optionally written
+// out -- at the last position.  The per-depth scan state lives in registers
+// of the lane whose index is the depth (depth <= 31), so no per-depth array
+// is indexed dynamically.
+//
+// Load balance: a persistent grid first drains the static chunk list, then a
+// global queue of donated runs.  A warp that finds both empty counts itself
+// idle; a busy warp that sees idle warps gives away the second half of the
+// unscanned list at its shallowest depth with at least two entries left --
+// a run of a list with a fixed prefix, i.e. again a chunk.  An outstanding-
+// work counter ends the launch.  Every wait is bounded and reports a status.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -25,6 +33,7 @@ using namespace fast;
 namespace {
 
 thread_local double g_last_match_ms = 0.0;
+thread_local uint64_t g_last_match_bytes = 0;
 
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -54,18 +63,30 @@ struct MatchPlan {
     const uint32_t* n_idx[kMaxNT];
 };
 
-enum : int { kStatusTimeout = 1, kStatusOverflow = 2 };
+enum : int { kStatusTimeout = 1, kStatusOverflow = 2, kStatusLimit = 4, kStatusStall = 8 };
+constexpr uint32_t kDonated = 1;
+constexpr unsigned long long kStallNs = 60ull * 1000 * 1000 * 1000;   // a claimed slot never published
+constexpr unsigned long long kIdleNs = 5ull * 1000 * 1000 * 1000;     // an idle warp gives up waiting
 
 struct MatchOut {
     unsigned long long* next_chunk;
     unsigned long long* total;
     unsigned long long* emb_slot;
     int* status;
-    uint64_t* chunk_counts;           // nullable
+    uint64_t* chunk_counts;           // nullable (static chunks; no donation then)
     uint32_t* emb;                    // nullable
-    uint64_t emb_cap;
-    unsigned long long* stats;        // nullable: [k+1]
+    uint64_t emb_cap;                 // rows that may be written
+    unsigned long long* stats;        // nullable: [k] partial results per depth
+    unsigned long long* bytes;        // algorithmic bytes read
     const unsigned long long* deadline;  // device word: %globaltimer limit, 0 = none
+    uint64_t limit;                   // 0 = enumerate everything
+    Chunk* dq;                        // donated runs
+    uint32_t* dq_ready;
+    uint64_t dq_cap;                  // 0 = no donation
+    unsigned long long* dq_head;
+    unsigned long long* dq_tail;
+    unsigned long long* outstanding;  // work items not yet finished
+    unsigned int* idle;               // warps waiting for work
 };
 
 __global__ void k_set_deadline(unsigned long long* d, unsigned long long budget_ns) {
@@ -81,6 +102,62 @@ __device__ __forceinline__ bool bsearch_u32(const uint32_t* __restrict__ a, int6
     return lo < end && __ldg(a + lo) == x;
 }
 
+__device__ __forceinline__ int vload(const int* p) { return *(volatile const int*)p; }
+__device__ __forceinline__ unsigned long long vload(const unsigned long long* p) {
+    return *(volatile const unsigned long long*)p;
+}
+
+// lane 0: add a local count to the total; flag the limit once it is reached
+__device__ __forceinline__ void flush_count(const MatchOut& O, unsigned long long& local) {
+    if (!local) return;
+    unsigned long long old = atomicAdd(O.total, local);
+    if (old + local < old) atomicOr(O.status, kStatusOverflow);
+    if (O.limit && old + local >= O.limit) atomicOr(O.status, kStatusLimit);
+    local = 0;
+}
+
+// lane 0: obtain the next work item.  kind 1 = static chunk, 2 = donated run,
+// 0 = nothing left (or stop requested).
+__device__ int acquire(const MatchOut& O, int64_t nchunks, unsigned long long deadline, unsigned long long* idx) {
+    bool was_idle = false;
+    int kind = 0;
+    unsigned long long t_idle = 0;
+    for (;;) {
+        if (vload(O.status) & (kStatusTimeout | kStatusLimit | kStatusStall)) break;
+        unsigned long long now = global_timer_ns();
+        if (deadline && now > deadline) { atomicOr(O.status, kStatusTimeout); break; }
+        if (vload(O.next_chunk) < (unsigned long long)nchunks) {
+            unsigned long long i = atomicAdd(O.next_chunk, 1ull);
+            if (i < (unsigned long long)nchunks) { *idx = i; kind = 1; break; }
+        }
+        if (O.dq_cap) {
+            unsigned long long h = vload(O.dq_head), t = vload(O.dq_tail);
+            if (t > O.dq_cap) t = O.dq_cap;
+            if (h < t) {
+                if (atomicCAS(O.dq_head, h, h + 1) == h) {
+                    unsigned long long w0 = global_timer_ns();
+                    bool ready = true;
+                    while (!*(volatile uint32_t*)&O.dq_ready[h]) {
+                        if (global_timer_ns() - w0 > kStallNs) { atomicOr(O.status, kStatusStall); ready = false; break; }
+                        __nanosleep(32);
+                    }
+                    if (!ready) break;
+                    *idx = h;
+                    kind = 2;
+                    break;
+                }
+                continue;
+            }
+        }
+        if (vload(O.outstanding) == 0) break;
+        if (!was_idle) { atomicAdd(O.idle, 1u); was_idle = true; t_idle = now; }
+        else if (now - t_idle > kIdleNs) break;   // the warps still busy finish (and drain) the rest
+        __nanosleep(200);
+    }
+    if (was_idle) atomicSub(O.idle, 1u);
+    return kind;
+}
+
 template <bool STATS, bool EMIT>
 __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* __restrict__ chunks, int64_t nchunks,
                                                MatchOut O) {
@@ -93,31 +170,33 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
     const int k = P.k;
     unsigned long long iter = 0;
     const unsigned long long deadline = *O.deadline;
+    unsigned long long bytes = 0;          // lane 0
+    unsigned long long local = 0;          // lane 0: count not yet flushed
 
     for (;;) {
         unsigned long long ci = 0;
-        if (lane == 0) {
-            ci = (*(volatile int*)O.status & kStatusTimeout) ? (unsigned long long)nchunks : atomicAdd(O.next_chunk, 1ull);
-            if (deadline && global_timer_ns() > deadline) { atomicOr(O.status, kStatusTimeout); ci = nchunks; }
-        }
+        int kind = 0;
+        if (lane == 0) kind = acquire(O, nchunks, deadline, &ci);
+        kind = __shfl_sync(0xffffffffu, kind, 0);
         ci = __shfl_sync(0xffffffffu, ci, 0);
-        if (ci >= (unsigned long long)nchunks) break;
-        const Chunk& ch = chunks[ci];
+        if (kind == 0) break;
+        const Chunk& ch = kind == 1 ? chunks[ci] : O.dq[ci];
         const int j = ch.j;
+        const bool donated = (ch.pad & kDonated) != 0;
         uint32_t m_reg = lane < j ? ch.prefix[lane] : 0u;      // lane p: candidate index of position p
         int32_t g_reg = -1;                                    // lane p: data vertex of position p
         if (lane < j) g_reg = P.cand[lane][m_reg];
         sm[lane] = m_reg;
         sg[lane] = g_reg;
         __syncwarp();
-        unsigned long long bytes = 0;
         // ---- the prefix must itself be a partial embedding (non-tree edges, injectivity)
         bool ok_prefix = true;
+        unsigned long long pb = 0;
         if (lane < j && lane > 0) {
             for (int e = P.nt_begin[lane]; e < P.nt_begin[lane + 1]; e++) {
                 uint32_t mf = sm[P.nt_from[e]];
                 int64_t lo = P.n_off[e][mf], hi = P.n_off[e][mf + 1];
-                if (STATS) bytes += 8 + 4 * (hi - lo);
+                pb += 8 + 4 * (hi - lo);
                 if (!bsearch_u32(P.n_idx[e], lo, hi, m_reg)) ok_prefix = false;
             }
             uint32_t sl = P.same_lab[lane];
@@ -127,25 +206,23 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
                 if (sg[p] == g_reg) ok_prefix = false;
             }
         }
-        if (STATS) {
-            for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
-        }
-        unsigned long long count = 0;
+        for (int o = 16; o > 0; o >>= 1) pb += __shfl_xor_sync(0xffffffffu, pb, o);
+        if (lane == 0 && !donated) bytes += pb;
+        unsigned long long ccount = 0;         // lane 0: this item's count
         if (__all_sync(0xffffffffu, ok_prefix)) {
-            // ---- depth j: the chunk's run of L_j
+            // ---- depth j: the item's run of L_j
             int d = j;
-            int64_t seg_next = 0, seg_end = 0;     // lane d: scan position in depth d's list
-            uint32_t bcnt = 0, bcur = 0;           // lane d: buffered survivors of depth d
+            int64_t seg_next = 0, seg_end = 0, seg_base = 0;   // lane d: depth d's list scan
+            uint32_t bcnt = 0, bcur = 0;                        // lane d: buffered survivors
             {
-                int64_t lo, hi;
-                if (j == 0) { lo = ch.a; hi = ch.b; }
-                else {
+                int64_t base = 0;
+                if (j > 0) {
                     uint32_t mp = __shfl_sync(0xffffffffu, m_reg, P.par[j]);
-                    int64_t base = P.t_off[j][mp];
-                    lo = base + ch.a; hi = base + ch.b;
+                    base = P.t_off[j][mp];
                 }
-                if (lane == d) { seg_next = lo; seg_end = hi; }
-                if (STATS && lane == 0) {
+                int64_t lo = base + ch.a, hi = base + ch.b;
+                if (lane == d) { seg_next = lo; seg_end = hi; seg_base = base; }
+                if (lane == 0 && !donated) {
                     if (j == 0) bytes += 4 * (hi - lo);
                     else {
                         bytes += 8 + 4 * (hi - lo);
@@ -157,27 +234,67 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
                 }
             }
             for (;;) {
-                if (deadline && ((++iter & 1023) == 0)) {
+                ++iter;
+                if ((iter & 255) == 0) {
                     int stop = 0;
                     if (lane == 0) {
-                        if (global_timer_ns() > deadline) atomicOr(O.status, kStatusTimeout);
-                        stop = *(volatile int*)O.status & kStatusTimeout;
+                        flush_count(O, local);
+                        if (deadline && global_timer_ns() > deadline) atomicOr(O.status, kStatusTimeout);
+                        stop = vload(O.status) & (kStatusTimeout | kStatusLimit | kStatusStall);
                     }
                     if (__shfl_sync(0xffffffffu, stop, 0)) break;
+                }
+                if (O.dq_cap && (iter & 63) == 0) {
+                    // give work away when some warp is idle
+                    unsigned int idl = 0;
+                    if (lane == 0) idl = *(volatile unsigned int*)O.idle;
+                    idl = __shfl_sync(0xffffffffu, idl, 0);
+                    if (idl) {
+                        bool can = lane >= j && lane <= d && (seg_end - seg_next) >= 2;
+                        uint32_t cm = __ballot_sync(0xffffffffu, can);
+                        if (cm) {
+                            int dd = __ffs(cm) - 1;
+                            unsigned long long slot = 0;
+                            if (lane == 0) slot = atomicAdd(O.dq_tail, 1ull);
+                            slot = __shfl_sync(0xffffffffu, slot, 0);
+                            if (slot < O.dq_cap) {
+                                int64_t sn_ = __shfl_sync(0xffffffffu, seg_next, dd);
+                                int64_t se_ = __shfl_sync(0xffffffffu, seg_end, dd);
+                                int64_t sb_ = __shfl_sync(0xffffffffu, seg_base, dd);
+                                int64_t mid = sn_ + (se_ - sn_) / 2;
+                                Chunk* dst = &O.dq[slot];
+                                if (lane < kMaxK) dst->prefix[lane] = lane < dd ? sm[lane] : 0u;
+                                if (lane == 0) {
+                                    atomicAdd(O.outstanding, 1ull);
+                                    dst->j = dd;
+                                    dst->a = (uint32_t)(mid - sb_);
+                                    dst->b = (uint32_t)(se_ - sb_);
+                                    dst->pad = kDonated;
+                                    dst->w = 0;
+                                    dst->id = 0;
+                                }
+                                __syncwarp();
+                                if (lane == 0) {
+                                    __threadfence();
+                                    atomicExch(&O.dq_ready[slot], 1u);
+                                }
+                                if (lane == dd) seg_end = mid;
+                            }
+                        }
+                    }
                 }
                 uint32_t cur_d = __shfl_sync(0xffffffffu, bcur, d);
                 uint32_t cnt_d = __shfl_sync(0xffffffffu, bcnt, d);
                 if (cur_d < cnt_d) {
                     // expand the next buffered survivor of depth d
                     uint32_t v = sbuf[d * 32 + cur_d];
-                    if (lane == d) { bcur++; m_reg = v; g_reg = P.cand[d][v]; }
-                    if (lane == d) { sm[d] = v; sg[d] = g_reg; }
+                    if (lane == d) { bcur++; m_reg = v; g_reg = P.cand[d][v]; sm[d] = v; sg[d] = g_reg; }
                     d++;
                     uint32_t mp = __shfl_sync(0xffffffffu, m_reg, P.par[d]);
                     int64_t lo = P.t_off[d][mp], hi = P.t_off[d][mp + 1];
-                    if (lane == d) { seg_next = lo; seg_end = hi; bcnt = 0; bcur = 0; }
+                    if (lane == d) { seg_next = lo; seg_end = hi; seg_base = lo; bcnt = 0; bcur = 0; }
                     __syncwarp();
-                    if (STATS && lane == 0) {
+                    if (lane == 0) {
                         bytes += 8 + 4 * (hi - lo);
                         for (int e = P.nt_begin[d]; e < P.nt_begin[d + 1]; e++) {
                             uint32_t mf = sm[P.nt_from[e]];
@@ -215,9 +332,9 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
                     // Synchronizer
                     uint32_t mask = __ballot_sync(0xffffffffu, ok);
                     if (lane == d) seg_next = sn + 32;
-                    if (STATS && lane == 0) atomicAdd(&O.stats[1 + d], (unsigned long long)__popc(mask));
+                    if (STATS && lane == 0) atomicAdd(&O.stats[d], (unsigned long long)__popc(mask));
                     if (d == k - 1) {
-                        count += __popc(mask);
+                        if (lane == 0) { local += __popc(mask); ccount += __popc(mask); }
                         if (EMIT && mask) {
                             unsigned long long base = 0;
                             if (lane == 0) base = atomicAdd(O.emb_slot, (unsigned long long)__popc(mask));
@@ -243,14 +360,15 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
             }
         }
         if (lane == 0) {
-            if (O.chunk_counts) O.chunk_counts[ci] = count;
-            if (count) {
-                unsigned long long old = atomicAdd(O.total, count);
-                if (old + count < old) atomicOr(O.status, kStatusOverflow);
-            }
-            if (STATS) atomicAdd(&O.stats[0], bytes);
+            flush_count(O, local);
+            if (O.chunk_counts && kind == 1) O.chunk_counts[ci] = ccount;
+            atomicAdd(O.outstanding, ~0ull);   // -1
         }
         __syncwarp();
+    }
+    if (lane == 0) {
+        flush_count(O, local);
+        if (bytes) atomicAdd(O.bytes, bytes);
     }
 }
 
@@ -287,6 +405,11 @@ MatchPlan make_plan(const fast_cst* c) {
 
 size_t smem_bytes(int warps) { return (size_t)warps * (kMaxK * 32 + 2 * kMaxK) * sizeof(uint32_t); }
 
+// counter block layout (unsigned long long words)
+enum { kNext = 0, kTotal, kSlot, kStatus, kBytes, kHead, kTail, kOut, kIdle, kDeadline, kStats,
+       kCtrWords = kStats + kMaxK + 1 };
+constexpr uint64_t kQueueCap = 1 << 16;
+
 int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* cfg_in, uint64_t kemb, uint32_t* emb_out,
               uint64_t* count_out, uint64_t* written_out, uint64_t* chunk_counts, uint64_t* stats_out,
               cudaStream_t s) {
@@ -319,36 +442,48 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
         if (e != cudaSuccess) { dfree(own, s); return cuda_status(e, "fast_match chunk", __FILE__, __LINE__); }
         dchunks = own; nchunks = (int64_t)parts;
     }
-    // counters: [0] next chunk, [1] total, [2] embedding slot, [3] status,
-    // [4 .. 4+k] stats, [4+kMaxK+1] deadline
+    const bool donate = chunk_counts == nullptr;
     unsigned long long* ctr = nullptr;
-    const int nctr = 4 + kMaxK + 2;
-    rc = dalloc(&ctr, nctr, s);
+    Chunk* dq = nullptr;
+    uint32_t* dq_ready = nullptr;
+    rc = dalloc(&ctr, kCtrWords, s);
+    if (rc == FAST_OK && donate) rc = dalloc(&dq, kQueueCap, s);
+    if (rc == FAST_OK && donate) rc = dalloc(&dq_ready, kQueueCap, s);
     uint32_t* emb_dev = emb_out;
     uint32_t* staged = nullptr;
     bool timed = false;
+    uint64_t emb_cap = kemb;
+    if (cfg.limit > 0 && cfg.limit < emb_cap) emb_cap = cfg.limit;
     if (rc == FAST_OK && kemb > 0) {
         cudaPointerAttributes at;
         cudaError_t e = cudaPointerGetAttributes(&at, emb_out);
         cudaGetLastError();
         bool device_ok = e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
         if (!device_ok) {
-            rc = dalloc(&staged, kemb * (uint64_t)c->k, s);
+            rc = dalloc(&staged, emb_cap * (uint64_t)c->k, s);
             emb_dev = staged;
         }
     }
     if (rc == FAST_OK) {
-        cudaMemsetAsync(ctr, 0, nctr * sizeof(unsigned long long), s);
+        cudaMemsetAsync(ctr, 0, kCtrWords * sizeof(unsigned long long), s);
+        unsigned long long out0 = (unsigned long long)nchunks;
+        cudaMemcpyAsync(ctr + kOut, &out0, sizeof(out0), cudaMemcpyHostToDevice, s);
+        if (donate) cudaMemsetAsync(dq_ready, 0, kQueueCap * sizeof(uint32_t), s);
         MatchOut O;
-        O.next_chunk = ctr; O.total = ctr + 1; O.emb_slot = ctr + 2; O.status = (int*)(ctr + 3);
-        O.chunk_counts = chunk_counts; O.emb = emb_dev; O.emb_cap = kemb;
-        O.stats = stats_out ? ctr + 4 : nullptr;
-        O.deadline = ctr + 4 + kMaxK + 1;
+        O.next_chunk = ctr + kNext; O.total = ctr + kTotal; O.emb_slot = ctr + kSlot; O.status = (int*)(ctr + kStatus);
+        O.chunk_counts = chunk_counts; O.emb = emb_dev; O.emb_cap = emb_cap;
+        O.stats = stats_out ? ctr + kStats : nullptr;
+        O.bytes = ctr + kBytes;
+        O.deadline = ctr + kDeadline;
+        O.limit = cfg.limit;
+        O.dq = dq; O.dq_ready = dq_ready; O.dq_cap = donate ? kQueueCap : 0;
+        O.dq_head = ctr + kHead; O.dq_tail = ctr + kTail; O.outstanding = ctr + kOut;
+        O.idle = (unsigned int*)(ctr + kIdle);
         unsigned long long budget_ns = cfg.time_budget_s > 0 ? (unsigned long long)(cfg.time_budget_s * 1e9) : 0ull;
-        if (budget_ns) { k_set_deadline<<<1, 1, 0, s>>>(ctr + 4 + kMaxK + 1, budget_ns); note_launch(); }
+        if (budget_ns) { k_set_deadline<<<1, 1, 0, s>>>(ctr + kDeadline, budget_ns); note_launch(); }
         if (nchunks > 0) {
             int64_t grid = (int64_t)num_sms() * bps;
-            grid = std::max<int64_t>(1, std::min<int64_t>(grid, ceil_div(nchunks, warps)));
+            if (!donate) grid = std::max<int64_t>(1, std::min<int64_t>(grid, ceil_div(nchunks, warps)));
             size_t sh = smem_bytes(warps);
             EventPair& ev = match_events();
             if (ev.ok) cudaEventRecord(ev.a, s);
@@ -361,31 +496,38 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
             timed = ev.ok;
         }
     }
-    unsigned long long h[nctr];
+    unsigned long long h[kCtrWords];
     memset(h, 0, sizeof(h));
     if (rc == FAST_OK) {
         cudaError_t e = cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_status(e, "fast_match", __FILE__, __LINE__);
         g_last_match_ms = 0.0;
+        g_last_match_bytes = h[kBytes];
         if (rc == FAST_OK && timed) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, match_events().a, match_events().b) == cudaSuccess) g_last_match_ms = ms;
             else cudaGetLastError();
         }
     }
+    uint64_t written = std::min<uint64_t>(emb_cap, h[kSlot]);
     if (rc == FAST_OK && staged) {
-        uint64_t rows = std::min<uint64_t>(kemb, h[2]);
-        cudaError_t e = rows ? cudaMemcpyAsync(emb_out, staged, rows * c->k * sizeof(uint32_t), cudaMemcpyDeviceToHost, s) : cudaSuccess;
+        cudaError_t e = written ? cudaMemcpyAsync(emb_out, staged, written * c->k * sizeof(uint32_t), cudaMemcpyDeviceToHost, s) : cudaSuccess;
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_status(e, "fast_match embedding readback", __FILE__, __LINE__);
     }
-    dfree(ctr, s); dfree(own, s); dfree(staged, s);
+    dfree(ctr, s); dfree(own, s); dfree(staged, s); dfree(dq, s); dfree(dq_ready, s);
     if (rc != FAST_OK) return rc;
-    if (count_out) *count_out = h[1];
-    if (written_out) *written_out = std::min<uint64_t>(kemb, h[2]);
-    if (stats_out) for (int i = 0; i <= c->k; i++) stats_out[i] = h[4 + i];
-    int st = (int)h[3];
+    uint64_t total = h[kTotal];
+    if (cfg.limit > 0 && total > cfg.limit) total = cfg.limit;
+    if (count_out) *count_out = total;
+    if (written_out) *written_out = written;
+    if (stats_out) {
+        stats_out[0] = h[kBytes];
+        for (int i = 0; i < c->k; i++) stats_out[1 + i] = h[kStats + i];
+    }
+    int st = (int)h[kStatus];
+    if (st & kStatusStall) return set_error(FAST_ERR_CUDA, "fast_match: a donated run was never published");
     if (st & kStatusTimeout) return set_error(FAST_ERR_TIMEOUT, "fast_match: time budget of %.3f s spent", cfg.time_budget_s);
     if (st & kStatusOverflow) return set_error(FAST_ERR_OVERFLOW, "fast_match: count reached 2^64");
     return FAST_OK;
@@ -412,3 +554,5 @@ extern "C" int fast_match_stats(const fast_cst* c, const fast_chunks* chunks, co
 }
 
 extern "C" double fast_last_match_ms(void) { return g_last_match_ms; }
+
+extern "C" uint64_t fast_last_match_bytes(void) { return g_last_match_bytes; }

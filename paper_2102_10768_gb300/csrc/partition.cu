@@ -24,13 +24,45 @@ struct PartPlan {
     int k;
     int par_pos[kMaxK];            // position -> parent position (-1 at 0)
     uint32_t child_mask[kMaxK];    // position -> bitmask of child positions
+    uint32_t same_lab[kMaxK];      // earlier positions with the same label
+    const int32_t* cand[kMaxK];    // by position
     const int64_t* t_off[kMaxK];   // by position (tree edge into it)
     const uint32_t* t_idx[kMaxK];
     const uint64_t* cval[kMaxK];   // by position
     const uint64_t* ssum[kMaxK];   // by position: per row of C(parent position)
+    int nt_begin[kMaxK + 1];       // non-tree edges into position i
+    int nt_from[kMaxNT];
+    const int64_t* n_off[kMaxNT];
+    const uint32_t* n_idx[kMaxNT];
     uint64_t delta_w;
     double c_root, c_deep;
 };
+
+__device__ __forceinline__ bool in_list(const uint32_t* a, int64_t lo, int64_t hi, uint32_t x) {
+    int64_t end = hi;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo < end && a[lo] == x;
+}
+
+// may candidate v (index into C of position j) join the fixed prefix?
+__device__ bool prefix_ok(const PartPlan& P, const Chunk& c, uint32_t v) {
+    int j = c.j;
+    int32_t g = P.cand[j][v];
+    uint32_t sl = P.same_lab[j];
+    while (sl) {
+        int p = __ffs(sl) - 1;
+        sl &= sl - 1;
+        if (P.cand[p][c.prefix[p]] == g) return false;
+    }
+    for (int e = P.nt_begin[j]; e < P.nt_begin[j + 1]; e++) {
+        uint32_t mf = c.prefix[P.nt_from[e]];
+        if (!in_list(P.n_idx[e], P.n_off[e][mf], P.n_off[e][mf + 1], v)) return false;
+    }
+    return true;
+}
 
 struct PartRec {
     uint32_t item;
@@ -70,7 +102,9 @@ __device__ int classify(const PartPlan& P, Chunk& c, uint32_t root_n, uint64_t* 
         uint32_t n = c.b - c.a;
         if (n == 1) {
             if (c.j + 1 >= P.k) return 1;
-            c.prefix[c.j] = list_at(P, c, c.a);
+            uint32_t v = list_at(P, c, c.a);
+            if (!prefix_ok(P, c, v)) return 0;
+            c.prefix[c.j] = v;
             c.j += 1;
             c.a = 0;
             c.b = list_len(P, c, root_n);
@@ -85,13 +119,14 @@ __device__ int classify(const PartPlan& P, Chunk& c, uint32_t root_n, uint64_t* 
 
 // one thread per pending item: classify and count the kept parts
 __global__ void k_part_count(const PartPlan P, Chunk* __restrict__ items, int64_t nitems, uint32_t root_n,
-                             int64_t* __restrict__ nparts, int64_t* __restrict__ nemit) {
+                             int64_t* __restrict__ nparts, int64_t* __restrict__ nemit, int64_t* __restrict__ nlive) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nitems) return;
     Chunk c = items[t];
     uint64_t kk = 0;
     int act = classify(P, c, root_n, &kk);
     items[t] = c;
+    nlive[t] = act != 0 ? 1 : 0;
     int64_t np = 0;
     if (act == 2) {
         for (uint64_t i = 0; i < kk; i++)
@@ -144,6 +179,14 @@ __global__ void k_part_write(const PartPlan P, const Chunk* __restrict__ items, 
     }
 }
 
+// cap reached: every live pending item becomes a chunk as it is
+__global__ void k_part_emit_live(const Chunk* __restrict__ items, int64_t nitems, const int64_t* __restrict__ live_off,
+                                 Chunk* __restrict__ emitted) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nitems) return;
+    if (live_off[t + 1] != live_off[t]) emitted[live_off[t]] = items[t];
+}
+
 // one warp per part: W' = F * (saturating sum of c over the run)
 __global__ void k_part_sum(const PartPlan P, const Chunk* __restrict__ items, const PartRec* __restrict__ parts,
                            int64_t nparts, Chunk* __restrict__ next) {
@@ -189,9 +232,25 @@ PartPlan make_plan(const fast_cst* c, const fast_config* cfg) {
         P.t_idx[i] = c->t_idx[u];
         P.cval[i] = c->cval[u];
         P.ssum[i] = c->ssum[u];
+        P.cand[i] = c->cand[u];
         P.child_mask[i] = 0;
+        P.same_lab[i] = 0;
+        for (int p = 0; p < i; p++)
+            if (c->qlabel[c->order[p]] == c->qlabel[u]) P.same_lab[i] |= 1u << p;
     }
     for (int i = 1; i < c->k; i++) P.child_mask[P.par_pos[i]] |= 1u << i;
+    int e = 0;
+    for (int i = 0; i < c->k; i++) {
+        P.nt_begin[i] = e;
+        for (int t = 0; t < c->nnt; t++) {
+            if (c->pos[c->nt_to[t]] != i) continue;
+            P.nt_from[e] = c->pos[c->nt_from[t]];
+            P.n_off[e] = c->n_off[t];
+            P.n_idx[e] = c->n_idx[t];
+            e++;
+        }
+    }
+    P.nt_begin[c->k] = e;
     P.delta_w = cfg->delta_w ? cfg->delta_w : 1;
     P.c_root = cfg->sample_root;
     P.c_deep = cfg->sample_deep;
@@ -214,7 +273,7 @@ int partition(const fast_cst* c, const fast_config* cfg_in, cudaStream_t s, fast
     int64_t* cnt = nullptr;
     PartRec* parts = nullptr;
     Chunk* next = nullptr;
-    const int64_t cap = cfg.max_chunks > 0 ? cfg.max_chunks : (1ll << 22);
+    const int64_t cap = cfg.max_chunks > 0 ? cfg.max_chunks : (1ll << 16);
 
     if (root_n > 0 && c->W > 0) {
         Chunk r0;
@@ -228,21 +287,33 @@ int partition(const fast_cst* c, const fast_config* cfg_in, cudaStream_t s, fast
         }
     }
     while (rc == FAST_OK && nitems > 0) {
-        // counts: [0, nitems] part offsets, [nitems+1, 2 nitems+1] emit offsets
-        rc = dalloc(&cnt, 2 * (nitems + 1), s); if (rc) break;
+        // per item: [0, n] part offsets, [n+1, 2n+1] emit offsets, [2n+2, 3n+2] live offsets
+        rc = dalloc(&cnt, 3 * (nitems + 1), s); if (rc) break;
         int64_t* part_off = cnt;
         int64_t* emit_off = cnt + nitems + 1;
-        k_part_count<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(P, items, nitems, root_n, part_off, emit_off);
+        int64_t* live_off = cnt + 2 * (nitems + 1);
+        k_part_count<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(P, items, nitems, root_n, part_off, emit_off, live_off);
         note_launch();
         rc = scan_exclusive<int64_t>(part_off, part_off, nitems, part_off + nitems, s); if (rc) break;
         rc = scan_exclusive<int64_t>(emit_off, emit_off, nitems, emit_off + nitems, s); if (rc) break;
-        int64_t np = 0, ne = 0;
+        rc = scan_exclusive<int64_t>(live_off, live_off, nitems, live_off + nitems, s); if (rc) break;
+        int64_t np = 0, ne = 0, nl = 0;
         cudaError_t e = cudaMemcpyAsync(&np, part_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&ne, emit_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, live_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { rc = cuda_status(e, "partition level sizes", __FILE__, __LINE__); break; }
-        if (total + ne > cap || np > 4 * cap) {
-            rc = set_error(FAST_ERR_LIMIT, "fast_partition: more than max_chunks=%lld chunks", (long long)cap);
+        if (total + ne + np > cap) {
+            // the level would pass max_chunks: pending runs become chunks as they are
+            Chunk* em = nullptr;
+            if (nl) {
+                rc = dalloc(&em, nl, s); if (rc) break;
+                levels.push_back({em, nl});
+                total += nl;
+                k_part_emit_live<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(items, nitems, live_off, em);
+                note_launch();
+            }
+            dfree(cnt, s);
             break;
         }
         Chunk* em = nullptr;

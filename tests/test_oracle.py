@@ -389,3 +389,46 @@ def test_balg_counts_lists_of_extended_partials():
     # extend {0,1}: list of 1 towards c = {2} (8+4); extend {0,3}: {4,5} (8+8)
     assert r["balg"] == 4 + (8 + 8) + (8 + 4) + (8 + 8)
     assert r["depth"].tolist() == [1, 2, 3]
+
+
+# ------------------------------------------------------------------- limit
+
+@pytest.mark.parametrize("seed", range(8))
+def test_limit_gives_min_of_total_and_limit(seed):
+    rng = np.random.default_rng(900 + seed)
+    n = 60
+    edges, labels = random_graph(rng, n, 0.2, 2)
+    ql, qe = random_connected_query(rng, 4, 2, 0.3)
+    g = oracle.Graph(n, edges, labels)
+    full = oracle.match(g, ql, qe, max_emb=1 << 20)
+    allrows = set(map(tuple, full["emb"].tolist()))
+    for L in (1, 7, max(1, full["count"] // 3), full["count"], full["count"] + 5):
+        r = oracle.match(g, ql, qe, limit=L, max_emb=1 << 20)
+        assert r["complete"] and r["count"] == min(full["count"], L)
+        rows = set(map(tuple, r["emb"].tolist()))
+        assert len(rows) == r["count"] and rows <= allrows
+
+
+def test_embedding_checker_rejects_each_kind_of_fault():
+    g = oracle.Graph(4, [[0, 1], [1, 2], [2, 3]], [0, 1, 0, 1])
+    ql, qe = [0, 1, 0], [[0, 1], [1, 2]]
+    assert oracle.invalid_rows(g, ql, qe, [[0, 1, 2], [2, 1, 0], [2, 3, 2]]) == 1   # repeat
+    assert oracle.invalid_rows(g, ql, qe, [[0, 3, 2]]) == 1                          # missing edge
+    assert oracle.invalid_rows(g, ql, qe, [[1, 0, 2]]) == 1                          # labels
+    assert oracle.invalid_rows(g, ql, qe, [[0, 1, 2]]) == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_partition_cap_keeps_chunks_disjoint_and_complete(seed):
+    n, edges, labels, ql, qe = _cst_case(950 + seed)
+    g = oracle.Graph(n, edges, labels)
+    c = oracle.Cst(g, ql, qe)
+    wf, wi, _, _ = c.workload()
+    if wi == 0:
+        return
+    total = oracle.count(g, ql, qe)
+    for cap in (1, 3, 10):
+        chunks = c.partition(max(1, wi // 50), max_chunks=cap)
+        assert len(chunks) <= cap
+        s = sum(oracle.count(g, ql, qe, allow=c.chunk_allow(j, pre, a, b)) for (j, pre, a, b, w, i) in chunks)
+        assert s == total
