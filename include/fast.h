@@ -258,6 +258,39 @@ int fast_match_ex(const fast_cst* c, const fast_chunks* chunks, const fast_confi
 int fast_match_stats(const fast_cst* c, const fast_chunks* chunks, const fast_config* cfg, uint64_t* out,
                      void* stream);
 
+/*
+ * fast_match_noalloc -- fast_match for callers that must not allocate device
+ * memory.  This entry point has no counterpart in the paper; it exists for
+ * embedders whose device memory is already owned by another allocator (a
+ * framework's caching pool that holds the whole GPU), for serving loops that
+ * forbid allocator calls once they are running so that latency and memory
+ * stay fixed, and for code on threads or callbacks where the CUDA allocator
+ * must not be entered.  Every other entry point allocates stream-ordered
+ * scratch; this one allocates nothing -- no cudaMalloc, cudaMallocAsync or
+ * cudaFree, no host staging buffer.
+ *
+ * Scratch: one file-scope device array of fast_match_noalloc_scratch_bytes()
+ * bytes (about 5.9 MB: the counter block, a queue of 4096 donated runs and
+ * up to 32768 root-run descriptors) that every GPU loading the library keeps
+ * until the process exits.  The first call on a device looks up its address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array and leave the last
+ * call's contents in it; each call clears what must start at zero.  Calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * the shared array and must be serialised by the caller.
+ *
+ * Arguments as fast_match_ex (no per-chunk counts), except: emb_out must be
+ * device (or managed) memory when k > 0 -- a host buffer would need staging
+ * -- and, with chunks == NULL, the launch shape may ask for at most 32768
+ * root runs (4 per warp).  Either violation returns FAST_ERR_INVALID with a
+ * message; nothing runs.  The call synchronises `stream`.
+ */
+int fast_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_config* cfg, uint64_t k,
+                       uint32_t* emb_out, uint64_t* count_out, uint64_t* written_out, void* stream);
+
+/* Size in bytes of the static scratch array fast_match_noalloc uses. */
+uint64_t fast_match_noalloc_scratch_bytes(void);
+
 /* ---------------------------------------------------------- measurement */
 
 /* Duration in milliseconds of the last matcher kernel launched by this host

@@ -78,6 +78,8 @@ _SIGS = {
     "fast_match": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp, _vp, _vp]),
     "fast_match_ex": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp]),
     "fast_match_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fast_match_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp]),
+    "fast_match_noalloc_scratch_bytes": (ctypes.c_uint64, []),
     "fast_last_match_ms": (ctypes.c_double, []),
     "fast_last_match_bytes": (ctypes.c_uint64, []),
     "fast_kernel_launches": (ctypes.c_uint64, []),
@@ -327,6 +329,20 @@ def match(cst: Cst, chunks: Chunks | None = None, k: int = 0, emb_out=None, cfg:
     if check and rc not in (FAST_OK,):
         _check(rc)
     return {"count": cnt.value, "written": wr.value, "status": rc, "emb": emb_out}
+
+
+def match_noalloc(cst: Cst, chunks: Chunks | None = None, k: int = 0, emb_out=None, cfg: Config | None = None,
+                  stream=None, check: bool = True):
+    """fast_match_noalloc: the matcher with its scratch in a static device
+    array, for callers that must not allocate.  emb_out (k > 0) must be a
+    device buffer.  Returns dict(count, written, status)."""
+    cnt, wr = _u64(), _u64()
+    rc = lib().fast_match_noalloc(cst.handle, chunks.handle if chunks else None, ctypes.byref(cfg) if cfg else None,
+                                  k, _p(emb_out), ctypes.byref(cnt), ctypes.byref(wr),
+                                  stream if stream is not None else cst.stream)
+    if check:
+        _check(rc)
+    return {"count": cnt.value, "written": wr.value, "status": rc}
 
 
 def match_stats(cst: Cst, chunks: Chunks | None = None, cfg: Config | None = None, stream=None):

@@ -23,6 +23,7 @@
 // work counter ends the launch.  Every wait is bounded and reports a status.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -556,3 +557,142 @@ extern "C" int fast_match_stats(const fast_cst* c, const fast_chunks* chunks, co
 extern "C" double fast_last_match_ms(void) { return g_last_match_ms; }
 
 extern "C" uint64_t fast_last_match_bytes(void) { return g_last_match_bytes; }
+
+// ------------------------------------------------------ allocation-free matcher
+//
+// Scratch of fast_match_noalloc, in one file-scope device array: the counter
+// block, the queue of donated runs with its ready flags, and the run
+// descriptors used when no partition is given.  Host code must not pass the
+// symbol itself to a kernel (on the host it only names a stand-in); the
+// device address is looked up once per device with cudaGetSymbolAddress.
+
+namespace {
+
+constexpr int kNoAllocQueue = 4096;                   // donated runs
+constexpr int kNoAllocRuns = 32768;                   // root runs when chunks == NULL
+constexpr size_t kNaCtrBytes = ((kCtrWords * sizeof(unsigned long long) + 255) / 256) * 256;
+constexpr size_t kNaQueueBytes = kNoAllocQueue * sizeof(Chunk);
+constexpr size_t kNaReadyBytes = ((kNoAllocQueue * sizeof(uint32_t) + 255) / 256) * 256;
+constexpr size_t kNaRunsBytes = kNoAllocRuns * sizeof(Chunk);
+constexpr size_t kNoAllocBytes = kNaCtrBytes + kNaQueueBytes + kNaReadyBytes + kNaRunsBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// device address of the scratch array on the current device (looked up once)
+int noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    FAST_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(FAST_ERR_INVALID, "fast_match_noalloc: device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        unsigned char* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(scratch)", __FILE__, __LINE__);
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return FAST_OK;
+}
+
+__global__ void k_root_runs(Chunk* runs, uint64_t parts, uint64_t nr) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= parts) return;
+    Chunk c;
+    memset(&c, 0, sizeof(c));
+    c.j = 0;
+    c.a = (uint32_t)(i * nr / parts);
+    c.b = (uint32_t)((i + 1) * nr / parts);
+    runs[i] = c;
+}
+
+int run_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_config* cfg_in, uint64_t kemb,
+                      uint32_t* emb_out, uint64_t* count_out, uint64_t* written_out, cudaStream_t s) {
+    if (!c) return set_error(FAST_ERR_INVALID, "fast_match_noalloc: cst is NULL");
+    if (kemb > 0 && !emb_out) return set_error(FAST_ERR_INVALID, "fast_match_noalloc: k > 0 needs emb_out");
+    if (chunks && chunks->c != c) return set_error(FAST_ERR_INVALID, "fast_match_noalloc: chunks belong to another CST");
+    if (kemb > 0) {
+        cudaPointerAttributes at;
+        cudaError_t e = cudaPointerGetAttributes(&at, emb_out);
+        cudaGetLastError();
+        if (e != cudaSuccess || (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged))
+            return set_error(FAST_ERR_INVALID, "fast_match_noalloc: emb_out must be device memory (a host buffer would need a staging allocation)");
+    }
+    fast_config cfg = cfg_in ? *cfg_in : c->cfg;
+    int warps = cfg.warps_per_block > 0 ? cfg.warps_per_block : 8;
+    if (warps > 8) warps = 8;
+    int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : 4;
+    unsigned char* base = nullptr;
+    FAST_TRY(noalloc_scratch(&base));
+    unsigned long long* ctr = (unsigned long long*)base;
+    Chunk* dq = (Chunk*)(base + kNaCtrBytes);
+    uint32_t* dq_ready = (uint32_t*)(base + kNaCtrBytes + kNaQueueBytes);
+    Chunk* runs = (Chunk*)(base + kNaCtrBytes + kNaQueueBytes + kNaReadyBytes);
+    const Chunk* dchunks = nullptr;
+    int64_t nchunks = 0;
+    if (chunks) { dchunks = chunks->d; nchunks = chunks->n; }
+    else if (c->ncand[c->root] > 0) {
+        uint64_t nr = (uint64_t)c->ncand[c->root];
+        uint64_t want = (uint64_t)num_sms() * bps * warps * 4;
+        uint64_t parts = std::min<uint64_t>(nr, want);
+        if (parts > (uint64_t)kNoAllocRuns)
+            return set_error(FAST_ERR_INVALID,
+                             "fast_match_noalloc: %llu root runs needed, the static scratch holds %d "
+                             "(pass a partition or fewer warps per SM)", (unsigned long long)parts, kNoAllocRuns);
+        k_root_runs<<<(unsigned)ceil_div((int64_t)parts, 256), 256, 0, s>>>(runs, parts, nr);
+        note_launch();
+        dchunks = runs;
+        nchunks = (int64_t)parts;
+    }
+    uint64_t emb_cap = kemb;
+    if (cfg.limit > 0 && cfg.limit < emb_cap) emb_cap = cfg.limit;
+    FAST_CUDA(cudaMemsetAsync(ctr, 0, kCtrWords * sizeof(unsigned long long), s));
+    unsigned long long out0 = (unsigned long long)nchunks;
+    FAST_CUDA(cudaMemcpyAsync(ctr + kOut, &out0, sizeof(out0), cudaMemcpyHostToDevice, s));
+    FAST_CUDA(cudaMemsetAsync(dq_ready, 0, kNoAllocQueue * sizeof(uint32_t), s));
+    MatchPlan P = make_plan(c);
+    MatchOut O;
+    O.next_chunk = ctr + kNext; O.total = ctr + kTotal; O.emb_slot = ctr + kSlot; O.status = (int*)(ctr + kStatus);
+    O.chunk_counts = nullptr; O.emb = emb_out; O.emb_cap = emb_cap;
+    O.stats = nullptr;
+    O.bytes = ctr + kBytes;
+    O.deadline = ctr + kDeadline;
+    O.limit = cfg.limit;
+    O.dq = dq; O.dq_ready = dq_ready; O.dq_cap = kNoAllocQueue;
+    O.dq_head = ctr + kHead; O.dq_tail = ctr + kTail; O.outstanding = ctr + kOut;
+    O.idle = (unsigned int*)(ctr + kIdle);
+    unsigned long long budget_ns = cfg.time_budget_s > 0 ? (unsigned long long)(cfg.time_budget_s * 1e9) : 0ull;
+    if (budget_ns) { k_set_deadline<<<1, 1, 0, s>>>(ctr + kDeadline, budget_ns); note_launch(); }
+    if (nchunks > 0) {
+        int64_t grid = (int64_t)num_sms() * bps;
+        size_t sh = smem_bytes(warps);
+        if (kemb > 0) k_match<false, true><<<(unsigned)grid, warps * 32, sh, s>>>(P, dchunks, nchunks, O);
+        else k_match<false, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, dchunks, nchunks, O);
+        note_launch();
+        FAST_CUDA(cudaGetLastError());
+    }
+    unsigned long long h[kCtrWords];
+    FAST_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FAST_CUDA(cudaStreamSynchronize(s));
+    uint64_t total = h[kTotal];
+    if (cfg.limit > 0 && total > cfg.limit) total = cfg.limit;
+    if (count_out) *count_out = total;
+    if (written_out) *written_out = std::min<uint64_t>(emb_cap, h[kSlot]);
+    int st = (int)h[kStatus];
+    if (st & kStatusStall) return set_error(FAST_ERR_CUDA, "fast_match_noalloc: a donated run was never published");
+    if (st & kStatusTimeout) return set_error(FAST_ERR_TIMEOUT, "fast_match_noalloc: time budget of %.3f s spent", cfg.time_budget_s);
+    if (st & kStatusOverflow) return set_error(FAST_ERR_OVERFLOW, "fast_match_noalloc: count reached 2^64");
+    return FAST_OK;
+}
+
+}  // namespace
+
+extern "C" int fast_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_config* cfg, uint64_t k,
+                                  uint32_t* emb_out, uint64_t* count_out, uint64_t* written_out, void* stream) {
+    return run_match_noalloc(c, chunks, cfg, k, emb_out, count_out, written_out, (cudaStream_t)stream);
+}
+
+extern "C" uint64_t fast_match_noalloc_scratch_bytes(void) { return (uint64_t)kNoAllocBytes; }
