@@ -135,7 +135,8 @@ def match(g: Graph, qlabels, qedges, order=None, par=None, allow=None, max_emb: 
     Returns a dict: count, complete (False if the per-thread node budget was
     hit), emb (sorted int32[rows][k] indexed by query vertex, at most
     max_emb rows), depth (partial results per number of mapped positions),
-    balg (see oracle_match in oracle.c).
+    balg / balg_max: floor and ceiling of the bytes a search over the CST
+    requests (see oracle_match in oracle.c).
     """
     ql, qe = _qarrays(qlabels, qedges)
     k = ql.shape[0]
@@ -156,7 +157,7 @@ def match(g: Graph, qlabels, qedges, order=None, par=None, allow=None, max_emb: 
     emb = np.zeros((max(max_emb, 1), k), dtype=np.int32)
     cnt = np.zeros(1, dtype=np.uint64)
     depth = np.zeros(k, dtype=np.uint64)
-    balg = np.zeros(1, dtype=np.float64)
+    balg = np.zeros(2, dtype=np.float64)
     rc = _L().oracle_match(g._h, k, _p(ql), qe.shape[0], _p(qe), _p(o), _p(pp), _p(aoff), _p(av), _p(aon),
                            max_emb, _p(emb), _p(cnt), _p(depth), _p(balg) if want_balg else None,
                            budget, threads, limit)
@@ -168,7 +169,8 @@ def match(g: Graph, qlabels, qedges, order=None, par=None, allow=None, max_emb: 
         rows = rows[np.lexsort(rows.T[::-1])]
     return {"count": count, "complete": rc == 0, "emb": rows,
             "depth": depth.astype(np.int64) if want_depth else None,
-            "balg": float(balg[0]) if want_balg else None}
+            "balg": float(balg[0]) if want_balg else None,
+            "balg_max": float(balg[1]) if want_balg else None}
 
 
 def invalid_rows(g: Graph, qlabels, qedges, emb) -> int:

@@ -367,9 +367,11 @@ void oracle_cst_workload(const ocst* c, double* w_f, uint64_t* w_i, int dump_u, 
  *            dropped (the CST validity rule applied to single candidates).
  *   cap      runs are processed level by level (all runs of one depth of the
  *            recursion, in order); a level whose chunks plus new parts
- *            would pass max_chunks turns its live runs into chunks as they
- *            are (their W' may exceed delta_w), which keeps them disjoint
- *            and complete.
+ *            would pass max_chunks caps each split at
+ *            max(1, (max_chunks - chunks so far - runs finishing) /
+ *            runs splitting) parts, and those parts become the last chunks
+ *            as they are (W' may exceed delta_w; W' = 0 parts included),
+ *            which keeps them disjoint and complete.
  *   sample   optional: a run produced by a split into k parts is kept iff
  *            u01(id) < min(1, c/k), c = c_root at the first position and
  *            c_deep later (c <= 0 keeps every run).  id(root) = mix64(seed),
@@ -548,10 +550,20 @@ static void p_levels(pctx* P, ochunk root) {
                 for (uint64_t i = 0; i < kk[t]; i++)
                     np += p_keep(P, cur[t].j, kk[t], pmix(cur[t].id + (i + 1) * 0x9E3779B97F4A7C15ull));
         }
+        int last = 0;
         if (P->nout + ne + np > P->max_chunks) {
-            for (int64_t t = 0; t < ncur; t++) if (act[t] != 0) p_emit(P, &cur[t]);
-            free(act); free(kk);
-            break;
+            /* cap every split at an even share of the room left; its parts
+             * are the last chunks */
+            int64_t nsplit = nl - ne, room = P->max_chunks - P->nout - ne;
+            uint64_t kcap = (uint64_t)((nsplit > 0 && room / nsplit > 1) ? room / nsplit : 1);
+            np = 0;
+            for (int64_t t = 0; t < ncur; t++) {
+                if (act[t] != 2) continue;
+                if (kk[t] > kcap) kk[t] = kcap;
+                for (uint64_t i = 0; i < kk[t]; i++)
+                    np += p_keep(P, cur[t].j, kk[t], pmix(cur[t].id + (i + 1) * 0x9E3779B97F4A7C15ull));
+            }
+            last = 1;
         }
         ochunk* nxt = (ochunk*)malloc((size_t)(np > 0 ? np : 1) * sizeof(ochunk));
         int64_t o = 0;
@@ -575,6 +587,10 @@ static void p_levels(pctx* P, ochunk root) {
         free(act); free(kk); free(cur);
         cur = nxt;
         ncur = o;
+        if (last) {
+            for (int64_t t = 0; t < ncur; t++) p_emit(P, &cur[t]);
+            ncur = 0;
+        }
     }
     free(cur);
 }

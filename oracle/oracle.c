@@ -140,7 +140,7 @@ typedef struct {
 typedef struct {
     uint64_t count;
     uint64_t depth[OMAXK];     /* valid partial results with d+1 positions mapped */
-    double balg;               /* list bytes read to extend them (see oracle_match) */
+    double balg[2];            /* bytes to extend them: floor and ceiling (see oracle_match) */
     int64_t nodes;
     int over;
 } sacc;
@@ -150,17 +150,56 @@ static int allowed(const sctx* c, int u, int32_t v) {
     return in_sorted(c->av + c->aoff[u], c->aoff[u + 1] - c->aoff[u], v);
 }
 
-/* |{w in N_G(x) : l(w) = l_q(u), w allowed for u}| -- the length of the list
- * the candidate search tree holds for x towards u when the allowed sets are
- * the tree's candidate sets. */
-static int64_t list_len(const sctx* c, int32_t x, int u) {
+/* The CST list of x towards u when the allowed sets are the tree's
+ * candidate sets: { w in N_G(x) : l(w) = l_q(u), w allowed for u }, in
+ * increasing id (N_G(x) is sorted).  Returns its length; fills buf. */
+static int64_t cst_list(const sctx* c, int32_t x, int u, int32_t* buf) {
     const og* g = c->g;
     int64_t n = 0;
     for (int64_t i = g->off[x]; i < g->off[x + 1]; i++) {
         int32_t w = g->adj[i];
-        if (g->lab[w] == c->ql[u] && allowed(c, u, w)) n++;
+        if (g->lab[w] == c->ql[u] && allowed(c, u, w)) buf[n++] = w;
     }
     return n;
+}
+
+/* Bytes a search over the candidate search tree requests to extend the
+ * valid partial M[0..d) by one position.  lo[0] is what any such search must
+ * read: 4 B for the image of the last position, 16 B of list offsets for the
+ * tree list and for each earlier non-tree neighbour's list, 4 B per
+ * tree-list entry, and 4 B for an entry's data vertex when an earlier
+ * position has the same label and the entry passed the non-tree checks.
+ * lo[1] adds a ceiling on the non-tree list reads of a warp-cooperative
+ * merge: per non-tree list, its entries plus one 32-entry tile, and per
+ * 32-entry segment of the tree list ten more 32-entry probe rounds. */
+static void extension_bytes(const sctx* c, const int32_t* M, int d, double* lo) {
+    const og* g = c->g;
+    int u = c->order[d];
+    int32_t x = M[c->par[d]];
+    double b = 4.0 + 16.0 + 16.0 * c->nb[d], extra = 0.0;
+    int64_t maxd = g->off[x + 1] - g->off[x];
+    for (int j = 0; j < c->nb[d]; j++) {
+        int32_t y = M[c->bn[d][j]];
+        if (g->off[y + 1] - g->off[y] > maxd) maxd = g->off[y + 1] - g->off[y];
+    }
+    int32_t* T = (int32_t*)malloc((size_t)(maxd > 0 ? maxd : 1) * sizeof(int32_t));
+    int32_t* N = (int32_t*)malloc((size_t)(maxd > 0 ? maxd : 1) * sizeof(int32_t));
+    int64_t nt = cst_list(c, x, u, T);
+    int same = 0;
+    for (int j = 0; j < d; j++) if (c->ql[c->order[j]] == c->ql[u]) same = 1;
+    uint8_t* ok = (uint8_t*)malloc((size_t)(nt > 0 ? nt : 1));
+    for (int64_t i = 0; i < nt; i++) { ok[i] = 1; b += 4.0; }
+    int64_t segs = (nt + 31) / 32;
+    for (int j = 0; j < c->nb[d]; j++) {
+        int64_t nn = cst_list(c, M[c->bn[d][j]], u, N);
+        extra += 4.0 * (double)(nn + 32) + 4.0 * 32.0 * 10.0 * (double)segs;
+        for (int64_t i = 0; i < nt; i++)
+            if (ok[i] && !in_sorted(N, nn, T[i])) ok[i] = 0;
+    }
+    if (same) for (int64_t i = 0; i < nt; i++) if (ok[i]) b += 4.0;
+    free(T); free(N); free(ok);
+    lo[0] += b;
+    lo[1] += b + extra;
 }
 
 static void emit(const sctx* c, const int32_t* M) {
@@ -189,11 +228,7 @@ static void extend(const sctx* c, sacc* a, int32_t* M, int d, int want_balg) {
     int32_t x = M[c->par[d]];
     a->nodes += 1 + (g->off[x + 1] - g->off[x]);
     if (c->budget > 0 && a->nodes > c->budget) { a->over = 1; return; }
-    if (want_balg) {
-        a->balg += 8.0 + 4.0 * (double)list_len(c, x, u);
-        for (int j = 0; j < c->nb[d]; j++)
-            a->balg += 8.0 + 4.0 * (double)list_len(c, M[c->bn[d][j]], u);
-    }
+    if (want_balg) extension_bytes(c, M, d, a->balg);
     /* candidates: N_G(x), or the allowed set of u when that is shorter
      * (then adjacency to x is tested by binary search) */
     int64_t na = (c->aon && c->aon[u]) ? c->aoff[u + 1] - c->aoff[u] : -1;
@@ -229,11 +264,11 @@ static void extend(const sctx* c, sacc* a, int32_t* M, int d, int want_balg) {
  *        emb_out[max_emb][k] indexed by query vertex id (any order);
  *        depth_out[d] (nullable) = number of partial embeddings of the first
  *        d+1 positions that satisfy labels, injectivity, every edge among
- *        them and the allowed sets; *balg_out (nullable) = for every such
- *        partial embedding of d = 1..k-1 positions, 8 + 4*|list| bytes for
- *        the list it is extended from and for each other earlier neighbour's
- *        list, where a list is N_G(x) restricted to the next query vertex's
- *        label and allowed set.
+ *        them and the allowed sets; *balg_out (nullable) = the bytes a search
+ *        over the candidate search tree requests to extend every such partial
+ *        embedding of d = 1..k-1 positions (extension_bytes): balg_out[0]
+ *        the floor, balg_out[1] the ceiling, with the allowed sets taken as
+ *        the tree's candidate sets.
  * limit (> 0) stops the search once `limit` embeddings are found; the count
  * is then exactly min(total, limit) and the rows any such embeddings.
  * Returns 0, 1 when some thread exceeded node_budget (>0) work units (one
@@ -323,18 +358,19 @@ int oracle_match(const og* g, int k, const int32_t* ql, int nqe, const int32_t* 
         }
     }
     uint64_t cnt = 0;
-    double balg = want_balg ? 4.0 * (double)nr : 0.0;
+    double balg[2] = {0.0, 0.0};
     int over = 0, limited = 0;
     if (depth_out) memset(depth_out, 0, (size_t)k * sizeof(uint64_t));
     for (int t = 0; t < nt; t++) {
         cnt += acc[t].count;
-        balg += acc[t].balg;
+        balg[0] += acc[t].balg[0];
+        balg[1] += acc[t].balg[1];
         over |= acc[t].over == 1;
         limited |= acc[t].over == 2;
         if (depth_out) for (int d = 0; d < k; d++) depth_out[d] += acc[t].depth[d];
     }
     *count_out = cnt;
-    if (balg_out) *balg_out = balg;
+    if (balg_out) { balg_out[0] = balg[0]; balg_out[1] = balg[1]; }
     free(acc); free(roots);
     if (over && !limited) return 1;
     return 0;

@@ -377,18 +377,39 @@ def test_partition_sampling_keeps_a_subset():
 # ------------------------------------------------------ algorithmic bytes
 
 def test_balg_counts_lists_of_extended_partials():
-    """The list-byte count of the enumerator, on a path a-b-c where every
-    list is known by hand."""
+    """The byte count of the enumerator, on a path a-b-c where every list
+    is known by hand."""
     # 0(a)-1(b)-2(c), 0-3(b), 3-4(c), 3-5(c)
     edges = [[0, 1], [1, 2], [0, 3], [3, 4], [3, 5]]
     labels = [0, 1, 2, 1, 2, 2]
     g = oracle.Graph(6, edges, labels)
     r = oracle.match(g, [0, 1, 2], [[0, 1], [1, 2]], want_balg=True, want_depth=True)
     assert r["count"] == 3
-    # root list: 1 candidate (4 B); extend {0}: list of 0 towards b = {1,3} (8+8);
-    # extend {0,1}: list of 1 towards c = {2} (8+4); extend {0,3}: {4,5} (8+8)
-    assert r["balg"] == 4 + (8 + 8) + (8 + 4) + (8 + 8)
+    # extend {0}: image 4 + offsets 16 + list {1,3} 2*4; extend {0,1}: 4 + 16 + {2} 4;
+    # extend {0,3}: 4 + 16 + {4,5} 2*4
+    assert r["balg"] == (4 + 16 + 8) + (4 + 16 + 4) + (4 + 16 + 8)
     assert r["depth"].tolist() == [1, 2, 3]
+
+
+def test_balg_floor_and_ceiling_on_a_triangle_query():
+    """A triangle query: one non-tree list per extension at the last
+    position; floor and ceiling by hand."""
+    # star centre 0 (a) with leaves 1..4 (b); leaves 1-2 and 3-4 joined
+    edges = [[0, 1], [0, 2], [0, 3], [0, 4], [1, 2], [3, 4]]
+    labels = [0, 1, 1, 1, 1]
+    g = oracle.Graph(5, edges, labels)
+    # q: a-b, a-b', b-b' in order (0, 1, 2), parents (-, 0, 0)
+    r = oracle.match(g, [0, 1, 1], [[0, 1], [0, 2], [1, 2]], order=[0, 1, 2], par=[0, 0, 0],
+                     want_balg=True, want_depth=True)
+    assert r["count"] == 4 and r["depth"].tolist() == [1, 4, 4]
+    # extend {0}: 4 + 16 + list {1,2,3,4} 16 = 36
+    # extend {0,x}: 4 + 16 + 16 (non-tree offsets) + tree list 16 + one entry passes
+    #   the non-tree check and has position 1's label: 4
+    floor = 36 + 4 * (4 + 16 + 16 + 16 + 4)
+    assert r["balg"] == floor
+    # ceiling: per extension {0,x}, the 1-entry non-tree list plus a tile (33 entries)
+    #   and one segment of ten 32-entry rounds
+    assert r["balg_max"] == floor + 4 * (4 * 33 + 4 * 32 * 10)
 
 
 # ------------------------------------------------------------------- limit
