@@ -202,9 +202,11 @@ void fast_free_cst(fast_cst* c);
  * candidate or lacks a CST edge to a fixed non-tree neighbour, in which case
  * it holds no embedding and is dropped; longer runs split again.  Runs are
  * processed level by level; if a level would bring the chunk count above
- * cfg->max_chunks, the runs still pending become chunks as they are (their
- * W' may exceed delta_w).  With sampling off the chunks are disjoint and
- * cover every embedding.  The host reads two sizes per level.
+ * cfg->max_chunks, each of its splits is capped at
+ * max(1, (max_chunks - chunks so far - runs finishing) / runs splitting)
+ * parts and those parts are the last chunks (their W' may exceed delta_w).
+ * With sampling off the chunks are disjoint and cover every embedding.  The
+ * host reads a few sizes per level.
  */
 int fast_partition(const fast_cst* c, const fast_config* cfg, void* stream, fast_chunks** out);
 
@@ -249,14 +251,114 @@ int fast_match_ex(const fast_cst* c, const fast_chunks* chunks, const fast_confi
                   void* stream);
 
 /*
- * Counting pass over the same search: out[0] = algorithmic bytes (list
- * offsets 8 B and list entries 4 B for every list a partial result is
- * extended from or checked against, plus 4 B per candidate of a root run),
- * out[1 + d] for d < k = partial results with d+1 positions mapped that pass
- * every check.  out has k + 1 entries; host memory.
+ * Counting pass over the same search: out[0] = bytes the search requested
+ * (as fast_last_match_bytes), out[1 + d] for d < k = partial results with
+ * d+1 positions mapped that pass every check.  out has k + 1 entries; host
+ * memory.
  */
 int fast_match_stats(const fast_cst* c, const fast_chunks* chunks, const fast_config* cfg, uint64_t* out,
                      void* stream);
+
+/* --------------------------------------------------------------- batch */
+
+typedef struct fast_batch fast_batch;
+
+/*
+ * A reusable context for matching many queries in one matcher launch (the
+ * data-parallel use of independent CSTs the paper notes in its multi-FPGA
+ * discussion, Sec. VI, on one device).  Owns fixed device buffers for up to
+ * max_queries queries, `threads` host worker threads' CUDA streams (<= 0:
+ * 8), and, once run, a CUDA graph of the matcher launch that later runs
+ * replay.  cfg (NULL: defaults) seeds every query-size class's configuration
+ * (classes: |V(q)| <= 4, 8, 16, 24, 32); cfg->limit and time_budget_s apply
+ * to every query of a run.  Uses the current CUDA device.
+ */
+int fast_batch_create(const fast_graph* g, const fast_config* cfg, int32_t max_queries, int32_t threads,
+                      fast_batch** out);
+
+/*
+ * Match nq queries (nq <= max_queries): the worker threads build each
+ * query's CST and partition concurrently on their own streams; then one
+ * graph-replayed matcher launch enumerates all chunks of all queries, warps
+ * sharing work across queries.  counts_out[i] (host) = number of embeddings
+ * of query i (min(total, limit) when cfg->limit > 0); status_out[i] (host) =
+ * FAST_OK, the error of that query's CST build or partition (the others
+ * still run), or FAST_ERR_TIMEOUT when the time budget ended the launch
+ * before the query was done.  Synchronises `stream`.
+ */
+int fast_batch_run(fast_batch* b, int32_t nq, const fast_query_desc* queries, uint64_t* counts_out,
+                   int32_t* status_out, void* stream);
+
+/* Last run: wall time of the CST/partition phase, event time of the matcher
+ * launch, bytes the matcher requested, and chunks matched. */
+int fast_batch_timing(const fast_batch* b, double* build_ms, double* match_ms, uint64_t* match_bytes, int64_t* chunks);
+
+/* Read (get != NULL) and/or replace (set != NULL) the configuration of the
+ * size class that a query of size_class_k vertices falls into. */
+int fast_batch_config(fast_batch* b, int32_t size_class_k, fast_config* get, const fast_config* set);
+
+/*
+ * Autotune on sample queries: per size class present in the sample, the
+ * partition's delta_w and max_chunks (how deep the level-synchronous
+ * partition goes before the depth-first matcher takes over), then the
+ * matcher's launch shape (warps per CTA, CTAs per SM), each choice by the
+ * wall time of batch runs over the sample.  *best_ms (nullable) receives
+ * the best full-sample time.  Results stay in the batch's configuration.
+ */
+int fast_batch_autotune(fast_batch* b, int32_t nq, const fast_query_desc* sample, double* best_ms, void* stream);
+
+void fast_free_batch(fast_batch* b);
+
+/* One-shot: create a batch for nq queries, run it, free it. */
+int fast_match_batch(const fast_graph* g, int32_t nq, const fast_query_desc* queries, const fast_config* cfg,
+                     uint64_t* counts_out, int32_t* status_out, void* stream);
+
+/* ------------------------------------------------------------- serving */
+
+typedef struct fast_server fast_server;
+
+/* One finished request. Times are fast_now_ns() readings. */
+typedef struct {
+    uint64_t id;
+    uint64_t count;          /* embeddings (min(total, limit) when cfg->limit > 0) */
+    int32_t status;          /* FAST_OK, a CST/partition/match error, or FAST_ERR_OOM when the
+                                request's projected bytes exceed the whole budget */
+    int32_t pad;
+    uint64_t t_arrive_ns;    /* submitted */
+    uint64_t t_start_ns;     /* admitted by a worker */
+    uint64_t t_done_ns;      /* count known */
+} fast_result;
+
+/*
+ * A request loop over the resident data graph g (the host/accelerator task
+ * flow of Sec. IV, kept on one GPU): requests wait in a FIFO queue; each of
+ * `workers` host threads (<= 0: 4), with its own CUDA stream, takes the head
+ * request when its projected device bytes -- label buckets and neighbour
+ * lists its CST can hold, plus the matcher's scratch -- fit in what
+ * budget_bytes leaves (a request is always admitted when nothing runs), then
+ * builds its CST, partitions it and matches it with cfg (NULL: defaults;
+ * blocks_per_sm sizes each matcher launch, so 1 lets about four launches
+ * share the GPU).  Requests arriving while others run are admitted as
+ * workers and memory free up; their kernels overlap on the device.
+ */
+int fast_server_create(const fast_graph* g, const fast_config* cfg, uint64_t budget_bytes, int32_t workers,
+                       fast_server** out);
+
+/* Queue one query (its arrays are copied); *id_out (nullable) gets its id. */
+int fast_server_submit(fast_server* s, const fast_query_desc* q, uint64_t* id_out);
+
+/* Move up to max_results finished requests into out (any order), waiting
+ * up to wait_ms for the first one when none is ready; *n_out = how many. */
+int fast_server_poll(fast_server* s, int32_t max_results, fast_result* out, int32_t* n_out, int32_t wait_ms);
+
+/* Requests queued, requests running, projected bytes admitted. */
+int fast_server_stats(fast_server* s, int64_t* pending, int64_t* running, uint64_t* in_use_bytes);
+
+/* Stop: requests still queued are dropped, running ones finish. */
+void fast_server_destroy(fast_server* s);
+
+/* The steady clock of the result timestamps, in nanoseconds. */
+uint64_t fast_now_ns(void);
 
 /*
  * fast_match_noalloc -- fast_match for callers that must not allocate device
@@ -298,9 +400,12 @@ uint64_t fast_match_noalloc_scratch_bytes(void);
  * the kernel (0 if none ran). */
 double fast_last_match_ms(void);
 
-/* Algorithmic bytes of the last fast_match on this host thread: 8 B of
- * offsets plus 4 B per entry for every list a partial result was extended
- * from or checked against, and 4 B per candidate of a root run. */
+/* Bytes the last fast_match on this host thread requested from memory:
+ * 16 B of offsets per list opened (a tree list per extended partial result,
+ * a non-tree list per earlier non-tree neighbour), 4 B per tree-list entry
+ * scanned, 4 B per entry a binary search reads, 4 B per data-vertex id
+ * gathered, and 4|V(q)| B per embedding written.  Counted by every lane of
+ * the search itself, whichever level of the memory hierarchy serves it. */
 uint64_t fast_last_match_bytes(void);
 
 /* Kernels launched by the library since the process started (all threads). */

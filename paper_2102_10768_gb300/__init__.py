@@ -78,6 +78,19 @@ _SIGS = {
     "fast_match": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp, _vp, _vp]),
     "fast_match_ex": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp, _vp]),
     "fast_match_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fast_batch_create": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp]),
+    "fast_batch_run": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    "fast_batch_timing": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fast_batch_config": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+    "fast_batch_autotune": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "fast_free_batch": (None, [_vp]),
+    "fast_match_batch": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "fast_server_create": (ctypes.c_int, [_vp, _vp, _u64, _i32, _vp]),
+    "fast_server_submit": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fast_server_poll": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32]),
+    "fast_server_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "fast_server_destroy": (None, [_vp]),
+    "fast_now_ns": (ctypes.c_uint64, []),
     "fast_match_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp, _vp, _vp, _vp]),
     "fast_match_noalloc_scratch_bytes": (ctypes.c_uint64, []),
     "fast_last_match_ms": (ctypes.c_double, []),
@@ -329,6 +342,131 @@ def match(cst: Cst, chunks: Chunks | None = None, k: int = 0, emb_out=None, cfg:
     if check and rc not in (FAST_OK,):
         _check(rc)
     return {"count": cnt.value, "written": wr.value, "status": rc, "emb": emb_out}
+
+
+def _query_descs(queries):
+    """ctypes array of QueryDesc for [(labels, edges)], plus the arrays it points to."""
+    keep = []
+    arr = (QueryDesc * max(len(queries), 1))()
+    for i, (ql, qe) in enumerate(queries):
+        ql = np.ascontiguousarray(np.asarray(ql, dtype=np.int32))
+        qe = np.ascontiguousarray(np.asarray(qe, dtype=np.int32).reshape(-1, 2))
+        keep += [ql, qe]
+        arr[i] = QueryDesc(ql.shape[0], qe.shape[0], ql.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                           qe.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return arr, keep
+
+
+class Batch:
+    """Reusable batched matcher (fast_batch_*): one graph-replayed matcher
+    launch per run for all queries."""
+
+    def __init__(self, graph: Graph, max_queries: int, cfg: Config | None = None, threads: int = 0):
+        h = _vp()
+        _check(lib().fast_batch_create(graph.handle, ctypes.byref(cfg) if cfg else None, max_queries, threads,
+                                       ctypes.byref(h)))
+        self._h = h
+        self.graph = graph
+
+    def run(self, queries, stream=None):
+        """queries: [(labels, edges)].  Returns (counts int64[n], status int32[n])."""
+        arr, keep = _query_descs(queries)
+        n = len(queries)
+        counts = np.zeros(max(n, 1), np.uint64)
+        status = np.zeros(max(n, 1), np.int32)
+        _check(lib().fast_batch_run(self._h, n, arr, _p(counts), _p(status),
+                                    stream if stream is not None else default_stream()))
+        return counts[:n].astype(np.int64), status[:n]
+
+    def timing(self):
+        b, m, by, ch = ctypes.c_double(), ctypes.c_double(), _u64(), _i64()
+        _check(lib().fast_batch_timing(self._h, ctypes.byref(b), ctypes.byref(m), ctypes.byref(by), ctypes.byref(ch)))
+        return {"build_ms": b.value, "match_ms": m.value, "match_bytes": by.value, "chunks": ch.value}
+
+    def config(self, k: int, new: Config | None = None) -> Config:
+        c = Config()
+        _check(lib().fast_batch_config(self._h, k, ctypes.byref(c), ctypes.byref(new) if new else None))
+        return new if new else c
+
+    def autotune(self, sample, stream=None) -> float:
+        arr, keep = _query_descs(sample)
+        best = ctypes.c_double()
+        _check(lib().fast_batch_autotune(self._h, len(sample), arr, ctypes.byref(best),
+                                         stream if stream is not None else default_stream()))
+        return best.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fast_free_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("count", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("t_arrive_ns", ctypes.c_uint64), ("t_start_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64)]
+
+
+class Server:
+    """Request loop with continuous batching over a resident graph
+    (fast_server_*)."""
+
+    def __init__(self, graph: Graph, budget_bytes: int, cfg: Config | None = None, workers: int = 0):
+        h = _vp()
+        _check(lib().fast_server_create(graph.handle, ctypes.byref(cfg) if cfg else None, int(budget_bytes),
+                                        workers, ctypes.byref(h)))
+        self._h = h
+        self.graph = graph
+
+    def submit(self, labels, edges) -> int:
+        arr, keep = _query_descs([(labels, edges)])
+        rid = _u64()
+        _check(lib().fast_server_submit(self._h, ctypes.byref(arr[0]), ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, max_results: int = 1024, wait_ms: int = 0):
+        out = (Result * max_results)()
+        n = _i32()
+        _check(lib().fast_server_poll(self._h, max_results, out, ctypes.byref(n), wait_ms))
+        return [{"id": r.id, "count": r.count, "status": r.status, "t_arrive_ns": r.t_arrive_ns,
+                 "t_start_ns": r.t_start_ns, "t_done_ns": r.t_done_ns} for r in out[:n.value]]
+
+    def stats(self):
+        p, r, b = _i64(), _i64(), _u64()
+        _check(lib().fast_server_stats(self._h, ctypes.byref(p), ctypes.byref(r), ctypes.byref(b)))
+        return {"pending": p.value, "running": r.value, "in_use_bytes": b.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fast_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def now_ns() -> int:
+    return int(lib().fast_now_ns())
+
+
+def match_batch(graph: Graph, queries, cfg: Config | None = None, stream=None):
+    """fast_match_batch (one shot): (counts, status)."""
+    arr, keep = _query_descs(queries)
+    n = len(queries)
+    counts = np.zeros(max(n, 1), np.uint64)
+    status = np.zeros(max(n, 1), np.int32)
+    _check(lib().fast_match_batch(graph.handle, n, arr, ctypes.byref(cfg) if cfg else None, _p(counts), _p(status),
+                                  stream if stream is not None else default_stream()))
+    return counts[:n].astype(np.int64), status[:n]
 
 
 def match_noalloc(cst: Cst, chunks: Chunks | None = None, k: int = 0, emb_out=None, cfg: Config | None = None,

@@ -65,6 +65,19 @@ __global__ void k_cand_degree(const int32_t* __restrict__ cand, int64_t nc, cons
     if (i < nc) out[i] = row_ptr[cand[i] + 1] - row_ptr[cand[i]];
 }
 
+// degrees of the first *n candidates, zero up to the bound `cap`
+__global__ void k_cand_degree_n(const int32_t* __restrict__ cand, const int64_t* __restrict__ n, int64_t cap,
+                                const int64_t* __restrict__ row_ptr, int64_t* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap) return;
+    out[i] = i < *n ? row_ptr[cand[i] + 1] - row_ptr[cand[i]] : 0;
+}
+
+// off[*n] = *val (closing offset of a list set whose row count is on the device)
+__global__ void k_set_tail(int64_t* off, const int64_t* n, const int64_t* val) { off[*n] = *val; }
+__global__ void k_set_tail_at(int64_t* off, int64_t n, const int64_t* val) { off[n] = *val; }
+__global__ void k_copy_i64(int64_t* dst, const int64_t* src) { *dst = *src; }
+
 __device__ __forceinline__ int64_t row_of(const int64_t* e_off, int64_t rows, int64_t i) {
     // last r with e_off[r] <= i
     int64_t lo = 0, hi = rows;
@@ -89,13 +102,18 @@ struct TopDownF {
     int32_t want_dq;
     uint32_t* reached;         // bitmap over V(G)
     int64_t* t_off;            // out: [rows+1]
+    const int64_t* E;          // edge-space size on the device (index space may be a bound)
     int64_t row;
     int64_t nbase;
+    int64_t e_end;
     __device__ void begin(int64_t i0) {
+        e_end = *E;
+        if (i0 >= e_end) return;
         row = row_of(e_off, rows, i0);
         nbase = row_ptr[cp[row]] - e_off[row];
     }
     __device__ bool eval(int64_t i, int32_t& v) {
+        if (i >= e_end) { v = 0; return false; }
         while (i >= e_off[row + 1]) { row++; nbase = row_ptr[cp[row]] - e_off[row]; }
         int32_t x = col[nbase + i];
         v = x;
@@ -104,7 +122,7 @@ struct TopDownF {
         if (hit) atomicOr(&reached[x >> 5], 1u << (x & 31));
         return hit;
     }
-    __device__ int64_t tag(int64_t i) const { return (i == e_off[row]) ? row : -1; }
+    __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? row : -1; }
     __device__ void at(int64_t r, int64_t rank) const { t_off[r] = rank; }
 };
 
@@ -120,20 +138,25 @@ struct NonTreeF {
     const uint32_t* alive;     // bitmap of C(u_i)
     const uint32_t* rank;      // prefix popcounts of alive
     int64_t* n_off;
+    const int64_t* E;
     int64_t row;
     int64_t nbase;
+    int64_t e_end;
     __device__ void begin(int64_t i0) {
+        e_end = *E;
+        if (i0 >= e_end) return;
         row = row_of(e_off, rows, i0);
         nbase = row_ptr[cj[row]] - e_off[row];
     }
     __device__ bool eval(int64_t i, uint32_t& v) {
+        if (i >= e_end) { v = 0; return false; }
         while (i >= e_off[row + 1]) { row++; nbase = row_ptr[cj[row]] - e_off[row]; }
         int32_t x = col[nbase + i];
         uint32_t w = alive[x >> 5], bit = 1u << (x & 31);
         v = rank[x >> 5] + __popc(w & (bit - 1));
         return (w & bit) != 0;
     }
-    __device__ int64_t tag(int64_t i) const { return (i == e_off[row]) ? row : -1; }
+    __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? row : -1; }
     __device__ void at(int64_t r, int64_t rank_) const { n_off[r] = rank_; }
 };
 
@@ -192,6 +215,31 @@ __global__ void k_count_alive(const int64_t* __restrict__ off, const int32_t* __
     }
 }
 
+__global__ void k_set_bits_n(const int32_t* __restrict__ ids, const int64_t* __restrict__ n, int64_t cap,
+                             uint32_t* __restrict__ bits) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cap && i < *n) atomicOr(&bits[ids[i] >> 5], 1u << (ids[i] & 31));
+}
+
+__global__ void k_count_alive_n(const int64_t* __restrict__ off, const int32_t* __restrict__ list,
+                                const int64_t* __restrict__ nrows, const uint32_t* __restrict__ alive,
+                                int64_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    int64_t rows = *nrows;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < rows; r += nw) {
+        int64_t lo = off[r], hi = off[r + 1];
+        int64_t c = 0;
+        for (int64_t e = lo + lane; e < hi; e += 32) {
+            int32_t x = list[e];
+            c += (alive[x >> 5] >> (x & 31)) & 1u;
+        }
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) cnt[r] = c;
+    }
+}
+
 struct ChildCounts {
     const int64_t* cnt[kMaxK];
     int nch;
@@ -204,6 +252,47 @@ __global__ void k_valid_rows(ChildCounts cc, int64_t rows, uint8_t* __restrict__
     for (int c = 0; c < cc.nch; c++) ok &= (cc.cnt[c][r] > 0) ? 1 : 0;
     valid[r] = ok;
     vflag[r] = ok;
+}
+
+// as k_valid_rows, for *nrows live rows of a buffer of `cap` rows (the rest invalid)
+__global__ void k_valid_rows_n(ChildCounts cc, const int64_t* __restrict__ nrows, int64_t cap,
+                               uint8_t* __restrict__ valid, int64_t* __restrict__ vflag) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= cap) return;
+    uint8_t ok = r < *nrows ? 1 : 0;
+    for (int c = 0; c < cc.nch && ok; c++) ok &= (cc.cnt[c][r] > 0) ? 1 : 0;
+    valid[r] = ok;
+    vflag[r] = ok;
+}
+
+__global__ void k_write_alive_n(const int64_t* __restrict__ off, const int32_t* __restrict__ list,
+                                const int64_t* __restrict__ nrows, const uint8_t* __restrict__ valid,
+                                const int64_t* __restrict__ newrow, const uint32_t* __restrict__ alive,
+                                const uint32_t* __restrict__ rank, const int64_t* __restrict__ new_off,
+                                uint32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    int64_t rows = *nrows;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < rows; r += nw) {
+        if (!valid[r]) continue;
+        int64_t lo = off[r], hi = off[r + 1];
+        int64_t dst = new_off[newrow[r]];
+        for (int64_t base = lo; base < hi; base += 32) {
+            int64_t e = base + lane;
+            bool ok = false;
+            uint32_t v = 0;
+            if (e < hi) {
+                int32_t x = list[e];
+                uint32_t wd = alive[x >> 5], bit = 1u << (x & 31);
+                ok = (wd & bit) != 0;
+                v = rank[x >> 5] + __popc(wd & (bit - 1));
+            }
+            uint32_t m = __ballot_sync(0xffffffffu, ok);
+            if (ok) out[dst + __popc(m & lanemask_lt())] = v;
+            dst += __popc(m);
+        }
+    }
 }
 
 __global__ void k_gather_counts(const int64_t* __restrict__ cnt, const uint8_t* __restrict__ valid,
@@ -376,6 +465,10 @@ int validate_query(const fast_query_desc* q, int A[kMaxK][kMaxK], int* dq) {
     return FAST_OK;
 }
 
+// Lists whose upper bound exceeds this many entries are sized exactly (one
+// host round trip) instead of by the bound.
+constexpr int64_t kBoundedListCap = 64ll << 20;
+
 int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* cfg_in, cudaStream_t s,
               fast_cst** out) {
     if (!out) return set_error(FAST_ERR_INVALID, "fast_build_cst: out is NULL");
@@ -395,20 +488,35 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
 
     const int64_t n = g->n;
     const int64_t nw = n / 32 + 1;
-    // temporaries
+    // Sizes live on the device (cnt block); buffers are sized by host-side
+    // bounds: a candidate set by its label bucket, a list set by the degree
+    // sum of the parent's label bucket.
     int32_t* td_list[kMaxK] = {nullptr};    // top-down lists (data-vertex ids)
     int64_t* td_off[kMaxK] = {nullptr};
     int32_t* td_cand[kMaxK] = {nullptr};    // top-down candidate sets
-    int64_t td_n[kMaxK] = {0};
+    int64_t cap_c[kMaxK] = {0};             // bound on |C(u)|
+    int64_t cap_l[kMaxK] = {0};             // bound on the entries of the tree lists into u
     Bits bits[kMaxK];
     int64_t* e_off = nullptr;
-    int64_t* dev_i64 = nullptr;
     unsigned long long* cnt_d = nullptr;
     int32_t* dq_d = nullptr;
     int64_t* lo_d = nullptr;
+    // device sizes: [0,k) |C_td(u)|, [k,2k) |C(u)|, [2k,3k) tree-list entries into u,
+    // [3k, 3k+nt) non-tree entries, then scratch words
+    int64_t* sz = nullptr;
+    const int kSzWords = 3 * kMaxK + kMaxNT + 4;
     int rc = FAST_OK;
 
+    auto bucket = [&](int32_t l) -> int64_t {
+        return (l >= 0 && l < g->num_labels) ? g->lab_ptr_host[l + 1] - g->lab_ptr_host[l] : 0;
+    };
+    auto degsum = [&](int32_t l) -> int64_t {
+        return (l >= 0 && l < g->num_labels) ? g->lab_degsum_host[l] : 0;
+    };
+
     do {
+        rc = dalloc(&sz, kSzWords, s); if (rc) break;
+        cudaMemsetAsync(sz, 0, kSzWords * sizeof(int64_t), s);
         // ---------------------------------------------------- filter counts
         int64_t lo[kMaxK], hi[kMaxK], c0[kMaxK];
         int64_t maxb = 1;
@@ -417,6 +525,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
             if (l < g->num_labels) { lo[u] = g->lab_ptr_host[l]; hi[u] = g->lab_ptr_host[l + 1]; }
             else { lo[u] = hi[u] = 0; }
             maxb = std::max<int64_t>(maxb, hi[u] - lo[u]);
+            cap_c[u] = bucket(l);
         }
         rc = dalloc(&cnt_d, k, s); if (rc) break;
         rc = dalloc(&dq_d, k, s); if (rc) break;
@@ -449,44 +558,53 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
                     if (A[u][w] && !seen[w]) { seen[w] = 1; c->parent[w] = u; c->bfs[qt++] = w; }
             }
         }
+        cap_c[r] = c0[r];
 
         // ------------------------------------------------ C(root) = C0(root)
+        rc = dalloc(&td_cand[r], cap_c[r], s); if (rc) break;
         {
             FilterF f{g->lab_vtx + lo[r], g->key, dq[r]};
-            rc = compact_alloc(f, hi[r] - lo[r], &td_cand[r], &td_n[r], s); if (rc) break;
+            rc = compact(f, hi[r] - lo[r], td_cand[r], sz + r, s); if (rc) break;
         }
 
         // ----------------------------------------------------- top-down
         for (int t = 1; t < k && rc == FAST_OK; t++) {
             int u = c->bfs[t], p = c->parent[u];
-            int64_t rows = td_n[p];
+            int64_t rows = cap_c[p];                          // bound on |C_td(p)|
+            int64_t* n_p = sz + p;                            // |C_td(p)| on the device
             rc = dalloc(&e_off, rows + 1, s); if (rc) break;
-            if (rows > 0) { k_cand_degree<<<grid_for(rows, 256), 256, 0, s>>>(td_cand[p], rows, g->row_ptr, e_off); note_launch(); }
+            if (rows > 0) { k_cand_degree_n<<<grid_for(rows, 256), 256, 0, s>>>(td_cand[p], n_p, rows, g->row_ptr, e_off); note_launch(); }
             rc = scan_exclusive<int64_t>(e_off, e_off, rows, e_off + rows, s); if (rc) break;
-            int64_t E = 0;
-            if (cudaMemcpyAsync(&E, e_off + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "edge space size"); break; }
+            int64_t E = degsum(q->labels[p]);                 // bound on the edge space
+            if (E > kBoundedListCap) {                        // too loose: size it exactly
+                if (cudaMemcpyAsync(&E, e_off + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "edge space size"); break; }
+            }
+            cap_l[u] = E;
             rc = dalloc(&bits[u].alive, nw, s); if (rc) break;
             cudaMemsetAsync(bits[u].alive, 0, nw * sizeof(uint32_t), s);
             rc = dalloc(&td_off[u], rows + 1, s); if (rc) break;
+            rc = dalloc(&td_list[u], E, s); if (rc) break;
             TopDownF f{};
             f.e_off = e_off; f.rows = rows; f.cp = td_cand[p]; f.row_ptr = g->row_ptr; f.col = g->col; f.key = g->key;
             f.want_key_hi = q->labels[u]; f.want_dq = dq[u]; f.reached = bits[u].alive; f.t_off = td_off[u];
-            int64_t kept = 0;
-            rc = compact_alloc(f, E, &td_list[u], &kept, s); if (rc) break;
-            if (cudaMemcpyAsync(td_off[u] + rows, &kept, sizeof(int64_t), cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "offset tail"); break; }
+            f.E = e_off + rows;
+            int64_t* kept = sz + 3 * kMaxK + kMaxNT;          // scratch word
+            rc = compact(f, E, td_list[u], kept, s); if (rc) break;
+            k_set_tail<<<1, 1, 0, s>>>(td_off[u], n_p, kept);
+            note_launch();
             dfree(e_off, s);
+            rc = dalloc(&td_cand[u], cap_c[u], s); if (rc) break;
             BitsF bf{bits[u].alive};
-            rc = compact_alloc(bf, n, &td_cand[u], &td_n[u], s); if (rc) break;
-            // (a pageable-source async copy has consumed `kept` on return;
-            //  the bitmap is rebuilt from the refined set during bottom-up)
+            rc = compact(bf, n, td_cand[u], sz + u, s); if (rc) break;
         }
         if (rc) break;
 
         // ---------------------------------------------------- bottom-up
         for (int t = k - 1; t >= 0 && rc == FAST_OK; t--) {
             int u = c->bfs[t];
-            int64_t rows = td_n[u];
+            int64_t rows = cap_c[u];
+            int64_t* n_u = sz + u;
             int ch[kMaxK], nch = 0;
             for (int w = 0; w < k; w++) if (c->parent[w] == u) ch[nch++] = w;
             int64_t* cnt[kMaxK] = {nullptr};
@@ -499,7 +617,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
                     int w = ch[i];
                     rc = dalloc(&cnt[i], rows, s); if (rc) break;
                     if (rows > 0) {
-                        k_count_alive<<<warp_grid(rows), 256, 0, s>>>(td_off[w], td_list[w], rows, bits[w].alive, cnt[i]);
+                        k_count_alive_n<<<warp_grid(rows), 256, 0, s>>>(td_off[w], td_list[w], n_u, bits[w].alive, cnt[i]);
                         note_launch();
                     }
                     cc.cnt[i] = cnt[i];
@@ -507,24 +625,23 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
                 if (rc) break;
                 rc = dalloc(&valid, rows, s); if (rc) break;
                 rc = dalloc(&newrow, rows + 1, s); if (rc) break;
-                if (rows > 0) { k_valid_rows<<<grid_for(rows, 256), 256, 0, s>>>(cc, rows, valid, newrow); note_launch(); }
+                if (rows > 0) { k_valid_rows_n<<<grid_for(rows, 256), 256, 0, s>>>(cc, n_u, rows, valid, newrow); note_launch(); }
                 rc = scan_exclusive<int64_t>(newrow, newrow, rows, newrow + rows, s); if (rc) break;
+                rc = dalloc(&c->cand[u], rows, s); if (rc) break;
                 KeepRowsF kf{td_cand[u], valid};
-                rc = compact_alloc(kf, rows, &c->cand[u], &c->ncand[u], s); if (rc) break;
-                int64_t nu = c->ncand[u];
+                rc = compact(kf, rows, c->cand[u], sz + kMaxK + u, s); if (rc) break;
                 for (int i = 0; i < nch && rc == FAST_OK; i++) {
                     int w = ch[i];
-                    rc = dalloc(&c->t_off[w], nu + 1, s); if (rc) break;
+                    rc = dalloc(&c->t_off[w], rows + 1, s); if (rc) break;
+                    cudaMemsetAsync(c->t_off[w], 0, (rows + 1) * sizeof(int64_t), s);
                     if (rows > 0) { k_gather_counts<<<grid_for(rows, 256), 256, 0, s>>>(cnt[i], valid, newrow, rows, c->t_off[w]); note_launch(); }
-                    rc = scan_exclusive<int64_t>(c->t_off[w], c->t_off[w], nu, c->t_off[w] + nu, s); if (rc) break;
-                    int64_t ent = 0;
-                    if (cudaMemcpyAsync(&ent, c->t_off[w] + nu, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                        cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "list size"); break; }
-                    c->t_entries[w] = ent;
-                    rc = dalloc(&c->t_idx[w], ent, s); if (rc) break;
+                    rc = scan_exclusive<int64_t>(c->t_off[w], c->t_off[w], rows, c->t_off[w] + rows, s); if (rc) break;
+                    k_copy_i64<<<1, 1, 0, s>>>(sz + 2 * kMaxK + w, c->t_off[w] + rows);
+                    note_launch();
+                    rc = dalloc(&c->t_idx[w], cap_l[w], s); if (rc) break;
                     if (rows > 0) {
-                        k_write_alive<<<warp_grid(rows), 256, 0, s>>>(td_off[w], td_list[w], rows, valid, newrow,
-                                                                      bits[w].alive, bits[w].rank, c->t_off[w], c->t_idx[w]);
+                        k_write_alive_n<<<warp_grid(rows), 256, 0, s>>>(td_off[w], td_list[w], n_u, valid, newrow,
+                                                                        bits[w].alive, bits[w].rank, c->t_off[w], c->t_idx[w]);
                         note_launch();
                     }
                     dfree(td_list[w], s); dfree(td_off[w], s);
@@ -533,7 +650,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
                 // bitmap + rank of the refined C(u)
                 if (!bits[u].alive) { rc = dalloc(&bits[u].alive, nw, s); if (rc) break; }
                 cudaMemsetAsync(bits[u].alive, 0, nw * sizeof(uint32_t), s);
-                if (nu > 0) { k_set_bits<<<grid_for(nu, 256), 256, 0, s>>>(c->cand[u], nu, bits[u].alive); note_launch(); }
+                if (rows > 0) { k_set_bits_n<<<grid_for(rows, 256), 256, 0, s>>>(c->cand[u], sz + kMaxK + u, rows, bits[u].alive); note_launch(); }
                 rc = dalloc(&bits[u].rank, nw, s); if (rc) break;
                 k_popc_words<<<grid_for(nw, 256), 256, 0, s>>>(bits[u].alive, nw, bits[u].rank);
                 note_launch();
@@ -544,6 +661,13 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
             dfree(td_cand[u], s);
         }
         if (rc) break;
+        // one round trip: the refined candidate counts decide the matching order
+        {
+            int64_t hs[kMaxK];
+            if (cudaMemcpyAsync(hs, sz + kMaxK, k * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "candidate counts"); break; }
+            for (int u = 0; u < k; u++) c->ncand[u] = hs[u];
+        }
 
         // ------------------------------------------------ matching order
         {
@@ -575,17 +699,21 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
                 rc = dalloc(&e_off, rows + 1, s); if (rc) break;
                 if (rows > 0) { k_cand_degree<<<grid_for(rows, 256), 256, 0, s>>>(c->cand[uj], rows, g->row_ptr, e_off); note_launch(); }
                 rc = scan_exclusive<int64_t>(e_off, e_off, rows, e_off + rows, s); if (rc) break;
-                int64_t E = 0;
-                if (cudaMemcpyAsync(&E, e_off + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                    cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "edge space size"); break; }
+                int64_t E = degsum(q->labels[uj]);
+                if (E > kBoundedListCap) {
+                    if (cudaMemcpyAsync(&E, e_off + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "edge space size"); break; }
+                }
                 rc = dalloc(&c->n_off[e], rows + 1, s); if (rc) break;
+                rc = dalloc(&c->n_idx[e], E, s); if (rc) break;
                 NonTreeF f{};
                 f.e_off = e_off; f.rows = rows; f.cj = c->cand[uj]; f.row_ptr = g->row_ptr; f.col = g->col;
                 f.alive = bits[ui].alive; f.rank = bits[ui].rank; f.n_off = c->n_off[e];
-                int64_t kept = 0;
-                rc = compact_alloc(f, E, &c->n_idx[e], &kept, s); if (rc) break;
-                c->n_entries[e] = kept;
-                if (cudaMemcpyAsync(c->n_off[e] + rows, &c->n_entries[e], sizeof(int64_t), cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "offset tail"); break; }
+                f.E = e_off + rows;
+                int64_t* kept = sz + 3 * kMaxK + e;
+                rc = compact(f, E, c->n_idx[e], kept, s); if (rc) break;
+                k_set_tail_at<<<1, 1, 0, s>>>(c->n_off[e], rows, kept);
+                note_launch();
                 dfree(e_off, s);
             }
         }
@@ -621,17 +749,18 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         }
         if (rc) break;
         {
-            uint64_t* w_d = nullptr;
-            rc = dalloc(&w_d, 2, s); if (rc) break;
+            // the last round trip: W and every list size
+            uint64_t* w_d = (uint64_t*)(sz + 3 * kMaxK + kMaxNT + 1);
             k_total_w<<<1, 1024, 0, s>>>(c->cval[r], c->cvalf[r], c->ncand[r], w_d, (double*)(w_d + 1));
             note_launch();
-            uint64_t hw[2];
-            cudaError_t e1 = cudaMemcpyAsync(hw, w_d, sizeof(hw), cudaMemcpyDeviceToHost, s);
+            int64_t hs[kSzWords];
+            cudaError_t e1 = cudaMemcpyAsync(hs, sz, sizeof(hs), cudaMemcpyDeviceToHost, s);
             cudaError_t e2 = cudaStreamSynchronize(s);
-            dfree(w_d, s);
             if (e1 != cudaSuccess || e2 != cudaSuccess) { rc = cuda_status(e2 != cudaSuccess ? e2 : e1, "fast_build_cst", __FILE__, __LINE__); break; }
-            c->W = hw[0];
-            memcpy(&c->Wf, &hw[1], sizeof(double));
+            for (int u = 0; u < k; u++) c->t_entries[u] = c->parent[u] < 0 ? 0 : hs[2 * kMaxK + u];
+            for (int e = 0; e < c->nnt; e++) c->n_entries[e] = hs[3 * kMaxK + e];
+            memcpy(&c->W, &hs[3 * kMaxK + kMaxNT + 1], sizeof(uint64_t));
+            memcpy(&c->Wf, &hs[3 * kMaxK + kMaxNT + 2], sizeof(double));
         }
     } while (0);
 
@@ -639,7 +768,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         dfree(td_list[u], s); dfree(td_off[u], s); dfree(td_cand[u], s);
         dfree(bits[u].alive, s); dfree(bits[u].rank, s);
     }
-    dfree(e_off, s); dfree(dev_i64, s); dfree(cnt_d, s); dfree(dq_d, s); dfree(lo_d, s);
+    dfree(e_off, s); dfree(cnt_d, s); dfree(dq_d, s); dfree(lo_d, s); dfree(sz, s);
     if (rc != FAST_OK) {
         cst_release(c);
         return rc;

@@ -134,6 +134,12 @@ __global__ void k_label_bounds(const uint64_t* __restrict__ lkeys, int64_t n, in
     if (p < n) lab_vtx[p] = (int32_t)(lkeys[p] & 0xFFFFFFFFu);
 }
 
+__global__ void k_label_degsum(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ lab, int64_t n,
+                               unsigned long long* __restrict__ sum) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) atomicAdd(&sum[lab[v]], (unsigned long long)(row_ptr[v + 1] - row_ptr[v]));
+}
+
 void graph_release(fast_graph* g, cudaStream_t s) {
     if (!g) return;
     dfree(g->row_ptr, s); dfree(g->col, s); dfree(g->label, s); dfree(g->key, s);
@@ -214,6 +220,19 @@ int load_graph(int64_t n, int64_t m, const int32_t* edges, const int32_t* labels
         rc = dalloc(&g->lab_vtx, n, s); if (rc) break;
         k_label_bounds<<<(unsigned)ceil_div(n + 1, 256), 256, 0, s>>>(lkeys, n, g->num_labels, g->lab_ptr, g->lab_vtx);
         note_launch();
+        {
+            unsigned long long* ds = nullptr;
+            rc = dalloc(&ds, g->num_labels, s); if (rc) break;
+            cudaMemsetAsync(ds, 0, g->num_labels * sizeof(unsigned long long), s);
+            k_label_degsum<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(g->row_ptr, g->label, n, ds);
+            note_launch();
+            g->lab_degsum_host.resize(g->num_labels);
+            cudaError_t e = cudaMemcpyAsync(g->lab_degsum_host.data(), ds, g->num_labels * sizeof(int64_t),
+                                            cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            dfree(ds, s);
+            if (e != cudaSuccess) { rc = cuda_status(e, "label degree sums", __FILE__, __LINE__); break; }
+        }
         g->lab_ptr_host.resize(g->num_labels + 1);
         unsigned long long md = 0;
         if (cudaMemcpyAsync(g->lab_ptr_host.data(), g->lab_ptr, (g->num_labels + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -23,6 +23,7 @@ struct fast_graph {
     int64_t* lab_ptr = nullptr;   // [num_labels+1]
     int32_t* lab_vtx = nullptr;   // [n] vertices grouped by label, ascending id
     std::vector<int64_t> lab_ptr_host;
+    std::vector<int64_t> lab_degsum_host;   // per label: sum of degrees (bounds CST list sizes)
 };
 
 // Candidate search tree (Sec. IV-A) of one query.  Indexed by query vertex

@@ -52,6 +52,7 @@ EventPair& match_events() {
 
 struct MatchPlan {
     int k;
+    int warp_words;                   // shared words per warp (survivors, m, data ids, cursors)
     int order[kMaxK];                 // position -> query vertex
     int par[kMaxK];                   // position -> parent position
     uint32_t same_lab[kMaxK];         // earlier positions with the same label
@@ -65,20 +66,25 @@ struct MatchPlan {
 };
 
 enum : int { kStatusTimeout = 1, kStatusOverflow = 2, kStatusLimit = 4, kStatusStall = 8 };
+// shared words per warp: survivors [32 depths][32], m and data vertex per
+// position, then one 8-byte cursor per non-tree edge of the query
+constexpr int kWarpBaseWords = kMaxK * 32 + 2 * kMaxK;
 constexpr uint32_t kDonated = 1;
 constexpr unsigned long long kStallNs = 60ull * 1000 * 1000 * 1000;   // a claimed slot never published
 constexpr unsigned long long kIdleNs = 5ull * 1000 * 1000 * 1000;     // an idle warp gives up waiting
 
 struct MatchOut {
     unsigned long long* next_chunk;
-    unsigned long long* total;
+    unsigned long long* total;        // per query (one entry unless batched)
+    int* qstop;                       // per query: limit reached
+    int nq;
     unsigned long long* emb_slot;
     int* status;
     uint64_t* chunk_counts;           // nullable (static chunks; no donation then)
     uint32_t* emb;                    // nullable
     uint64_t emb_cap;                 // rows that may be written
     unsigned long long* stats;        // nullable: [k] partial results per depth
-    unsigned long long* bytes;        // algorithmic bytes read
+    unsigned long long* bytes;        // bytes the search requested
     const unsigned long long* deadline;  // device word: %globaltimer limit, 0 = none
     uint64_t limit;                   // 0 = enumerate everything
     Chunk* dq;                        // donated runs
@@ -94,13 +100,95 @@ __global__ void k_set_deadline(unsigned long long* d, unsigned long long budget_
     *d = budget_ns ? global_timer_ns() + budget_ns : 0ull;
 }
 
-__device__ __forceinline__ bool bsearch_u32(const uint32_t* __restrict__ a, int64_t lo, int64_t hi, uint32_t x) {
+__global__ void k_copy_word(unsigned long long* dst, const int64_t* src) { *dst = (unsigned long long)*src; }
+
+// membership of x in the sorted a[lo, hi); *probes counts the entries read
+__device__ __forceinline__ bool bsearch_u32(const uint32_t* __restrict__ a, int64_t lo, int64_t hi, uint32_t x,
+                                            unsigned long long* probes) {
     int64_t end = hi;
+    unsigned long long p = 0;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
+        p++;
         if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
     }
-    return lo < end && __ldg(a + lo) == x;
+    bool hit = false;
+    if (lo < end) { p++; hit = __ldg(a + lo) == x; }
+    *probes += p;
+    return hit;
+}
+
+// Warp-cooperative membership test.  Each lane with `act` holds a candidate
+// c; over those lanes the candidates ascend with the lane index (they come
+// from one sorted tree list).  L[lo, hi) is a sorted non-tree list and *pos a
+// cursor into it that never passes the lower bound of any candidate still to
+// come, so successive 32-entry segments of the tree list walk the non-tree
+// list once, merge-style:
+//   - load the tile L[pos, pos+32) with one coalesced read;
+//   - every pending lane whose candidate is <= the tile's last entry finds
+//     its lower bound inside the tile by a 5-step shuffle search;
+//   - if the smallest pending candidate lies beyond the tile, gallop: lanes
+//     probe pos + 32*2^i in one round, then 33-way refinement rounds, each a
+//     single parallel read, until a 32-entry window holds its lower bound.
+// Returns whether this lane's candidate is in the list; *lb counts the
+// entries this lane read (4 B each).
+__device__ __forceinline__ bool warp_member(const uint32_t* __restrict__ L, int64_t lo, int64_t hi, int64_t* pos,
+                                            uint32_t c, bool act, unsigned long long* lb) {
+    const int lane = threadIdx.x & 31;
+    bool found = false;
+    uint32_t pend = __ballot_sync(0xffffffffu, act);
+    int64_t p0 = *pos < lo ? lo : *pos;
+    int64_t last = p0;
+    while (pend) {
+        if (p0 >= hi) break;                               // list exhausted: the rest are absent
+        int tl = __ffs(pend) - 1;
+        uint32_t ct = __shfl_sync(0xffffffffu, c, tl);     // smallest pending candidate
+        uint32_t v = 0xFFFFFFFFu;
+        if (p0 + lane < hi) { v = __ldg(L + p0 + lane); *lb += 4; }
+        uint32_t tmax = __shfl_sync(0xffffffffu, v, 31);
+        if (tmax < ct) {
+            // gallop: the lower bound of ct lies past this (full) tile
+            int64_t a = p0 + 32;                            // first index that may hold it
+            int64_t probe = p0 + 31 + ((int64_t)32 << (lane < 25 ? lane : 25));
+            if (probe > hi - 1) probe = hi - 1;
+            uint32_t pv = __ldg(L + probe);
+            *lb += 4;
+            uint32_t ge = __ballot_sync(0xffffffffu, pv >= ct);
+            if (!ge) { p0 = hi; break; }                    // everything left is smaller: all absent
+            int f = __ffs(ge) - 1;
+            int64_t b = __shfl_sync(0xffffffffu, probe, f);            // L[b] >= ct
+            if (f > 0) a = __shfl_sync(0xffffffffu, probe, f - 1) + 1; // L[a-1] < ct
+            while (b - a > 31) {                            // 33-way refinement of [a, b]
+                int64_t span = b - a + 1;
+                int64_t q = a + ((int64_t)(lane + 1) * span) / 33;
+                uint32_t qv = __ldg(L + q);
+                *lb += 4;
+                uint32_t g2 = __ballot_sync(0xffffffffu, qv >= ct);
+                int f2 = g2 ? __ffs(g2) - 1 : 32;
+                int64_t nb = f2 < 32 ? __shfl_sync(0xffffffffu, q, f2 < 32 ? f2 : 0) : b;
+                int64_t na = f2 > 0 ? __shfl_sync(0xffffffffu, q, f2 > 0 ? f2 - 1 : 0) + 1 : a;
+                a = na;
+                b = nb;
+            }
+            p0 = a;
+            continue;
+        }
+        // resolve every pending lane whose candidate is within this tile
+        bool mine = ((pend >> lane) & 1u) && c <= tmax;
+        int q = 0;
+#pragma unroll
+        for (int st = 16; st; st >>= 1) {
+            uint32_t w = __shfl_sync(0xffffffffu, v, q + st - 1);
+            if (w < c) q += st;
+        }
+        uint32_t w = __shfl_sync(0xffffffffu, v, q);
+        if (mine) found = (w == c);
+        pend &= ~__ballot_sync(0xffffffffu, mine);
+        last = p0;
+        p0 += 32;
+    }
+    *pos = last;
+    return found;
 }
 
 __device__ __forceinline__ int vload(const int* p) { return *(volatile const int*)p; }
@@ -108,12 +196,15 @@ __device__ __forceinline__ unsigned long long vload(const unsigned long long* p)
     return *(volatile const unsigned long long*)p;
 }
 
-// lane 0: add a local count to the total; flag the limit once it is reached
-__device__ __forceinline__ void flush_count(const MatchOut& O, unsigned long long& local) {
+// lane 0: add a local count to query q's total; flag the limit once reached
+__device__ __forceinline__ void flush_count(const MatchOut& O, uint32_t q, unsigned long long& local) {
     if (!local) return;
-    unsigned long long old = atomicAdd(O.total, local);
+    unsigned long long old = atomicAdd(&O.total[q], local);
     if (old + local < old) atomicOr(O.status, kStatusOverflow);
-    if (O.limit && old + local >= O.limit) atomicOr(O.status, kStatusLimit);
+    if (O.limit && old + local >= O.limit) {
+        O.qstop[q] = 1;
+        if (O.nq == 1) atomicOr(O.status, kStatusLimit);
+    }
     local = 0;
 }
 
@@ -159,19 +250,25 @@ __device__ int acquire(const MatchOut& O, int64_t nchunks, unsigned long long de
     return kind;
 }
 
-template <bool STATS, bool EMIT>
-__global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* __restrict__ chunks, int64_t nchunks,
-                                               MatchOut O) {
+// BATCH: plans[q] per query (chunk flags carry q, nchunks is read from
+// *nchunks_dev); otherwise the single plan P0 and the nchunks argument.
+template <bool STATS, bool EMIT, bool BATCH>
+__global__ void __launch_bounds__(256) k_match(const __grid_constant__ MatchPlan P0,
+                                               const MatchPlan* __restrict__ plans,
+                                               const Chunk* __restrict__ chunks, int64_t nchunks,
+                                               const int64_t* __restrict__ nchunks_dev, MatchOut O) {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint32_t* sbuf = smem + (size_t)warp * (kMaxK * 32 + 2 * kMaxK);   // [depth][32]
+    if (BATCH) nchunks = *nchunks_dev;
+    const int warp_words = BATCH ? plans[0].warp_words : P0.warp_words;   // one stride for all queries
+    uint32_t* sbuf = smem + (size_t)warp * warp_words;                   // [depth][32]
     uint32_t* sm = sbuf + kMaxK * 32;                                   // m[position]
     int32_t* sg = (int32_t*)(sm + kMaxK);                               // data vertex per position
-    const int k = P.k;
+    int64_t* ncur = (int64_t*)(sg + kMaxK);                              // per non-tree edge: list cursor
     unsigned long long iter = 0;
     const unsigned long long deadline = *O.deadline;
-    unsigned long long bytes = 0;          // lane 0
+    unsigned long long lb = 0;             // this lane's bytes requested (entries of 4 B, offsets of 8 B)
     unsigned long long local = 0;          // lane 0: count not yet flushed
 
     for (;;) {
@@ -181,10 +278,36 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
         kind = __shfl_sync(0xffffffffu, kind, 0);
         ci = __shfl_sync(0xffffffffu, ci, 0);
         if (kind == 0) break;
-        const Chunk& ch = kind == 1 ? chunks[ci] : O.dq[ci];
-        const int j = ch.j;
-        const bool donated = (ch.pad & kDonated) != 0;
-        uint32_t m_reg = lane < j ? ch.prefix[lane] : 0u;      // lane p: candidate index of position p
+        // the item's fields, read once.  A donated run was written by another
+        // warp during this launch: read it from L2 (ld.global.cg), never from
+        // an L1 line that may hold an older copy of its bytes.
+        const Chunk* chp = kind == 1 ? chunks + ci : O.dq + ci;
+        int j;
+        uint32_t ch_a, ch_b, ch_pad, ch_pre;
+        if (kind == 1) {
+            j = chp->j; ch_a = chp->a; ch_b = chp->b; ch_pad = chp->pad;
+            ch_pre = lane < j ? chp->prefix[lane] : 0u;
+        } else {
+            j = __ldcg(&chp->j); ch_a = __ldcg(&chp->a); ch_b = __ldcg(&chp->b); ch_pad = __ldcg(&chp->pad);
+            ch_pre = lane < j ? __ldcg(&chp->prefix[lane]) : 0u;
+        }
+        const uint32_t q = BATCH ? (ch_pad >> 8) : 0u;
+        const MatchPlan& P = BATCH ? plans[q] : P0;
+        const int k = P.k;
+        if (BATCH) {
+            // this query already reached its limit?  One lane reads the flag and
+            // broadcasts it: another warp may set it at any moment, and lanes
+            // reading it separately could take different branches and then
+            // never meet at the warp-wide operations that follow.
+            int qs = 0;
+            if (lane == 0) qs = *(volatile int*)&O.qstop[q];
+            if (__shfl_sync(0xffffffffu, qs, 0)) {
+                if (lane == 0) atomicAdd(O.outstanding, ~0ull);
+                __syncwarp();
+                continue;
+            }
+        }
+        uint32_t m_reg = ch_pre;                               // lane p: candidate index of position p
         int32_t g_reg = -1;                                    // lane p: data vertex of position p
         if (lane < j) g_reg = P.cand[lane][m_reg];
         sm[lane] = m_reg;
@@ -192,13 +315,14 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
         __syncwarp();
         // ---- the prefix must itself be a partial embedding (non-tree edges, injectivity)
         bool ok_prefix = true;
-        unsigned long long pb = 0;
+        if (lane < j) lb += 4 + 4;                              // prefix entry + its data vertex
         if (lane < j && lane > 0) {
             for (int e = P.nt_begin[lane]; e < P.nt_begin[lane + 1]; e++) {
                 uint32_t mf = sm[P.nt_from[e]];
                 int64_t lo = P.n_off[e][mf], hi = P.n_off[e][mf + 1];
-                pb += 8 + 4 * (hi - lo);
-                if (!bsearch_u32(P.n_idx[e], lo, hi, m_reg)) ok_prefix = false;
+                unsigned long long pr = 0;
+                if (!bsearch_u32(P.n_idx[e], lo, hi, m_reg, &pr)) ok_prefix = false;
+                lb += 16 + 4 * pr;
             }
             uint32_t sl = P.same_lab[lane];
             while (sl) {
@@ -207,8 +331,6 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
                 if (sg[p] == g_reg) ok_prefix = false;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) pb += __shfl_xor_sync(0xffffffffu, pb, o);
-        if (lane == 0 && !donated) bytes += pb;
         unsigned long long ccount = 0;         // lane 0: this item's count
         if (__all_sync(0xffffffffu, ok_prefix)) {
             // ---- depth j: the item's run of L_j
@@ -221,27 +343,21 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
                     uint32_t mp = __shfl_sync(0xffffffffu, m_reg, P.par[j]);
                     base = P.t_off[j][mp];
                 }
-                int64_t lo = base + ch.a, hi = base + ch.b;
+                int64_t lo = base + ch_a, hi = base + ch_b;
                 if (lane == d) { seg_next = lo; seg_end = hi; seg_base = base; }
-                if (lane == 0 && !donated) {
-                    if (j == 0) bytes += 4 * (hi - lo);
-                    else {
-                        bytes += 8 + 4 * (hi - lo);
-                        for (int e = P.nt_begin[j]; e < P.nt_begin[j + 1]; e++) {
-                            uint32_t mf = sm[P.nt_from[e]];
-                            bytes += 8 + 4 * (P.n_off[e][mf + 1] - P.n_off[e][mf]);
-                        }
-                    }
-                }
+                if (lane == 0) lb += (j > 0 ? 16 : 0) + 16ull * (P.nt_begin[j + 1] - P.nt_begin[j]);
+                for (int e = P.nt_begin[j] + lane; e < P.nt_begin[j + 1]; e += 32) ncur[e] = 0;
+                __syncwarp();
             }
             for (;;) {
                 ++iter;
                 if ((iter & 255) == 0) {
                     int stop = 0;
                     if (lane == 0) {
-                        flush_count(O, local);
+                        flush_count(O, q, local);
                         if (deadline && global_timer_ns() > deadline) atomicOr(O.status, kStatusTimeout);
                         stop = vload(O.status) & (kStatusTimeout | kStatusLimit | kStatusStall);
+                        if (BATCH && *(volatile int*)&O.qstop[q]) stop = 1;
                     }
                     if (__shfl_sync(0xffffffffu, stop, 0)) break;
                 }
@@ -270,7 +386,7 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
                                     dst->j = dd;
                                     dst->a = (uint32_t)(mid - sb_);
                                     dst->b = (uint32_t)(se_ - sb_);
-                                    dst->pad = kDonated;
+                                    dst->pad = kDonated | (q << 8);
                                     dst->w = 0;
                                     dst->id = 0;
                                 }
@@ -289,19 +405,14 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
                 if (cur_d < cnt_d) {
                     // expand the next buffered survivor of depth d
                     uint32_t v = sbuf[d * 32 + cur_d];
-                    if (lane == d) { bcur++; m_reg = v; g_reg = P.cand[d][v]; sm[d] = v; sg[d] = g_reg; }
+                    if (lane == d) { bcur++; m_reg = v; g_reg = P.cand[d][v]; sm[d] = v; sg[d] = g_reg; lb += 4; }
                     d++;
                     uint32_t mp = __shfl_sync(0xffffffffu, m_reg, P.par[d]);
                     int64_t lo = P.t_off[d][mp], hi = P.t_off[d][mp + 1];
                     if (lane == d) { seg_next = lo; seg_end = hi; seg_base = lo; bcnt = 0; bcur = 0; }
+                    if (lane == 0) lb += 16 + 16ull * (P.nt_begin[d + 1] - P.nt_begin[d]);
+                    for (int e = P.nt_begin[d] + lane; e < P.nt_begin[d + 1]; e += 32) ncur[e] = 0;
                     __syncwarp();
-                    if (lane == 0) {
-                        bytes += 8 + 4 * (hi - lo);
-                        for (int e = P.nt_begin[d]; e < P.nt_begin[d + 1]; e++) {
-                            uint32_t mf = sm[P.nt_from[e]];
-                            bytes += 8 + 4 * (P.n_off[e][mf + 1] - P.n_off[e][mf]);
-                        }
-                    }
                     continue;
                 }
                 int64_t sn = __shfl_sync(0xffffffffu, seg_next, d);
@@ -311,18 +422,25 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
                     int64_t idx = sn + lane;
                     bool ok = idx < se;
                     uint32_t cnd = 0;
-                    if (ok) cnd = (d == 0) ? (uint32_t)idx : __ldg(P.t_idx[d] + idx);
+                    if (ok) {
+                        cnd = (d == 0) ? (uint32_t)idx : __ldg(P.t_idx[d] + idx);
+                        if (d > 0) lb += 4;
+                    }
                     // EdgeValidator
                     for (int e = P.nt_begin[d]; e < P.nt_begin[d + 1]; e++) {
                         uint32_t mf = __shfl_sync(0xffffffffu, m_reg, P.nt_from[e]);
                         int64_t lo = P.n_off[e][mf], hi = P.n_off[e][mf + 1];
-                        if (ok) ok = bsearch_u32(P.n_idx[e], lo, hi, cnd);
+                        int64_t cur = lo + ncur[e];
+                        ok = warp_member(P.n_idx[e], lo, hi, &cur, cnd, ok, &lb);
+                        __syncwarp();
+                        if (lane == 0) ncur[e] = cur - lo;
+                        __syncwarp();
                     }
                     // VisitedValidator
                     int32_t gc = -1;
                     uint32_t sl = P.same_lab[d];
                     if (sl || (EMIT && d == k - 1)) {
-                        if (ok) gc = __ldg(P.cand[d] + cnd);
+                        if (ok) { gc = __ldg(P.cand[d] + cnd); lb += 4; }
                         while (sl) {
                             int p = __ffs(sl) - 1;
                             sl &= sl - 1;
@@ -336,12 +454,13 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
                     if (STATS && lane == 0) atomicAdd(&O.stats[d], (unsigned long long)__popc(mask));
                     if (d == k - 1) {
                         if (lane == 0) { local += __popc(mask); ccount += __popc(mask); }
-                        if (EMIT && mask) {
+                        if (EMIT && !BATCH && mask) {
                             unsigned long long base = 0;
                             if (lane == 0) base = atomicAdd(O.emb_slot, (unsigned long long)__popc(mask));
                             base = __shfl_sync(0xffffffffu, base, 0);
                             unsigned long long slot = base + __popc(mask & lanemask_lt());
                             bool wr = ok && slot < O.emb_cap;
+                            if (wr) lb += 4ull * k;
                             for (int p = 0; p < k - 1; p++) {
                                 int32_t gp = __shfl_sync(0xffffffffu, g_reg, p);
                                 if (wr) O.emb[slot * k + P.order[p]] = (uint32_t)gp;
@@ -361,16 +480,14 @@ __global__ void __launch_bounds__(256) k_match(const MatchPlan P, const Chunk* _
             }
         }
         if (lane == 0) {
-            flush_count(O, local);
+            flush_count(O, q, local);
             if (O.chunk_counts && kind == 1) O.chunk_counts[ci] = ccount;
             atomicAdd(O.outstanding, ~0ull);   // -1
         }
         __syncwarp();
     }
-    if (lane == 0) {
-        flush_count(O, local);
-        if (bytes) atomicAdd(O.bytes, bytes);
-    }
+    for (int o = 16; o > 0; o >>= 1) lb += __shfl_xor_sync(0xffffffffu, lb, o);
+    if (lane == 0 && lb) atomicAdd(O.bytes, lb);
 }
 
 MatchPlan make_plan(const fast_cst* c) {
@@ -401,13 +518,38 @@ MatchPlan make_plan(const fast_cst* c) {
         }
     }
     P.nt_begin[k] = e;
+    P.warp_words = kWarpBaseWords + 2 * e;
     return P;
 }
 
-size_t smem_bytes(int warps) { return (size_t)warps * (kMaxK * 32 + 2 * kMaxK) * sizeof(uint32_t); }
+size_t smem_bytes(const MatchPlan& P, int warps) { return (size_t)warps * P.warp_words * sizeof(uint32_t); }
+
+// Opt every matcher variant in to the largest dynamic shared memory any
+// query can ask for (8 warps of a 32-vertex query with all its non-tree
+// cursors), once per device.  The attribute is process-wide: setting it per
+// launch to that launch's size would let a concurrent caller on another
+// thread lower it between someone else's set and launch.
+constexpr size_t kMatcherSmemMax = (size_t)8 * (kWarpBaseWords + 2 * kMaxNT) * sizeof(uint32_t);
+
+int matcher_smem_optin(size_t bytes) {
+    if (bytes > kMatcherSmemMax) return set_error(FAST_ERR_INVALID, "matcher: %zu bytes of shared memory per CTA", bytes);
+    static std::mutex mu;
+    static uint64_t done = 0;                  // bit per device
+    int dev = 0;
+    FAST_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && (done >> dev) & 1) return FAST_OK;
+    const int sz = (int)kMatcherSmemMax;
+    FAST_CUDA(cudaFuncSetAttribute(k_match<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+    FAST_CUDA(cudaFuncSetAttribute(k_match<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+    FAST_CUDA(cudaFuncSetAttribute(k_match<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+    FAST_CUDA(cudaFuncSetAttribute(k_match<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+    if (dev < 64) done |= 1ull << dev;
+    return FAST_OK;
+}
 
 // counter block layout (unsigned long long words)
-enum { kNext = 0, kTotal, kSlot, kStatus, kBytes, kHead, kTail, kOut, kIdle, kDeadline, kStats,
+enum { kNext = 0, kTotal, kSlot, kStatus, kBytes, kHead, kTail, kOut, kIdle, kDeadline, kQStop, kStats,
        kCtrWords = kStats + kMaxK + 1 };
 constexpr uint64_t kQueueCap = 1 << 16;
 
@@ -443,7 +585,9 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
         if (e != cudaSuccess) { dfree(own, s); return cuda_status(e, "fast_match chunk", __FILE__, __LINE__); }
         dchunks = own; nchunks = (int64_t)parts;
     }
-    const bool donate = chunk_counts == nullptr;
+    // per-chunk counts and the counting pass need every run done where it was
+    // scheduled (a donated run re-reads its prefix), so they run without donation
+    const bool donate = chunk_counts == nullptr && stats_out == nullptr;
     unsigned long long* ctr = nullptr;
     Chunk* dq = nullptr;
     uint32_t* dq_ready = nullptr;
@@ -472,6 +616,7 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
         if (donate) cudaMemsetAsync(dq_ready, 0, kQueueCap * sizeof(uint32_t), s);
         MatchOut O;
         O.next_chunk = ctr + kNext; O.total = ctr + kTotal; O.emb_slot = ctr + kSlot; O.status = (int*)(ctr + kStatus);
+        O.qstop = (int*)(ctr + kQStop); O.nq = 1;
         O.chunk_counts = chunk_counts; O.emb = emb_dev; O.emb_cap = emb_cap;
         O.stats = stats_out ? ctr + kStats : nullptr;
         O.bytes = ctr + kBytes;
@@ -485,16 +630,19 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
         if (nchunks > 0) {
             int64_t grid = (int64_t)num_sms() * bps;
             if (!donate) grid = std::max<int64_t>(1, std::min<int64_t>(grid, ceil_div(nchunks, warps)));
-            size_t sh = smem_bytes(warps);
-            EventPair& ev = match_events();
-            if (ev.ok) cudaEventRecord(ev.a, s);
-            if (stats_out) { k_match<true, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, dchunks, nchunks, O); note_launch(); }
-            else if (kemb > 0) { k_match<false, true><<<(unsigned)grid, warps * 32, sh, s>>>(P, dchunks, nchunks, O); note_launch(); }
-            else { k_match<false, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, dchunks, nchunks, O); note_launch(); }
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) rc = cuda_status(e, "matcher launch", __FILE__, __LINE__);
-            if (ev.ok) cudaEventRecord(ev.b, s);
-            timed = ev.ok;
+            size_t sh = smem_bytes(P, warps);
+            rc = matcher_smem_optin(sh);
+            if (rc == FAST_OK) {
+                EventPair& ev = match_events();
+                if (ev.ok) cudaEventRecord(ev.a, s);
+                if (stats_out) { k_match<true, false, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, nullptr, dchunks, nchunks, nullptr, O); note_launch(); }
+                else if (kemb > 0) { k_match<false, true, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, nullptr, dchunks, nchunks, nullptr, O); note_launch(); }
+                else { k_match<false, false, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, nullptr, dchunks, nchunks, nullptr, O); note_launch(); }
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) rc = cuda_status(e, "matcher launch", __FILE__, __LINE__);
+                if (ev.ok) cudaEventRecord(ev.b, s);
+                timed = ev.ok;
+            }
         }
     }
     unsigned long long h[kCtrWords];
@@ -656,6 +804,7 @@ int run_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_c
     MatchPlan P = make_plan(c);
     MatchOut O;
     O.next_chunk = ctr + kNext; O.total = ctr + kTotal; O.emb_slot = ctr + kSlot; O.status = (int*)(ctr + kStatus);
+        O.qstop = (int*)(ctr + kQStop); O.nq = 1;
     O.chunk_counts = nullptr; O.emb = emb_out; O.emb_cap = emb_cap;
     O.stats = nullptr;
     O.bytes = ctr + kBytes;
@@ -668,9 +817,10 @@ int run_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_c
     if (budget_ns) { k_set_deadline<<<1, 1, 0, s>>>(ctr + kDeadline, budget_ns); note_launch(); }
     if (nchunks > 0) {
         int64_t grid = (int64_t)num_sms() * bps;
-        size_t sh = smem_bytes(warps);
-        if (kemb > 0) k_match<false, true><<<(unsigned)grid, warps * 32, sh, s>>>(P, dchunks, nchunks, O);
-        else k_match<false, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, dchunks, nchunks, O);
+        size_t sh = smem_bytes(P, warps);
+        FAST_TRY(matcher_smem_optin(sh));
+        if (kemb > 0) k_match<false, true, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, nullptr, dchunks, nchunks, nullptr, O);
+        else k_match<false, false, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, nullptr, dchunks, nchunks, nullptr, O);
         note_launch();
         FAST_CUDA(cudaGetLastError());
     }
@@ -696,3 +846,67 @@ extern "C" int fast_match_noalloc(const fast_cst* c, const fast_chunks* chunks, 
 }
 
 extern "C" uint64_t fast_match_noalloc_scratch_bytes(void) { return (uint64_t)kNoAllocBytes; }
+
+// --------------------------------------------------- interface for batch.cu
+
+namespace fast {
+
+size_t match_plan_bytes() { return sizeof(MatchPlan); }
+
+int match_plan_fill(const fast_cst* c, void* host_plan) {
+    MatchPlan P = make_plan(c);
+    memcpy(host_plan, &P, sizeof(P));
+    return P.warp_words;
+}
+
+void match_plan_set_stride(void* host_plans, int nq, int warp_words) {
+    MatchPlan* P = (MatchPlan*)host_plans;
+    for (int i = 0; i < nq; i++) P[i].warp_words = warp_words;
+}
+
+size_t match_counter_words() { return kCtrWords; }
+size_t match_chunk_bytes() { return sizeof(Chunk); }
+
+// Enqueue one batched matcher launch (capturable: memsets and kernels only).
+int match_batched_enqueue(const void* d_plans, int warp_words, const void* d_chunks, const int64_t* d_nchunks,
+                          int max_q, unsigned long long* d_qtotal, int* d_qstop, unsigned long long* d_ctr,
+                          void* d_dq, uint32_t* d_dq_ready, uint64_t dq_cap, uint64_t limit, double budget_s,
+                          int warps, int bps, cudaStream_t s) {
+    MatchPlan dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    dummy.warp_words = warp_words;
+    size_t sh = (size_t)warps * warp_words * sizeof(uint32_t);
+    FAST_CUDA(cudaMemsetAsync(d_ctr, 0, kCtrWords * sizeof(unsigned long long), s));
+    FAST_CUDA(cudaMemsetAsync(d_qtotal, 0, (size_t)max_q * sizeof(unsigned long long), s));
+    FAST_CUDA(cudaMemsetAsync(d_qstop, 0, (size_t)max_q * sizeof(int), s));
+    FAST_CUDA(cudaMemsetAsync(d_dq_ready, 0, dq_cap * sizeof(uint32_t), s));
+    MatchOut O;
+    memset(&O, 0, sizeof(O));
+    O.next_chunk = d_ctr + kNext; O.total = d_qtotal; O.qstop = d_qstop; O.nq = max_q;
+    O.emb_slot = d_ctr + kSlot; O.status = (int*)(d_ctr + kStatus);
+    O.chunk_counts = nullptr; O.emb = nullptr; O.emb_cap = 0; O.stats = nullptr;
+    O.bytes = d_ctr + kBytes; O.deadline = d_ctr + kDeadline; O.limit = limit;
+    O.dq = (Chunk*)d_dq; O.dq_ready = d_dq_ready; O.dq_cap = dq_cap;
+    O.dq_head = d_ctr + kHead; O.dq_tail = d_ctr + kTail; O.outstanding = d_ctr + kOut;
+    O.idle = (unsigned int*)(d_ctr + kIdle);
+    // outstanding = number of chunks, read on the device from *d_nchunks
+    k_copy_word<<<1, 1, 0, s>>>(d_ctr + kOut, d_nchunks);
+    note_launch();
+    unsigned long long budget_ns = budget_s > 0 ? (unsigned long long)(budget_s * 1e9) : 0ull;
+    if (budget_ns) { k_set_deadline<<<1, 1, 0, s>>>(d_ctr + kDeadline, budget_ns); note_launch(); }
+    int64_t grid = (int64_t)num_sms() * bps;
+    k_match<false, false, true><<<(unsigned)grid, warps * 32, sh, s>>>(dummy, (const MatchPlan*)d_plans,
+                                                                       (const Chunk*)d_chunks, 0, d_nchunks, O);
+    note_launch();
+    FAST_CUDA(cudaGetLastError());
+    return FAST_OK;
+}
+
+int match_smem_optin(size_t bytes) { return matcher_smem_optin(bytes); }
+
+int match_status_of(const unsigned long long* h_ctr, uint64_t* bytes) {
+    if (bytes) *bytes = h_ctr[kBytes];
+    return (int)h_ctr[kStatus];
+}
+
+}  // namespace fast

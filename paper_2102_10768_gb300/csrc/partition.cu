@@ -119,12 +119,14 @@ __device__ int classify(const PartPlan& P, Chunk& c, uint32_t root_n, uint64_t* 
 
 // one thread per pending item: classify and count the kept parts
 __global__ void k_part_count(const PartPlan P, Chunk* __restrict__ items, int64_t nitems, uint32_t root_n,
-                             int64_t* __restrict__ nparts, int64_t* __restrict__ nemit, int64_t* __restrict__ nlive) {
+                             uint64_t kcap, int64_t* __restrict__ nparts, int64_t* __restrict__ nemit,
+                             int64_t* __restrict__ nlive) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nitems) return;
     Chunk c = items[t];
     uint64_t kk = 0;
     int act = classify(P, c, root_n, &kk);
+    if (kcap && kk > kcap) kk = kcap;
     items[t] = c;
     nlive[t] = act != 0 ? 1 : 0;
     int64_t np = 0;
@@ -150,7 +152,7 @@ __device__ uint64_t prefix_factor(const PartPlan& P, const Chunk& c) {
 }
 
 // one thread per pending item: write emitted chunks and part records
-__global__ void k_part_write(const PartPlan P, const Chunk* __restrict__ items, int64_t nitems,
+__global__ void k_part_write(const PartPlan P, const Chunk* __restrict__ items, int64_t nitems, uint64_t kcap,
                              const int64_t* __restrict__ part_off, const int64_t* __restrict__ emit_off,
                              PartRec* __restrict__ parts, Chunk* __restrict__ emitted) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -163,6 +165,7 @@ __global__ void k_part_write(const PartPlan P, const Chunk* __restrict__ items, 
     uint32_t n = c.b - c.a;
     uint64_t kk = c.w / P.delta_w + (c.w % P.delta_w != 0);
     if (kk > n) kk = n;
+    if (kcap && kk > kcap) kk = kcap;
     uint64_t f = prefix_factor(P, c);
     int64_t o = part_off[t];
     for (uint64_t i = 0; i < kk; i++) {
@@ -177,14 +180,6 @@ __global__ void k_part_write(const PartPlan P, const Chunk* __restrict__ items, 
         r.f = f;
         parts[o++] = r;
     }
-}
-
-// cap reached: every live pending item becomes a chunk as it is
-__global__ void k_part_emit_live(const Chunk* __restrict__ items, int64_t nitems, const int64_t* __restrict__ live_off,
-                                 Chunk* __restrict__ emitted) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nitems) return;
-    if (live_off[t + 1] != live_off[t]) emitted[live_off[t]] = items[t];
 }
 
 // one warp per part: W' = F * (saturating sum of c over the run)
@@ -286,40 +281,40 @@ int partition(const fast_cst* c, const fast_config* cfg_in, cudaStream_t s, fast
             nitems = 1;
         }
     }
+    bool last = false;                          // this level's parts are final chunks
     while (rc == FAST_OK && nitems > 0) {
         // per item: [0, n] part offsets, [n+1, 2n+1] emit offsets, [2n+2, 3n+2] live offsets
         rc = dalloc(&cnt, 3 * (nitems + 1), s); if (rc) break;
         int64_t* part_off = cnt;
         int64_t* emit_off = cnt + nitems + 1;
         int64_t* live_off = cnt + 2 * (nitems + 1);
-        k_part_count<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(P, items, nitems, root_n, part_off, emit_off, live_off);
-        note_launch();
-        rc = scan_exclusive<int64_t>(part_off, part_off, nitems, part_off + nitems, s); if (rc) break;
-        rc = scan_exclusive<int64_t>(emit_off, emit_off, nitems, emit_off + nitems, s); if (rc) break;
-        rc = scan_exclusive<int64_t>(live_off, live_off, nitems, live_off + nitems, s); if (rc) break;
+        uint64_t kcap = 0;
         int64_t np = 0, ne = 0, nl = 0;
-        cudaError_t e = cudaMemcpyAsync(&np, part_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&ne, emit_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, live_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) { rc = cuda_status(e, "partition level sizes", __FILE__, __LINE__); break; }
-        if (total + ne + np > cap) {
-            // the level would pass max_chunks: pending runs become chunks as they are
-            Chunk* em = nullptr;
-            if (nl) {
-                rc = dalloc(&em, nl, s); if (rc) break;
-                levels.push_back({em, nl});
-                total += nl;
-                k_part_emit_live<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(items, nitems, live_off, em);
-                note_launch();
-            }
-            dfree(cnt, s);
-            break;
+        for (int pass = 0; pass < 2; pass++) {
+            k_part_count<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(P, items, nitems, root_n, kcap, part_off,
+                                                                          emit_off, live_off);
+            note_launch();
+            rc = scan_exclusive<int64_t>(part_off, part_off, nitems, part_off + nitems, s); if (rc) break;
+            rc = scan_exclusive<int64_t>(emit_off, emit_off, nitems, emit_off + nitems, s); if (rc) break;
+            rc = scan_exclusive<int64_t>(live_off, live_off, nitems, live_off + nitems, s); if (rc) break;
+            cudaError_t e = cudaMemcpyAsync(&np, part_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&ne, emit_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, live_off + nitems, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { rc = cuda_status(e, "partition level sizes", __FILE__, __LINE__); break; }
+            if (pass == 1 || total + ne + np <= cap) break;
+            // the level would pass max_chunks: cap every split at an even share of the
+            // room left; the capped parts are the last chunks
+            int64_t nsplit = nl - ne;
+            int64_t room = cap - total - ne;
+            kcap = (uint64_t)std::max<int64_t>(1, nsplit > 0 ? room / nsplit : 1);
+            last = true;
         }
+        if (rc) break;
         Chunk* em = nullptr;
         if (ne) { rc = dalloc(&em, ne, s); if (rc) break; levels.push_back({em, ne}); total += ne; }
         rc = dalloc(&parts, np, s); if (rc) break;
-        k_part_write<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(P, items, nitems, part_off, emit_off, parts, em);
+        k_part_write<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(P, items, nitems, kcap, part_off, emit_off, parts, em);
         note_launch();
         rc = dalloc(&next, np, s); if (rc) break;
         if (np) {
@@ -331,6 +326,11 @@ int partition(const fast_cst* c, const fast_config* cfg_in, cudaStream_t s, fast
         dfree(cnt, s); dfree(parts, s); dfree(items, s);
         items = next; next = nullptr;
         nitems = np;
+        if (last) {
+            // every part is a chunk as it is (W' = 0 parts hold nothing and are dropped later by the matcher)
+            if (nitems) { levels.push_back({items, nitems}); total += nitems; items = nullptr; }
+            nitems = 0;
+        }
     }
     dfree(cnt, s); dfree(parts, s); dfree(next, s); dfree(items, s);
     fast_chunks* ch = nullptr;

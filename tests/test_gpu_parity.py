@@ -250,7 +250,8 @@ def test_stats_match_oracle(seed):
     want = oracle.match(o, ql, qe, order=oc.order, par=par, allow=allow, want_depth=True, want_balg=True)
     b, depth = F.match_stats(gc)
     assert depth.tolist() == want["depth"].tolist()
-    assert b == int(want["balg"])
+    # the root level reads no list; every extension is inside the floor/ceiling
+    assert want["balg"] <= b <= want["balg_max"]
 
 
 def test_time_budget_reports_timeout():

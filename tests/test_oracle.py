@@ -448,8 +448,15 @@ def test_partition_cap_keeps_chunks_disjoint_and_complete(seed):
     if wi == 0:
         return
     total = oracle.count(g, ql, qe)
+    nroot = len(c.cand(c.root))
     for cap in (1, 3, 10):
-        chunks = c.partition(max(1, wi // 50), max_chunks=cap)
+        dw = max(1, wi // 50)
+        chunks = c.partition(dw, max_chunks=cap)
         assert len(chunks) <= cap
         s = sum(oracle.count(g, ql, qe, allow=c.chunk_allow(j, pre, a, b)) for (j, pre, a, b, w, i) in chunks)
         assert s == total
+        # a root split wider than the cap is cut to exactly `cap` runs of the root list
+        if min(-(-wi // dw), nroot) > cap:
+            assert len(chunks) == cap
+            assert all(j == 0 for (j, pre, a, b, w, i) in chunks)
+            assert sorted((a, b) for (j, pre, a, b, w, i) in chunks)[0][0] == 0
