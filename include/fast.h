@@ -94,6 +94,11 @@ typedef struct {
     /* Enumeration limit: fast_match stops once `limit` embeddings are found
      * and reports min(total, limit), exactly (0: enumerate everything). */
     uint64_t limit;
+    /* Cells of the matcher's ring of donated runs (work given away to idle
+     * warps); a full ring only means a busy warp keeps its work.  0: the
+     * default, 65536 (4096 for fast_match_noalloc); larger values are
+     * clamped to the default.  Results never depend on it. */
+    int64_t queue_cells;
 } fast_config;
 
 /* Default tunables: delta_w = 2^20, no sampling, max_chunks = 2^16,

@@ -35,7 +35,7 @@ size_t match_counter_words();
 size_t match_chunk_bytes();
 int match_batched_enqueue(const void* d_plans, int warp_words, const void* d_chunks, const int64_t* d_nchunks,
                           int max_q, unsigned long long* d_qtotal, int* d_qstop, unsigned long long* d_ctr,
-                          void* d_dq, uint32_t* d_dq_ready, uint64_t dq_cap, uint64_t limit, double budget_s,
+                          void* d_dq, uint32_t* d_dq_state, uint64_t dq_cap, uint64_t limit, double budget_s,
                           int warps, int bps, cudaStream_t s);
 int match_smem_optin(size_t bytes);
 int match_status_of(const unsigned long long* h_ctr, uint64_t* bytes);
@@ -46,8 +46,8 @@ using namespace fast;
 namespace {
 
 constexpr int kClasses = 5;                       // |V(q)| <= 4, 8, 16, 24, 32
-constexpr uint64_t kBatchQueue = 1 << 16;         // donated runs
-enum { kStatusTimeout = 1, kStatusOverflow = 2, kStatusLimit = 4, kStatusStall = 8 };
+constexpr uint64_t kBatchQueue = 1 << 16;         // cells of the ring of donated runs
+enum { kStatusTimeout = 1, kStatusOverflow = 2, kStatusLimit = 4 };
 
 int size_class(int k) { return k <= 4 ? 0 : k <= 8 ? 1 : k <= 16 ? 2 : k <= 24 ? 3 : 4; }
 
@@ -75,11 +75,12 @@ struct fast_batch {
     unsigned long long* h_ctr = nullptr;    // pinned
     int* d_qstop = nullptr;
     unsigned char* d_dq = nullptr;
-    uint32_t* d_dq_ready = nullptr;
+    uint32_t* d_dq_state = nullptr;
     cudaGraphExec_t exec = nullptr;
     int g_warp_words = -1, g_warps = -1, g_bps = -1;
     double g_budget = -1.0;
     uint64_t g_limit = ~0ull;
+    uint64_t g_cells = 0;
     unsigned char* g_chunks = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_build_ms = 0.0, last_match_ms = 0.0;
@@ -107,7 +108,7 @@ void batch_release(fast_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     cudaStream_t s = nullptr;
     dfree(b->d_plans, s); dfree(b->d_off, s); dfree(b->d_nchunks, s); dfree(b->d_chunks, s);
-    dfree(b->d_ctr, s); dfree(b->d_qtotal, s); dfree(b->d_qstop, s); dfree(b->d_dq, s); dfree(b->d_dq_ready, s);
+    dfree(b->d_ctr, s); dfree(b->d_qtotal, s); dfree(b->d_qstop, s); dfree(b->d_dq, s); dfree(b->d_dq_state, s);
     cudaStreamSynchronize(s);
     if (b->h_plans) cudaFreeHost(b->h_plans);
     if (b->h_off) cudaFreeHost(b->h_off);
@@ -145,7 +146,7 @@ int batch_create(const fast_graph* g, const fast_config* cfg, int32_t max_q, int
         rc = dalloc(&b->d_qtotal, max_q, s); if (rc) break;
         rc = dalloc(&b->d_qstop, max_q, s); if (rc) break;
         rc = dalloc(&b->d_dq, kBatchQueue * match_chunk_bytes(), s); if (rc) break;
-        rc = dalloc(&b->d_dq_ready, kBatchQueue, s); if (rc) break;
+        rc = dalloc(&b->d_dq_state, kBatchQueue, s); if (rc) break;
         if (cudaMallocHost((void**)&b->h_plans, (size_t)max_q * b->psize) != cudaSuccess ||
             cudaMallocHost((void**)&b->h_off, (size_t)(max_q + 1) * sizeof(int64_t)) != cudaSuccess ||
             cudaMallocHost((void**)&b->h_qtotal, (size_t)max_q * sizeof(unsigned long long)) != cudaSuccess ||
@@ -164,8 +165,10 @@ int batch_create(const fast_graph* g, const fast_config* cfg, int32_t max_q, int
 
 // (Re)capture the matcher launch as a graph when its shape changed.
 int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream_t s) {
+    const uint64_t cells = lc.queue_cells > 0 ? std::min<uint64_t>((uint64_t)lc.queue_cells, kBatchQueue) : kBatchQueue;
     if (b->exec && b->g_warp_words == warp_words && b->g_warps == lc.warps_per_block && b->g_bps == lc.blocks_per_sm &&
-        b->g_budget == lc.time_budget_s && b->g_limit == lc.limit && b->g_chunks == b->d_chunks)
+        b->g_budget == lc.time_budget_s && b->g_limit == lc.limit && b->g_chunks == b->d_chunks &&
+        b->g_cells == cells)
         return FAST_OK;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     int warps = lc.warps_per_block > 0 ? std::min(lc.warps_per_block, 8) : 8;
@@ -179,7 +182,7 @@ int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream
     if (e != cudaSuccess) rc = cuda_status(e, "begin capture", __FILE__, __LINE__);
     if (rc == FAST_OK) {
         int rc2 = match_batched_enqueue(b->d_plans, warp_words, b->d_chunks, b->d_nchunks, b->max_q, b->d_qtotal,
-                                        b->d_qstop, b->d_ctr, b->d_dq, b->d_dq_ready, kBatchQueue, lc.limit,
+                                        b->d_qstop, b->d_ctr, b->d_dq, b->d_dq_state, cells, lc.limit,
                                         lc.time_budget_s, warps, bps, cap);
         e = cudaStreamEndCapture(cap, &graph);
         if (rc2 != FAST_OK) rc = rc2;
@@ -194,7 +197,7 @@ int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream
     (void)s;
     if (rc == FAST_OK) {
         b->g_warp_words = warp_words; b->g_warps = lc.warps_per_block; b->g_bps = lc.blocks_per_sm;
-        b->g_budget = lc.time_budget_s; b->g_limit = lc.limit; b->g_chunks = b->d_chunks;
+        b->g_budget = lc.time_budget_s; b->g_limit = lc.limit; b->g_chunks = b->d_chunks; b->g_cells = cells;
     }
     return rc;
 }
@@ -291,7 +294,6 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
         if (csts[i]) fast_free_cst(csts[i]);
     }
     if (rc != FAST_OK) return rc;
-    if (gst & kStatusStall) return set_error(FAST_ERR_CUDA, "fast_batch_run: a donated run was never published");
     uint64_t limit = b->base.limit;
     for (int i = 0; i < nq; i++) {
         if (st[i] != FAST_OK) { counts[i] = 0; status[i] = st[i]; continue; }

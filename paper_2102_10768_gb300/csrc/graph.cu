@@ -55,6 +55,7 @@ extern "C" void fast_config_default(fast_config* cfg) {
     cfg->blocks_per_sm = 4;
     cfg->time_budget_s = 0.0;
     cfg->limit = 0;
+    cfg->queue_cells = 0;
 }
 
 namespace {

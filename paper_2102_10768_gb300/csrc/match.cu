@@ -16,7 +16,7 @@
 // is indexed dynamically.
 //
 // Load balance: a persistent grid first drains the static chunk list, then a
-// global queue of donated runs.  A warp that finds both empty counts itself
+// global ring of donated runs.  A warp that finds both empty counts itself
 // idle; a busy warp that sees idle warps gives away the second half of the
 // unscanned list at its shallowest depth with at least two entries left --
 // a run of a list with a fixed prefix, i.e. again a chunk.  An outstanding-
@@ -65,12 +65,11 @@ struct MatchPlan {
     const uint32_t* n_idx[kMaxNT];
 };
 
-enum : int { kStatusTimeout = 1, kStatusOverflow = 2, kStatusLimit = 4, kStatusStall = 8 };
+enum : int { kStatusTimeout = 1, kStatusOverflow = 2, kStatusLimit = 4 };
 // shared words per warp: survivors [32 depths][32], m and data vertex per
 // position, then one 8-byte cursor per non-tree edge of the query
 constexpr int kWarpBaseWords = kMaxK * 32 + 2 * kMaxK;
 constexpr uint32_t kDonated = 1;
-constexpr unsigned long long kStallNs = 60ull * 1000 * 1000 * 1000;   // a claimed slot never published
 constexpr unsigned long long kIdleNs = 5ull * 1000 * 1000 * 1000;     // an idle warp gives up waiting
 
 struct MatchOut {
@@ -87,8 +86,15 @@ struct MatchOut {
     unsigned long long* bytes;        // bytes the search requested
     const unsigned long long* deadline;  // device word: %globaltimer limit, 0 = none
     uint64_t limit;                   // 0 = enumerate everything
-    Chunk* dq;                        // donated runs
-    uint32_t* dq_ready;
+    // Donated runs: a bounded ring of dq_cap cells.  Ticket t (a count of
+    // claims, dq_tail for donors and dq_head for takers) uses cell t % dq_cap
+    // in generation g = t / dq_cap; the cell's state is 2g while it is free
+    // for that ticket and 2g+1 once the run is published; the taker sets
+    // 2g+2 after reading it.  States start at 0.  Nobody waits on a cell: a
+    // donor that finds its cell still occupied keeps its work, and a taker
+    // that finds no published cell looks again later.
+    Chunk* dq;
+    uint32_t* dq_state;
     uint64_t dq_cap;                  // 0 = no donation
     unsigned long long* dq_head;
     unsigned long long* dq_tail;
@@ -215,7 +221,7 @@ __device__ int acquire(const MatchOut& O, int64_t nchunks, unsigned long long de
     int kind = 0;
     unsigned long long t_idle = 0;
     for (;;) {
-        if (vload(O.status) & (kStatusTimeout | kStatusLimit | kStatusStall)) break;
+        if (vload(O.status) & (kStatusTimeout | kStatusLimit)) break;
         unsigned long long now = global_timer_ns();
         if (deadline && now > deadline) { atomicOr(O.status, kStatusTimeout); break; }
         if (vload(O.next_chunk) < (unsigned long long)nchunks) {
@@ -223,22 +229,16 @@ __device__ int acquire(const MatchOut& O, int64_t nchunks, unsigned long long de
             if (i < (unsigned long long)nchunks) { *idx = i; kind = 1; break; }
         }
         if (O.dq_cap) {
-            unsigned long long h = vload(O.dq_head), t = vload(O.dq_tail);
-            if (t > O.dq_cap) t = O.dq_cap;
-            if (h < t) {
+            unsigned long long h = vload(O.dq_head);
+            uint32_t want = (uint32_t)(2 * (h / O.dq_cap) + 1);          // published, ticket h
+            if (*(volatile uint32_t*)&O.dq_state[h % O.dq_cap] == want) {
                 if (atomicCAS(O.dq_head, h, h + 1) == h) {
-                    unsigned long long w0 = global_timer_ns();
-                    bool ready = true;
-                    while (!*(volatile uint32_t*)&O.dq_ready[h]) {
-                        if (global_timer_ns() - w0 > kStallNs) { atomicOr(O.status, kStatusStall); ready = false; break; }
-                        __nanosleep(32);
-                    }
-                    if (!ready) break;
+                    __threadfence();
                     *idx = h;
                     kind = 2;
                     break;
                 }
-                continue;
+                continue;                                                 // taken by another warp
             }
         }
         if (vload(O.outstanding) == 0) break;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256) k_match(const __grid_constant__ MatchPlan
         // the item's fields, read once.  A donated run was written by another
         // warp during this launch: read it from L2 (ld.global.cg), never from
         // an L1 line that may hold an older copy of its bytes.
-        const Chunk* chp = kind == 1 ? chunks + ci : O.dq + ci;
+        const Chunk* chp = kind == 1 ? chunks + ci : O.dq + ci % O.dq_cap;
         int j;
         uint32_t ch_a, ch_b, ch_pad, ch_pre;
         if (kind == 1) {
@@ -290,6 +290,11 @@ __global__ void __launch_bounds__(256) k_match(const __grid_constant__ MatchPlan
         } else {
             j = __ldcg(&chp->j); ch_a = __ldcg(&chp->a); ch_b = __ldcg(&chp->b); ch_pad = __ldcg(&chp->pad);
             ch_pre = lane < j ? __ldcg(&chp->prefix[lane]) : 0u;
+            __syncwarp();
+            if (lane == 0) {                      // hand the cell back for ticket ci + dq_cap
+                __threadfence();
+                atomicExch(&O.dq_state[ci % O.dq_cap], (uint32_t)(2 * (ci / O.dq_cap) + 2));
+            }
         }
         const uint32_t q = BATCH ? (ch_pad >> 8) : 0u;
         const MatchPlan& P = BATCH ? plans[q] : P0;
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(256) k_match(const __grid_constant__ MatchPlan
                     if (lane == 0) {
                         flush_count(O, q, local);
                         if (deadline && global_timer_ns() > deadline) atomicOr(O.status, kStatusTimeout);
-                        stop = vload(O.status) & (kStatusTimeout | kStatusLimit | kStatusStall);
+                        stop = vload(O.status) & (kStatusTimeout | kStatusLimit);
                         if (BATCH && *(volatile int*)&O.qstop[q]) stop = 1;
                     }
                     if (__shfl_sync(0xffffffffu, stop, 0)) break;
@@ -371,15 +376,32 @@ __global__ void __launch_bounds__(256) k_match(const __grid_constant__ MatchPlan
                         uint32_t cm = __ballot_sync(0xffffffffu, can);
                         if (cm) {
                             int dd = __ffs(cm) - 1;
-                            unsigned long long slot = 0;
-                            if (lane == 0) slot = atomicAdd(O.dq_tail, 1ull);
+                            // claim the next ticket whose cell is free; a full
+                            // ring (or a lost race, a few times) keeps the work here
+                            unsigned long long slot = ~0ull;
+                            if (lane == 0) {
+                                unsigned long long t = vload(O.dq_tail);
+                                for (int tries = 0; tries < 4; tries++) {
+                                    uint32_t st = *(volatile uint32_t*)&O.dq_state[t % O.dq_cap];
+                                    uint32_t g2 = (uint32_t)(2 * (t / O.dq_cap));
+                                    if (st == g2) {
+                                        unsigned long long prev = atomicCAS(O.dq_tail, t, t + 1);
+                                        if (prev == t) { slot = t; break; }
+                                        t = prev;
+                                    } else if (st < g2) {
+                                        break;                            // its previous run is not taken yet
+                                    } else {
+                                        t = vload(O.dq_tail);
+                                    }
+                                }
+                            }
                             slot = __shfl_sync(0xffffffffu, slot, 0);
-                            if (slot < O.dq_cap) {
+                            if (slot != ~0ull) {
                                 int64_t sn_ = __shfl_sync(0xffffffffu, seg_next, dd);
                                 int64_t se_ = __shfl_sync(0xffffffffu, seg_end, dd);
                                 int64_t sb_ = __shfl_sync(0xffffffffu, seg_base, dd);
                                 int64_t mid = sn_ + (se_ - sn_) / 2;
-                                Chunk* dst = &O.dq[slot];
+                                Chunk* dst = &O.dq[slot % O.dq_cap];
                                 if (lane < kMaxK) dst->prefix[lane] = lane < dd ? sm[lane] : 0u;
                                 if (lane == 0) {
                                     atomicAdd(O.outstanding, 1ull);
@@ -393,7 +415,7 @@ __global__ void __launch_bounds__(256) k_match(const __grid_constant__ MatchPlan
                                 __syncwarp();
                                 if (lane == 0) {
                                     __threadfence();
-                                    atomicExch(&O.dq_ready[slot], 1u);
+                                    atomicExch(&O.dq_state[slot % O.dq_cap], (uint32_t)(2 * (slot / O.dq_cap) + 1));
                                 }
                                 if (lane == dd) seg_end = mid;
                             }
@@ -553,6 +575,11 @@ enum { kNext = 0, kTotal, kSlot, kStatus, kBytes, kHead, kTail, kOut, kIdle, kDe
        kCtrWords = kStats + kMaxK + 1 };
 constexpr uint64_t kQueueCap = 1 << 16;
 
+// cells of the donation ring for a launch: cfg.queue_cells, at most (and by default) cap
+uint64_t ring_cells(const fast_config& cfg, uint64_t cap) {
+    return cfg.queue_cells > 0 ? std::min<uint64_t>((uint64_t)cfg.queue_cells, cap) : cap;
+}
+
 int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* cfg_in, uint64_t kemb, uint32_t* emb_out,
               uint64_t* count_out, uint64_t* written_out, uint64_t* chunk_counts, uint64_t* stats_out,
               cudaStream_t s) {
@@ -590,10 +617,11 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
     const bool donate = chunk_counts == nullptr && stats_out == nullptr;
     unsigned long long* ctr = nullptr;
     Chunk* dq = nullptr;
-    uint32_t* dq_ready = nullptr;
+    uint32_t* dq_state = nullptr;
+    const uint64_t cells = ring_cells(cfg, kQueueCap);
     rc = dalloc(&ctr, kCtrWords, s);
-    if (rc == FAST_OK && donate) rc = dalloc(&dq, kQueueCap, s);
-    if (rc == FAST_OK && donate) rc = dalloc(&dq_ready, kQueueCap, s);
+    if (rc == FAST_OK && donate) rc = dalloc(&dq, cells, s);
+    if (rc == FAST_OK && donate) rc = dalloc(&dq_state, cells, s);
     uint32_t* emb_dev = emb_out;
     uint32_t* staged = nullptr;
     bool timed = false;
@@ -613,7 +641,7 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
         cudaMemsetAsync(ctr, 0, kCtrWords * sizeof(unsigned long long), s);
         unsigned long long out0 = (unsigned long long)nchunks;
         cudaMemcpyAsync(ctr + kOut, &out0, sizeof(out0), cudaMemcpyHostToDevice, s);
-        if (donate) cudaMemsetAsync(dq_ready, 0, kQueueCap * sizeof(uint32_t), s);
+        if (donate) cudaMemsetAsync(dq_state, 0, cells * sizeof(uint32_t), s);
         MatchOut O;
         O.next_chunk = ctr + kNext; O.total = ctr + kTotal; O.emb_slot = ctr + kSlot; O.status = (int*)(ctr + kStatus);
         O.qstop = (int*)(ctr + kQStop); O.nq = 1;
@@ -622,7 +650,7 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
         O.bytes = ctr + kBytes;
         O.deadline = ctr + kDeadline;
         O.limit = cfg.limit;
-        O.dq = dq; O.dq_ready = dq_ready; O.dq_cap = donate ? kQueueCap : 0;
+        O.dq = dq; O.dq_state = dq_state; O.dq_cap = donate ? cells : 0;
         O.dq_head = ctr + kHead; O.dq_tail = ctr + kTail; O.outstanding = ctr + kOut;
         O.idle = (unsigned int*)(ctr + kIdle);
         unsigned long long budget_ns = cfg.time_budget_s > 0 ? (unsigned long long)(cfg.time_budget_s * 1e9) : 0ull;
@@ -665,7 +693,7 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_status(e, "fast_match embedding readback", __FILE__, __LINE__);
     }
-    dfree(ctr, s); dfree(own, s); dfree(staged, s); dfree(dq, s); dfree(dq_ready, s);
+    dfree(ctr, s); dfree(own, s); dfree(staged, s); dfree(dq, s); dfree(dq_state, s);
     if (rc != FAST_OK) return rc;
     uint64_t total = h[kTotal];
     if (cfg.limit > 0 && total > cfg.limit) total = cfg.limit;
@@ -676,7 +704,6 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
         for (int i = 0; i < c->k; i++) stats_out[1 + i] = h[kStats + i];
     }
     int st = (int)h[kStatus];
-    if (st & kStatusStall) return set_error(FAST_ERR_CUDA, "fast_match: a donated run was never published");
     if (st & kStatusTimeout) return set_error(FAST_ERR_TIMEOUT, "fast_match: time budget of %.3f s spent", cfg.time_budget_s);
     if (st & kStatusOverflow) return set_error(FAST_ERR_OVERFLOW, "fast_match: count reached 2^64");
     return FAST_OK;
@@ -777,7 +804,8 @@ int run_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_c
     FAST_TRY(noalloc_scratch(&base));
     unsigned long long* ctr = (unsigned long long*)base;
     Chunk* dq = (Chunk*)(base + kNaCtrBytes);
-    uint32_t* dq_ready = (uint32_t*)(base + kNaCtrBytes + kNaQueueBytes);
+    uint32_t* dq_state = (uint32_t*)(base + kNaCtrBytes + kNaQueueBytes);
+    const uint64_t cells = ring_cells(cfg, kNoAllocQueue);
     Chunk* runs = (Chunk*)(base + kNaCtrBytes + kNaQueueBytes + kNaReadyBytes);
     const Chunk* dchunks = nullptr;
     int64_t nchunks = 0;
@@ -800,7 +828,7 @@ int run_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_c
     FAST_CUDA(cudaMemsetAsync(ctr, 0, kCtrWords * sizeof(unsigned long long), s));
     unsigned long long out0 = (unsigned long long)nchunks;
     FAST_CUDA(cudaMemcpyAsync(ctr + kOut, &out0, sizeof(out0), cudaMemcpyHostToDevice, s));
-    FAST_CUDA(cudaMemsetAsync(dq_ready, 0, kNoAllocQueue * sizeof(uint32_t), s));
+    FAST_CUDA(cudaMemsetAsync(dq_state, 0, cells * sizeof(uint32_t), s));
     MatchPlan P = make_plan(c);
     MatchOut O;
     O.next_chunk = ctr + kNext; O.total = ctr + kTotal; O.emb_slot = ctr + kSlot; O.status = (int*)(ctr + kStatus);
@@ -810,7 +838,7 @@ int run_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_c
     O.bytes = ctr + kBytes;
     O.deadline = ctr + kDeadline;
     O.limit = cfg.limit;
-    O.dq = dq; O.dq_ready = dq_ready; O.dq_cap = kNoAllocQueue;
+    O.dq = dq; O.dq_state = dq_state; O.dq_cap = cells;
     O.dq_head = ctr + kHead; O.dq_tail = ctr + kTail; O.outstanding = ctr + kOut;
     O.idle = (unsigned int*)(ctr + kIdle);
     unsigned long long budget_ns = cfg.time_budget_s > 0 ? (unsigned long long)(cfg.time_budget_s * 1e9) : 0ull;
@@ -832,7 +860,6 @@ int run_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_c
     if (count_out) *count_out = total;
     if (written_out) *written_out = std::min<uint64_t>(emb_cap, h[kSlot]);
     int st = (int)h[kStatus];
-    if (st & kStatusStall) return set_error(FAST_ERR_CUDA, "fast_match_noalloc: a donated run was never published");
     if (st & kStatusTimeout) return set_error(FAST_ERR_TIMEOUT, "fast_match_noalloc: time budget of %.3f s spent", cfg.time_budget_s);
     if (st & kStatusOverflow) return set_error(FAST_ERR_OVERFLOW, "fast_match_noalloc: count reached 2^64");
     return FAST_OK;
@@ -870,7 +897,7 @@ size_t match_chunk_bytes() { return sizeof(Chunk); }
 // Enqueue one batched matcher launch (capturable: memsets and kernels only).
 int match_batched_enqueue(const void* d_plans, int warp_words, const void* d_chunks, const int64_t* d_nchunks,
                           int max_q, unsigned long long* d_qtotal, int* d_qstop, unsigned long long* d_ctr,
-                          void* d_dq, uint32_t* d_dq_ready, uint64_t dq_cap, uint64_t limit, double budget_s,
+                          void* d_dq, uint32_t* d_dq_state, uint64_t dq_cap, uint64_t limit, double budget_s,
                           int warps, int bps, cudaStream_t s) {
     MatchPlan dummy;
     memset(&dummy, 0, sizeof(dummy));
@@ -879,14 +906,14 @@ int match_batched_enqueue(const void* d_plans, int warp_words, const void* d_chu
     FAST_CUDA(cudaMemsetAsync(d_ctr, 0, kCtrWords * sizeof(unsigned long long), s));
     FAST_CUDA(cudaMemsetAsync(d_qtotal, 0, (size_t)max_q * sizeof(unsigned long long), s));
     FAST_CUDA(cudaMemsetAsync(d_qstop, 0, (size_t)max_q * sizeof(int), s));
-    FAST_CUDA(cudaMemsetAsync(d_dq_ready, 0, dq_cap * sizeof(uint32_t), s));
+    FAST_CUDA(cudaMemsetAsync(d_dq_state, 0, dq_cap * sizeof(uint32_t), s));
     MatchOut O;
     memset(&O, 0, sizeof(O));
     O.next_chunk = d_ctr + kNext; O.total = d_qtotal; O.qstop = d_qstop; O.nq = max_q;
     O.emb_slot = d_ctr + kSlot; O.status = (int*)(d_ctr + kStatus);
     O.chunk_counts = nullptr; O.emb = nullptr; O.emb_cap = 0; O.stats = nullptr;
     O.bytes = d_ctr + kBytes; O.deadline = d_ctr + kDeadline; O.limit = limit;
-    O.dq = (Chunk*)d_dq; O.dq_ready = d_dq_ready; O.dq_cap = dq_cap;
+    O.dq = (Chunk*)d_dq; O.dq_state = d_dq_state; O.dq_cap = dq_cap;
     O.dq_head = d_ctr + kHead; O.dq_tail = d_ctr + kTail; O.outstanding = d_ctr + kOut;
     O.idle = (unsigned int*)(d_ctr + kIdle);
     // outstanding = number of chunks, read on the device from *d_nchunks

@@ -316,6 +316,31 @@ def test_work_stealing_on_a_skewed_tree():
         assert F.match(cst, F.Chunks(cst, F.default_config(delta_w=max(1, cst.W // 64))))["count"] == want
 
 
+@pytest.mark.parametrize("cells", [1, 2, 7, 64])
+def test_work_stealing_with_a_tiny_ring(cells):
+    """The ring of donated runs wraps around thousands of times and is often
+    full (a donor then keeps its work); counts stay exact on every path."""
+    rng = np.random.default_rng(12)
+    n = 3000
+    e = [(0, v) for v in range(1, n)] + [tuple(x) for x in rng.integers(1, n, size=(6000, 2)) if x[0] != x[1]]
+    e = np.array(e, np.int32)
+    lab = np.zeros(n, np.int32)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    cfg = F.default_config(queue_cells=cells)
+    for qe in ([[0, 1], [1, 2], [2, 3]], [[0, 1], [1, 2], [0, 2], [2, 3]], [[0, 1], [1, 2], [2, 3], [3, 4]]):
+        ql = np.zeros(int(np.max(qe)) + 1, np.int32)
+        want = oracle.count(o, ql, qe)
+        cst = F.Cst(g, ql, qe)
+        assert F.match(cst, cfg=cfg)["count"] == want
+        assert F.match_noalloc(cst, cfg=cfg)["count"] == want
+        lim = F.default_config(queue_cells=cells, limit=max(1, want // 3))
+        assert F.match(cst, cfg=lim)["count"] == min(want, max(1, want // 3))
+    qs = [(np.zeros(4, np.int32), [[0, 1], [1, 2], [2, 3]]), (np.zeros(4, np.int32), [[0, 1], [1, 2], [0, 2], [2, 3]])]
+    counts, status = F.Batch(g, 4, cfg).run(qs * 2)
+    assert status.tolist() == [0] * 4
+    assert counts.tolist() == [oracle.count(o, ql, qe) for ql, qe in qs] * 2
+
+
 # ------------------------------------------------- power-law graph, full size
 
 @pytest.fixture(scope="module")
