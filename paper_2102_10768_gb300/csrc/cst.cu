@@ -9,15 +9,17 @@
 //              ordered compaction keeps neighbours that pass u's filter,
 //              writing N^{u_p}_u(v_p) in place and marking the reached
 //              vertices in a bitmap, whose compaction is C(u).
-//   bottom-up  per u, children first: one warp per candidate counts the
-//              list entries still alive in each child's bitmap; candidates
-//              with an empty child list are dropped; the surviving lists are
-//              rewritten as candidate-local indices (bitmap rank).
+//   bottom-up  per u, children first: a pass over each child's flattened
+//              lists flags the candidates that keep an entry alive in the
+//              child's bitmap; candidates with an empty child list are
+//              dropped; an ordered compaction rewrites the surviving lists as
+//              candidate-local indices (bitmap rank).
 //   non-tree   per non-tree edge (earlier u_j -> later u_i in the order):
 //              the same edge-space compaction over C(u_j) with the bitmap of
 //              C(u_i) as predicate and its rank as output.
-//   workload   one warp per candidate, children first: the saturating sum of
-//              c over each child list, and their product.
+//   workload   children first: the saturating sum of c over each child
+//              list (entry-parallel, one atomic per row segment), then their
+//              product per candidate.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -76,7 +78,6 @@ __global__ void k_cand_degree_n(const int32_t* __restrict__ cand, const int64_t*
 // off[*n] = *val (closing offset of a list set whose row count is on the device)
 __global__ void k_set_tail(int64_t* off, const int64_t* n, const int64_t* val) { off[*n] = *val; }
 __global__ void k_set_tail_at(int64_t* off, int64_t n, const int64_t* val) { off[n] = *val; }
-__global__ void k_copy_i64(int64_t* dst, const int64_t* src) { *dst = *src; }
 
 __device__ __forceinline__ int64_t row_of(const int64_t* e_off, int64_t rows, int64_t i) {
     // last r with e_off[r] <= i
@@ -187,32 +188,10 @@ struct KeepRowsF {
     __device__ void at(int64_t, int64_t) const {}
 };
 
-__global__ void k_set_bits(const int32_t* __restrict__ ids, int64_t n, uint32_t* __restrict__ bits) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicOr(&bits[ids[i] >> 5], 1u << (ids[i] & 31));
-}
 
 __global__ void k_popc_words(const uint32_t* __restrict__ bits, int64_t nw, uint32_t* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nw) out[i] = __popc(bits[i]);
-}
-
-// per row: entries of the list whose id is alive in the child's bitmap
-__global__ void k_count_alive(const int64_t* __restrict__ off, const int32_t* __restrict__ list, int64_t rows,
-                              const uint32_t* __restrict__ alive, int64_t* __restrict__ cnt) {
-    const int lane = threadIdx.x & 31;
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = w; r < rows; r += nw) {
-        int64_t lo = off[r], hi = off[r + 1];
-        int64_t c = 0;
-        for (int64_t e = lo + lane; e < hi; e += 32) {
-            int32_t x = list[e];
-            c += (alive[x >> 5] >> (x & 31)) & 1u;
-        }
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0) cnt[r] = c;
-    }
 }
 
 __global__ void k_set_bits_n(const int32_t* __restrict__ ids, const int64_t* __restrict__ n, int64_t cap,
@@ -221,122 +200,94 @@ __global__ void k_set_bits_n(const int32_t* __restrict__ ids, const int64_t* __r
     if (i < cap && i < *n) atomicOr(&bits[ids[i] >> 5], 1u << (ids[i] & 31));
 }
 
-__global__ void k_count_alive_n(const int64_t* __restrict__ off, const int32_t* __restrict__ list,
-                                const int64_t* __restrict__ nrows, const uint32_t* __restrict__ alive,
-                                int64_t* __restrict__ cnt) {
-    const int lane = threadIdx.x & 31;
-    int64_t rows = *nrows;
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = w; r < rows; r += nw) {
-        int64_t lo = off[r], hi = off[r + 1];
-        int64_t c = 0;
-        for (int64_t e = lo + lane; e < hi; e += 32) {
+// ------------------------------------------------- balanced list kernels
+//
+// The lists of a CST level are one flattened entry space (offsets over the
+// rows of a candidate set).  On a power-law graph a few hub rows hold most
+// entries, so these kernels split the entry space, not the rows: a block
+// takes tiles of kTileItems entries (grid-stride), each thread kItems
+// consecutive entries, finds its first row by binary search and advances it.
+
+constexpr int kItems = 8;
+constexpr int kTileItems = 256 * kItems;
+
+inline unsigned tile_grid(int64_t entries_bound) {
+    int64_t t = ceil_div(entries_bound, (int64_t)kTileItems);
+    int64_t cap = (int64_t)num_sms() * 8;
+    if (t > cap) t = cap;
+    return (unsigned)(t < 1 ? 1 : t);
+}
+
+// has[r] = 1 if row r (of *nrows) keeps an entry alive in `alive`
+__global__ void __launch_bounds__(256) k_any_alive(const int64_t* __restrict__ off, const int64_t* __restrict__ nrows,
+                                                   const int32_t* __restrict__ list, const uint32_t* __restrict__ alive,
+                                                   uint8_t* __restrict__ has) {
+    const int64_t rows = *nrows;
+    const int64_t e_end = off[rows];
+    for (int64_t t = blockIdx.x; t * kTileItems < e_end; t += gridDim.x) {
+        int64_t i0 = t * kTileItems + (int64_t)threadIdx.x * kItems;
+        if (i0 >= e_end) continue;
+        int64_t row = row_of(off, rows, i0), done = -1;
+        for (int i = 0; i < kItems; i++) {
+            int64_t e = i0 + i;
+            if (e >= e_end) break;
+            while (e >= off[row + 1]) row++;
+            if (row == done) continue;
             int32_t x = list[e];
-            c += (alive[x >> 5] >> (x & 31)) & 1u;
+            if ((alive[x >> 5] >> (x & 31)) & 1u) { has[row] = 1; done = row; }
         }
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0) cnt[r] = c;
     }
 }
 
-struct ChildCounts {
-    const int64_t* cnt[kMaxK];
+struct ChildFlags {
+    const uint8_t* has[kMaxK];
     int nch;
 };
 
-__global__ void k_valid_rows(ChildCounts cc, int64_t rows, uint8_t* __restrict__ valid, int64_t* __restrict__ vflag) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    uint8_t ok = 1;
-    for (int c = 0; c < cc.nch; c++) ok &= (cc.cnt[c][r] > 0) ? 1 : 0;
-    valid[r] = ok;
-    vflag[r] = ok;
-}
-
-// as k_valid_rows, for *nrows live rows of a buffer of `cap` rows (the rest invalid)
-__global__ void k_valid_rows_n(ChildCounts cc, const int64_t* __restrict__ nrows, int64_t cap,
+// valid[r] = r < *nrows and every child list of row r keeps an entry
+__global__ void k_valid_rows_n(ChildFlags cf, const int64_t* __restrict__ nrows, int64_t cap,
                                uint8_t* __restrict__ valid, int64_t* __restrict__ vflag) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= cap) return;
     uint8_t ok = r < *nrows ? 1 : 0;
-    for (int c = 0; c < cc.nch && ok; c++) ok &= (cc.cnt[c][r] > 0) ? 1 : 0;
+    for (int c = 0; c < cf.nch && ok; c++) ok &= cf.has[c][r];
     valid[r] = ok;
     vflag[r] = ok;
 }
 
-__global__ void k_write_alive_n(const int64_t* __restrict__ off, const int32_t* __restrict__ list,
-                                const int64_t* __restrict__ nrows, const uint8_t* __restrict__ valid,
-                                const int64_t* __restrict__ newrow, const uint32_t* __restrict__ alive,
-                                const uint32_t* __restrict__ rank, const int64_t* __restrict__ new_off,
-                                uint32_t* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    int64_t rows = *nrows;
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = w; r < rows; r += nw) {
-        if (!valid[r]) continue;
-        int64_t lo = off[r], hi = off[r + 1];
-        int64_t dst = new_off[newrow[r]];
-        for (int64_t base = lo; base < hi; base += 32) {
-            int64_t e = base + lane;
-            bool ok = false;
-            uint32_t v = 0;
-            if (e < hi) {
-                int32_t x = list[e];
-                uint32_t wd = alive[x >> 5], bit = 1u << (x & 31);
-                ok = (wd & bit) != 0;
-                v = rank[x >> 5] + __popc(wd & (bit - 1));
-            }
-            uint32_t m = __ballot_sync(0xffffffffu, ok);
-            if (ok) out[dst + __popc(m & lanemask_lt())] = v;
-            dst += __popc(m);
-        }
+// Bottom-up rewrite: the entries of valid rows still alive in the child's
+// bitmap, as candidate-local indices (bitmap rank), rows renumbered by
+// newrow; each kept row's new offset comes from the compaction's rank.
+struct WriteAliveF {
+    using value_type = uint32_t;
+    const int64_t* off;
+    const int64_t* nrows;
+    const int32_t* list;
+    const uint32_t* alive;
+    const uint32_t* rank;
+    const uint8_t* valid;
+    const int64_t* newrow;
+    int64_t* new_off;
+    int64_t rows;
+    int64_t row;
+    int64_t e_end;
+    __device__ void begin(int64_t i0) {
+        rows = *nrows;
+        e_end = off[rows];
+        if (i0 < e_end) row = row_of(off, rows, i0);
     }
-}
-
-__global__ void k_gather_counts(const int64_t* __restrict__ cnt, const uint8_t* __restrict__ valid,
-                                const int64_t* __restrict__ newrow, int64_t rows, int64_t* __restrict__ out) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < rows && valid[r]) out[newrow[r]] = cnt[r];
-}
-
-// rewrite the alive entries of valid rows as candidate-local indices
-__global__ void k_write_alive(const int64_t* __restrict__ off, const int32_t* __restrict__ list, int64_t rows,
-                              const uint8_t* __restrict__ valid, const int64_t* __restrict__ newrow,
-                              const uint32_t* __restrict__ alive, const uint32_t* __restrict__ rank,
-                              const int64_t* __restrict__ new_off, uint32_t* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = w; r < rows; r += nw) {
-        if (!valid[r]) continue;
-        int64_t lo = off[r], hi = off[r + 1];
-        int64_t dst = new_off[newrow[r]];
-        for (int64_t base = lo; base < hi; base += 32) {
-            int64_t e = base + lane;
-            bool ok = false;
-            uint32_t v = 0;
-            if (e < hi) {
-                int32_t x = list[e];
-                uint32_t wd = alive[x >> 5], bit = 1u << (x & 31);
-                ok = (wd & bit) != 0;
-                v = rank[x >> 5] + __popc(wd & (bit - 1));
-            }
-            uint32_t m = __ballot_sync(0xffffffffu, ok);
-            if (ok) out[dst + __popc(m & lanemask_lt())] = v;
-            dst += __popc(m);
-        }
+    __device__ bool eval(int64_t i, uint32_t& v) {
+        v = 0;
+        if (i >= e_end) return false;
+        while (i >= off[row + 1]) row++;
+        if (!valid[row]) return false;
+        int32_t x = list[i];
+        uint32_t wd = alive[x >> 5], bit = 1u << (x & 31);
+        v = rank[x >> 5] + __popc(wd & (bit - 1));
+        return (wd & bit) != 0;
     }
-}
-
-struct ChildLists {
-    const int64_t* off[kMaxK];
-    const uint32_t* idx[kMaxK];
-    const uint64_t* cval[kMaxK];
-    const double* cvalf[kMaxK];
-    uint64_t* ssum[kMaxK];
-    int nch;
+    __device__ int64_t tag(int64_t i) const { return (i < e_end && i == off[row] && valid[row]) ? row : -1; }
+    __device__ void at(int64_t r, int64_t rk) const { new_off[newrow[r]] = rk; }
 };
 
 __device__ __forceinline__ uint64_t warp_sat_sum(uint64_t v) {
@@ -349,31 +300,72 @@ __device__ __forceinline__ double warp_sum_f(double v) {
     return v;
 }
 
-// c_u(v) = prod over children of the sum of c over v's list (Sec. IV-C)
-__global__ void k_workload(ChildLists cl, int64_t rows, uint64_t* __restrict__ cval, double* __restrict__ cvalf) {
-    const int lane = threadIdx.x & 31;
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = w; r < rows; r += nw) {
-        uint64_t prod = 1;
-        double prodf = 1.0;
-        for (int c = 0; c < cl.nch; c++) {
-            int64_t lo = cl.off[c][r], hi = cl.off[c][r + 1];
-            uint64_t s = 0;
-            double sf = 0.0;
-            for (int64_t e = lo + lane; e < hi; e += 32) {
-                uint32_t x = cl.idx[c][e];
-                s = sat_add(s, cl.cval[c][x]);
-                sf += cl.cvalf[c][x];
+// Workload, first half (Sec. IV-C): per row r of C(u) and one child c, the
+// sum of c_c over r's list into c.  Entries are split as above; a thread
+// adds each row segment it covers with one atomic.  Saturation: a segment
+// that wrapped or carried a saturated term, or an atomic that wrapped, sets
+// ovf[r], and the row's sum then reads as 2^64 - 1.
+__global__ void __launch_bounds__(256) k_child_sums(const int64_t* __restrict__ off, int64_t rows,
+                                                    const uint32_t* __restrict__ idx,
+                                                    const uint64_t* __restrict__ cv, const double* __restrict__ cvf,
+                                                    unsigned long long* __restrict__ ssum, double* __restrict__ sumf,
+                                                    uint32_t* __restrict__ ovf) {
+    const int64_t e_end = off[rows];
+    for (int64_t t = blockIdx.x; t * kTileItems < e_end; t += gridDim.x) {
+        int64_t i0 = t * kTileItems + (int64_t)threadIdx.x * kItems;
+        if (i0 >= e_end) continue;
+        int64_t row = row_of(off, rows, i0);
+        unsigned long long s = 0;
+        double sf = 0.0;
+        bool sat = false;
+        auto flush = [&]() {
+            unsigned long long old = atomicAdd(&ssum[row], s);
+            if (old + s < old) sat = true;
+            if (sat) atomicOr(&ovf[row], 1u);
+            atomicAdd(&sumf[row], sf);
+        };
+        for (int i = 0; i < kItems; i++) {
+            int64_t e = i0 + i;
+            if (e >= e_end) break;
+            if (e >= off[row + 1]) {
+                flush();
+                s = 0; sf = 0.0; sat = false;
+                do row++; while (e >= off[row + 1]);
             }
-            s = warp_sat_sum(s);
-            sf = warp_sum_f(sf);
-            if (lane == 0) cl.ssum[c][r] = s;
-            prod = sat_mul(prod, s);
-            prodf *= sf;
+            uint32_t x = idx[e];
+            uint64_t v = cv[x];
+            unsigned long long ns = s + v;
+            if (ns < s || v == ~0ull) sat = true;
+            s = ns;
+            sf += cvf[x];
         }
-        if (lane == 0) { cval[r] = prod; cvalf[r] = prodf; }
+        flush();
     }
+}
+
+struct ChildSums {
+    uint64_t* ssum[kMaxK];
+    const double* sumf[kMaxK];
+    const uint32_t* ovf[kMaxK];
+    int nch;
+};
+
+// Workload, second half: c_u(v) = product over children of those sums
+// (saturating), and the float64 twin; the saturated sums are kept for the
+// partitioner.
+__global__ void k_workload_prod(ChildSums cs, int64_t rows, uint64_t* __restrict__ cval, double* __restrict__ cvalf) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    uint64_t prod = 1;
+    double prodf = 1.0;
+    for (int c = 0; c < cs.nch; c++) {
+        uint64_t sm = cs.ovf[c][r] ? ~0ull : cs.ssum[c][r];
+        cs.ssum[c][r] = sm;
+        prod = sat_mul(prod, sm);
+        prodf *= cs.sumf[c][r];
+    }
+    cval[r] = prod;
+    cvalf[r] = prodf;
 }
 
 __global__ void k_total_w(const uint64_t* __restrict__ cval, const double* __restrict__ cvalf, int64_t n,
@@ -412,13 +404,6 @@ inline unsigned grid_for(int64_t n, int threads) {
     return (unsigned)(b < 1 ? 1 : (b > 0x7FFFFFFF ? 0x7FFFFFFF : b));
 }
 
-inline unsigned warp_grid(int64_t rows) {
-    // one warp per row up to a persistent cap
-    int64_t blocks = ceil_div(rows, 8);
-    int64_t cap = (int64_t)num_sms() * 32;
-    if (blocks > cap) blocks = cap;
-    return (unsigned)(blocks < 1 ? 1 : blocks);
-}
 
 // ----------------------------------------------------------------- build
 
@@ -607,25 +592,26 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
             int64_t* n_u = sz + u;
             int ch[kMaxK], nch = 0;
             for (int w = 0; w < k; w++) if (c->parent[w] == u) ch[nch++] = w;
-            int64_t* cnt[kMaxK] = {nullptr};
+            uint8_t* has[kMaxK] = {nullptr};
             uint8_t* valid = nullptr;
             int64_t* newrow = nullptr;
             do {
-                ChildCounts cc{};
-                cc.nch = nch;
+                ChildFlags cf{};
+                cf.nch = nch;
                 for (int i = 0; i < nch; i++) {
                     int w = ch[i];
-                    rc = dalloc(&cnt[i], rows, s); if (rc) break;
+                    rc = dalloc(&has[i], rows, s); if (rc) break;
                     if (rows > 0) {
-                        k_count_alive_n<<<warp_grid(rows), 256, 0, s>>>(td_off[w], td_list[w], n_u, bits[w].alive, cnt[i]);
+                        cudaMemsetAsync(has[i], 0, rows, s);
+                        k_any_alive<<<tile_grid(cap_l[w]), 256, 0, s>>>(td_off[w], n_u, td_list[w], bits[w].alive, has[i]);
                         note_launch();
                     }
-                    cc.cnt[i] = cnt[i];
+                    cf.has[i] = has[i];
                 }
                 if (rc) break;
                 rc = dalloc(&valid, rows, s); if (rc) break;
                 rc = dalloc(&newrow, rows + 1, s); if (rc) break;
-                if (rows > 0) { k_valid_rows_n<<<grid_for(rows, 256), 256, 0, s>>>(cc, n_u, rows, valid, newrow); note_launch(); }
+                if (rows > 0) { k_valid_rows_n<<<grid_for(rows, 256), 256, 0, s>>>(cf, n_u, rows, valid, newrow); note_launch(); }
                 rc = scan_exclusive<int64_t>(newrow, newrow, rows, newrow + rows, s); if (rc) break;
                 rc = dalloc(&c->cand[u], rows, s); if (rc) break;
                 KeepRowsF kf{td_cand[u], valid};
@@ -633,17 +619,14 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
                 for (int i = 0; i < nch && rc == FAST_OK; i++) {
                     int w = ch[i];
                     rc = dalloc(&c->t_off[w], rows + 1, s); if (rc) break;
-                    cudaMemsetAsync(c->t_off[w], 0, (rows + 1) * sizeof(int64_t), s);
-                    if (rows > 0) { k_gather_counts<<<grid_for(rows, 256), 256, 0, s>>>(cnt[i], valid, newrow, rows, c->t_off[w]); note_launch(); }
-                    rc = scan_exclusive<int64_t>(c->t_off[w], c->t_off[w], rows, c->t_off[w] + rows, s); if (rc) break;
-                    k_copy_i64<<<1, 1, 0, s>>>(sz + 2 * kMaxK + w, c->t_off[w] + rows);
-                    note_launch();
                     rc = dalloc(&c->t_idx[w], cap_l[w], s); if (rc) break;
-                    if (rows > 0) {
-                        k_write_alive_n<<<warp_grid(rows), 256, 0, s>>>(td_off[w], td_list[w], n_u, valid, newrow,
-                                                                        bits[w].alive, bits[w].rank, c->t_off[w], c->t_idx[w]);
-                        note_launch();
-                    }
+                    WriteAliveF f{};
+                    f.off = td_off[w]; f.nrows = n_u; f.list = td_list[w];
+                    f.alive = bits[w].alive; f.rank = bits[w].rank;
+                    f.valid = valid; f.newrow = newrow; f.new_off = c->t_off[w];
+                    rc = compact(f, cap_l[w], c->t_idx[w], sz + 2 * kMaxK + w, s); if (rc) break;
+                    k_set_tail<<<1, 1, 0, s>>>(c->t_off[w], sz + kMaxK + u, sz + 2 * kMaxK + w);
+                    note_launch();
                     dfree(td_list[w], s); dfree(td_off[w], s);
                 }
                 if (rc) break;
@@ -656,7 +639,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
                 note_launch();
                 rc = scan_exclusive<uint32_t>(bits[u].rank, bits[u].rank, nw, (uint32_t*)nullptr, s);
             } while (0);
-            for (int i = 0; i < nch; i++) dfree(cnt[i], s);
+            for (int i = 0; i < nch; i++) dfree(has[i], s);
             dfree(valid, s); dfree(newrow, s);
             dfree(td_cand[u], s);
         }
@@ -725,27 +708,38 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
             int64_t rows = c->ncand[u];
             rc = dalloc(&c->cval[u], rows, s); if (rc) break;
             rc = dalloc(&c->cvalf[u], rows, s); if (rc) break;
-            ChildLists cl{};
-            cl.nch = 0;
+            ChildSums cs{};
+            cs.nch = 0;
+            double* sumf[kMaxK] = {nullptr};
+            uint32_t* ovf[kMaxK] = {nullptr};
             for (int w = 0; w < k && rc == FAST_OK; w++) {
                 if (c->parent[w] != u) continue;
+                int i = cs.nch++;
                 rc = dalloc(&c->ssum[w], rows, s); if (rc) break;
-                cl.off[cl.nch] = c->t_off[w]; cl.idx[cl.nch] = c->t_idx[w];
-                cl.cval[cl.nch] = c->cval[w]; cl.cvalf[cl.nch] = c->cvalf[w]; cl.ssum[cl.nch] = c->ssum[w];
-                cl.nch++;
+                rc = dalloc(&sumf[i], rows, s); if (rc) break;
+                rc = dalloc(&ovf[i], rows, s); if (rc) break;
+                if (rows > 0) {
+                    cudaMemsetAsync(c->ssum[w], 0, rows * sizeof(uint64_t), s);
+                    cudaMemsetAsync(sumf[i], 0, rows * sizeof(double), s);
+                    cudaMemsetAsync(ovf[i], 0, rows * sizeof(uint32_t), s);
+                    k_child_sums<<<tile_grid(cap_l[w]), 256, 0, s>>>(c->t_off[w], rows, c->t_idx[w], c->cval[w], c->cvalf[w],
+                                                                   (unsigned long long*)c->ssum[w], sumf[i], ovf[i]);
+                    note_launch();
+                }
+                cs.ssum[i] = c->ssum[w]; cs.sumf[i] = sumf[i]; cs.ovf[i] = ovf[i];
             }
-            if (rc) break;
-            if (rows > 0) {
-                if (cl.nch == 0) {
+            if (rc == FAST_OK && rows > 0) {
+                if (cs.nch == 0) {
                     k_fill_u64<<<grid_for(rows, 256), 256, 0, s>>>(c->cval[u], rows, 1);
                     note_launch();
                     k_fill_f64<<<grid_for(rows, 256), 256, 0, s>>>(c->cvalf[u], rows, 1.0);
                     note_launch();
                 } else {
-                    k_workload<<<warp_grid(rows), 256, 0, s>>>(cl, rows, c->cval[u], c->cvalf[u]);
+                    k_workload_prod<<<grid_for(rows, 256), 256, 0, s>>>(cs, rows, c->cval[u], c->cvalf[u]);
                     note_launch();
                 }
             }
+            for (int i = 0; i < kMaxK; i++) { dfree(sumf[i], s); dfree(ovf[i], s); }
         }
         if (rc) break;
         {

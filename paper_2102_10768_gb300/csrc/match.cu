@@ -253,7 +253,7 @@ __device__ int acquire(const MatchOut& O, int64_t nchunks, unsigned long long de
 // BATCH: plans[q] per query (chunk flags carry q, nchunks is read from
 // *nchunks_dev); otherwise the single plan P0 and the nchunks argument.
 template <bool STATS, bool EMIT, bool BATCH>
-__global__ void __launch_bounds__(256) k_match(const __grid_constant__ MatchPlan P0,
+__global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchPlan P0,
                                                const MatchPlan* __restrict__ plans,
                                                const Chunk* __restrict__ chunks, int64_t nchunks,
                                                const int64_t* __restrict__ nchunks_dev, MatchOut O) {

@@ -84,6 +84,8 @@ __device__ __forceinline__ uint32_t list_len(const PartPlan& P, const Chunk& c, 
     return (uint32_t)(P.t_off[c.j][m + 1] - P.t_off[c.j][m]);
 }
 
+__device__ __forceinline__ bool sampled(const PartPlan& P) { return P.c_root > 0.0 || P.c_deep > 0.0; }
+
 __device__ __forceinline__ bool keep_part(const PartPlan& P, int j, uint64_t kk, uint64_t id) {
     double cs = j == 0 ? P.c_root : P.c_deep;
     if (cs <= 0.0) return true;
@@ -131,8 +133,10 @@ __global__ void k_part_count(const PartPlan P, Chunk* __restrict__ items, int64_
     nlive[t] = act != 0 ? 1 : 0;
     int64_t np = 0;
     if (act == 2) {
-        for (uint64_t i = 0; i < kk; i++)
-            np += keep_part(P, c.j, kk, mix64(c.id + (i + 1) * 0x9E3779B97F4A7C15ull)) ? 1 : 0;
+        if (!sampled(P)) np = (int64_t)kk;
+        else
+            for (uint64_t i = 0; i < kk; i++)
+                np += keep_part(P, c.j, kk, mix64(c.id + (i + 1) * 0x9E3779B97F4A7C15ull)) ? 1 : 0;
     }
     nparts[t] = np;
     nemit[t] = act == 1 ? 1 : 0;
@@ -151,7 +155,9 @@ __device__ uint64_t prefix_factor(const PartPlan& P, const Chunk& c) {
     return f;
 }
 
-// one thread per pending item: write emitted chunks and part records
+// one thread per pending item: write emitted chunks, and the part records
+// of sampled splits (without sampling, k_part_sum derives every part from
+// its item and its index there)
 __global__ void k_part_write(const PartPlan P, const Chunk* __restrict__ items, int64_t nitems, uint64_t kcap,
                              const int64_t* __restrict__ part_off, const int64_t* __restrict__ emit_off,
                              PartRec* __restrict__ parts, Chunk* __restrict__ emitted) {
@@ -161,7 +167,7 @@ __global__ void k_part_write(const PartPlan P, const Chunk* __restrict__ items, 
     int64_t np = part_off[t + 1] - part_off[t];
     int64_t ne = emit_off[t + 1] - emit_off[t];
     if (ne) emitted[emit_off[t]] = c;
-    if (!np) return;
+    if (!np || !sampled(P)) return;
     uint32_t n = c.b - c.a;
     uint64_t kk = c.w / P.delta_w + (c.w % P.delta_w != 0);
     if (kk > n) kk = n;
@@ -182,14 +188,40 @@ __global__ void k_part_write(const PartPlan P, const Chunk* __restrict__ items, 
     }
 }
 
-// one warp per part: W' = F * (saturating sum of c over the run)
-__global__ void k_part_sum(const PartPlan P, const Chunk* __restrict__ items, const PartRec* __restrict__ parts,
+// Part p of an unsampled level: its item t (the last with part_off[t] <= p)
+// and run i = p - part_off[t] of the item's kk = part_off[t+1] - part_off[t]
+// even runs (the split factor after the cap).
+__device__ PartRec part_of(const PartPlan& P, const Chunk* __restrict__ items, int64_t nitems,
+                           const int64_t* __restrict__ part_off, int64_t p) {
+    int64_t lo = 0, hi = nitems;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (part_off[mid] <= p) lo = mid; else hi = mid;
+    }
+    const Chunk& c = items[lo];
+    uint64_t i = (uint64_t)(p - part_off[lo]);
+    uint64_t kk = (uint64_t)(part_off[lo + 1] - part_off[lo]);
+    uint64_t n = c.b - c.a;
+    PartRec r;
+    r.item = (uint32_t)lo;
+    r.a = c.a + (uint32_t)((i * n) / kk);
+    r.b = c.a + (uint32_t)(((i + 1) * n) / kk);
+    r.pad = 0;
+    r.id = mix64(c.id + (i + 1) * 0x9E3779B97F4A7C15ull);
+    r.f = prefix_factor(P, c);
+    return r;
+}
+
+// one warp per part: W' = F * (saturating sum of c over the run).  parts ==
+// nullptr: the level is unsampled and part_of() gives each part.
+__global__ void k_part_sum(const PartPlan P, const Chunk* __restrict__ items, int64_t nitems,
+                           const int64_t* __restrict__ part_off, const PartRec* __restrict__ parts,
                            int64_t nparts, Chunk* __restrict__ next) {
     const int lane = threadIdx.x & 31;
     int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t p = w; p < nparts; p += nw) {
-        PartRec r = parts[p];
+        PartRec r = parts ? parts[p] : part_of(P, items, nitems, part_off, p);
         const Chunk& it = items[r.item];
         int j = it.j;
         const uint64_t* cv = P.cval[j];
@@ -313,13 +345,16 @@ int partition(const fast_cst* c, const fast_config* cfg_in, cudaStream_t s, fast
         if (rc) break;
         Chunk* em = nullptr;
         if (ne) { rc = dalloc(&em, ne, s); if (rc) break; levels.push_back({em, ne}); total += ne; }
-        rc = dalloc(&parts, np, s); if (rc) break;
-        k_part_write<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(P, items, nitems, kcap, part_off, emit_off, parts, em);
-        note_launch();
+        const bool smp = cfg.sample_root > 0.0 || cfg.sample_deep > 0.0;
+        if (smp) { rc = dalloc(&parts, np, s); if (rc) break; }
+        if (ne || smp) {
+            k_part_write<<<(unsigned)ceil_div(nitems, 128), 128, 0, s>>>(P, items, nitems, kcap, part_off, emit_off, parts, em);
+            note_launch();
+        }
         rc = dalloc(&next, np, s); if (rc) break;
         if (np) {
             int64_t blocks = std::min<int64_t>(ceil_div(np, 8), (int64_t)num_sms() * 32);
-            k_part_sum<<<(unsigned)blocks, 256, 0, s>>>(P, items, parts, np, next);
+            k_part_sum<<<(unsigned)blocks, 256, 0, s>>>(P, items, nitems, part_off, smp ? parts : nullptr, np, next);
             note_launch();
         }
         if (cudaGetLastError() != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "partition kernel launch"); break; }
