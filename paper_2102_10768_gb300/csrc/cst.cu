@@ -104,6 +104,7 @@ struct TopDownF {
     uint32_t* reached;         // bitmap over V(G)
     int64_t* t_off;            // out: [rows+1]
     const int64_t* E;          // edge-space size on the device (index space may be a bound)
+    bool counting;             // set in the compaction's count pass: mark nothing then
     int64_t row;
     int64_t nbase;
     int64_t e_end;
@@ -120,7 +121,7 @@ struct TopDownF {
         v = x;
         int32_t kk = key[x];
         bool hit = (kk >> 8) == want_key_hi && (kk & 255) >= want_dq;
-        if (hit) atomicOr(&reached[x >> 5], 1u << (x & 31));
+        if (hit && !counting) atomicOr(&reached[x >> 5], 1u << (x & 31));
         return hit;
     }
     __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? row : -1; }

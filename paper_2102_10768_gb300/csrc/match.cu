@@ -448,8 +448,9 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                         cnd = (d == 0) ? (uint32_t)idx : __ldg(P.t_idx[d] + idx);
                         if (d > 0) lb += 4;
                     }
-                    // EdgeValidator
+                    // EdgeValidator (most selective edge first; stop once no lane is pending)
                     for (int e = P.nt_begin[d]; e < P.nt_begin[d + 1]; e++) {
+                        if (!__any_sync(0xffffffffu, ok)) break;
                         uint32_t mf = __shfl_sync(0xffffffffu, m_reg, P.nt_from[e]);
                         int64_t lo = P.n_off[e][mf], hi = P.n_off[e][mf + 1];
                         int64_t cur = lo + ncur[e];
@@ -528,11 +529,22 @@ MatchPlan make_plan(const fast_cst* c) {
         for (int p = 0; p < i; p++)
             if (c->qlabel[c->order[p]] == c->qlabel[u]) P.same_lab[i] |= 1u << p;
     }
+    // Non-tree edges into each position, the shortest lists on average (the
+    // likeliest to reject a candidate) first: a segment stops checking once
+    // no candidate is left.  The order does not change the result.
     int e = 0;
     for (int i = 0; i < k; i++) {
         P.nt_begin[i] = e;
-        for (int t = 0; t < c->nnt; t++) {
-            if (c->pos[c->nt_to[t]] != i) continue;
+        int ts[kMaxNT], nts = 0;
+        for (int t = 0; t < c->nnt; t++)
+            if (c->pos[c->nt_to[t]] == i) ts[nts++] = t;
+        auto avg = [&](int t) {
+            int64_t rows = c->ncand[c->nt_from[t]];
+            return (double)c->n_entries[t] / (double)(rows > 0 ? rows : 1);
+        };
+        std::stable_sort(ts, ts + nts, [&](int a, int b) { return avg(a) < avg(b); });
+        for (int x = 0; x < nts; x++) {
+            int t = ts[x];
             P.nt_from[e] = c->pos[c->nt_from[t]];
             P.n_off[e] = c->n_off[t];
             P.n_idx[e] = c->n_idx[t];

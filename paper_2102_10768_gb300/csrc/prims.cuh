@@ -4,6 +4,9 @@
 // with cudaMallocAsync on the caller's stream.
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include "common.cuh"
 
 namespace fast {
@@ -121,12 +124,20 @@ constexpr int kCompBlock = 256;
 constexpr int kCompItems = 8;
 constexpr int kCompTile = kCompBlock * kCompItems;
 
+// A functor with a member `bool counting` has it set in the count pass, so
+// that side effects of eval (marking a bitmap) happen once, in the write pass.
+template <class F, class = void>
+struct has_counting : std::false_type {};
+template <class F>
+struct has_counting<F, std::void_t<decltype(std::declval<F&>().counting)>> : std::true_type {};
+
 template <class F>
 __global__ void k_compact_count(F f, int64_t n, int64_t* __restrict__ counts) {
     __shared__ int64_t tmp[kCompBlock / 32 + 1];
     int64_t base = (int64_t)blockIdx.x * kCompTile + (int64_t)threadIdx.x * kCompItems;
     int64_t v[kCompItems];
     F g = f;
+    if constexpr (has_counting<F>::value) g.counting = true;
     g.begin(base);
 #pragma unroll
     for (int i = 0; i < kCompItems; i++) {

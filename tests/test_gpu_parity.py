@@ -291,12 +291,13 @@ def test_limit_matches_oracle(seed):
     total = oracle.count(o, ql, qe)
     for L in (1, 33, max(1, total // 2), total + 1):
         cfg = F.default_config(limit=L)
-        r = F.match(gc, k=L, cfg=cfg)
+        kemb = min(L, 1 << 18)                 # rows copied out (the count is always exact)
+        r = F.match(gc, k=kemb, cfg=cfg)
         assert r["count"] == min(total, L)
         rows = r["emb"][:r["written"]].astype(np.int32)
-        assert r["written"] == min(total, L)
+        assert r["written"] == min(total, L, kemb)
         assert oracle.invalid_rows(o, ql, qe, rows) == 0
-        assert len(set(map(tuple, rows.tolist()))) == rows.shape[0]
+        assert np.unique(rows, axis=0).shape[0] == rows.shape[0]
 
 
 def test_work_stealing_on_a_skewed_tree():
