@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--threads", type=int, default=8, help="host threads building CSTs in a batched step")
     p.add_argument("--batch-budget", type=float, default=60.0, help="seconds for one batched matcher launch")
     p.add_argument("--no-serve", dest="serve", action="store_false", help="skip the serving sweep")
+    p.add_argument("--order", choices=["path", "greedy"], default="greedy",
+                   help="matching order: the greedy rule (default) or the paper's path-based order "
+                        "(also reported beside the headline as path_order)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     return p.parse_args()
 
@@ -68,7 +71,7 @@ def workload(args, rank: int):
             qs += synth.walk_queries(n, e, lab, k, args.queries, kind, seed=args.seed, stream0=stream0)
     desc = (f"Chung-Lu gamma=2.1, n=1,000,000, m=16,000,000, 16 Zipf(1.0) labels; "
             f"{len(qs)} random-walk queries (8/16 vertices x dense/sparse); per query: CST, Alg. 2 partition "
-            f"(delta_w={args.delta_w}, max_chunks={args.max_chunks}), match until limit={args.limit} "
+            f"(delta_w={args.delta_w}, max_chunks={args.max_chunks}), {args.order} matching order, match until limit={args.limit} "
             f"embeddings (count = min(total, limit)), budget {args.budget} s; seed={args.seed}")
     return n, e, lab, qs, desc
 
@@ -251,7 +254,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     g = F.Graph(n, e, lab)
     cfg = F.default_config(delta_w=args.delta_w, max_chunks=args.max_chunks, limit=args.limit,
-                           time_budget_s=args.budget)
+                           time_budget_s=args.budget, order_rule=1 if args.order == "greedy" else 0)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
     bq = [(q.labels, q.edges) for q in qs]
 
@@ -313,6 +316,31 @@ def run_ours(args):
         t_e2e += time.perf_counter() - ts
         e2e_emb += int(c.sum())
     bt.close()
+
+    # ---- the same batched step in the other matching order (the paper adopts
+    # the path-based one; its method takes any connected order)
+    other = "path" if args.order == "greedy" else "greedy"
+    ocfg = F.Config.from_buffer_copy(bcfg)
+    ocfg.order_rule = 1 if other == "greedy" else 0
+    obt = F.Batch(g, len(bq), ocfg, threads=args.threads)
+    obt.run(bq, stream=stream.cuda_stream)
+    o_emb, o_ms, o_kms = 0, 0.0, 0.0
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        c, st = obt.run(bq, stream=stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        o_emb += int(c.sum())
+        o_ms += ev0.elapsed_time(ev1)
+        o_kms += obt.timing()["match_ms"]
+    obt.close()
+    other_line = {"order": other, "value": o_emb / (o_ms / 1000.0), "unit": UNIT,
+                  "ms_per_step": o_ms / max(1, min(args.steps, 3)),
+                  "match_ms_per_step": o_kms / max(1, min(args.steps, 3))}
 
     # ---- per query: the same queries, one fast_build_cst + fast_partition +
     # fast_match_ex each (latency percentiles; the comparison the metric asks for)
@@ -390,6 +418,7 @@ def run_ours(args):
         "config": {"workload": desc, "queries_per_step": len(qs),
                    "mode": f"batched: fast_batch_run, {args.threads} build threads, one graph-replayed matcher "
                            f"launch per step (budget {args.batch_budget} s)",
+                   "order": args.order,
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}, queries per rank"},
         "queries_per_sec": len(qs) * steps * world / t_s,
         "embeddings_per_step": tot_emb / steps,
@@ -404,6 +433,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": ck,
+        f"{other}_order": other_line,
         "per_query": {"value": q_emb / (q_ms / 1000.0), "unit": UNIT,
                       "queries_per_sec": len(qs) * qsteps / (q_ms / 1000.0),
                       "ms_per_step": q_ms / qsteps, "steps": qsteps,

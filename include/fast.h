@@ -99,6 +99,13 @@ typedef struct {
      * default, 65536 (4096 for fast_match_noalloc); larger values are
      * clamped to the default.  Results never depend on it. */
     int64_t queue_cells;
+    /* Matching order O of fast_build_cst.  0: the paper's path-based order
+     * (Sec. IV-B): a depth-first walk of t_q, children by increasing
+     * (|C(u)|, u).  1: greedy: after the root, repeatedly the vertex whose
+     * t_q parent is placed with the most query edges to placed vertices
+     * (ties: smaller |C(u)|, then smaller u).  The paper's method takes any
+     * connected order; embeddings and counts never depend on it. */
+    int32_t order_rule;
 } fast_config;
 
 /* Default tunables: delta_w = 2^20, no sampling, max_chunks = 2^16,

@@ -19,8 +19,14 @@
  *            to the (already refined) C(u_c); v stays in C(u) iff every such
  *            list is non-empty and (u is the root or v lies in some list of
  *            the parent).  One pass, as written.
- *   order    depth-first preorder of t_q from the root, children visited in
- *            increasing (|C(u_c)|, u_c): whole root-to-leaf paths in turn.
+ *   order    rule 0 (the paper's path-based order, Sec. IV-B): depth-first
+ *            preorder of t_q from the root, children visited in increasing
+ *            (|C(u_c)|, u_c): whole root-to-leaf paths in turn.
+ *            rule 1 (greedy; the paper's method takes any connected order,
+ *            Sec. IV-B): after the root, repeatedly the unplaced vertex whose
+ *            t_q parent is placed with the most query edges to placed
+ *            vertices; ties to the smaller |C(u)|, then the smaller id.
+ *            Either way every vertex follows its t_q parent.
  *   non-tree for each query edge outside t_q, from its earlier endpoint u_j
  *            to its later endpoint u_i in the order: N^{u_j}_{u_i}(v) =
  *            N_G(v) n C(u_i) for v in C(u_j).  Only this direction is read
@@ -97,8 +103,8 @@ void oracle_cst_free(ocst* c) {
  * Build the CST of q over G (Algorithm 1 with the readings above).
  * Returns a handle, or NULL on invalid or disconnected input.
  */
-ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int32_t* qe) {
-    if (k < 1 || k > CMAXK) return NULL;
+ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int32_t* qe, int order_rule) {
+    if (k < 1 || k > CMAXK || order_rule < 0 || order_rule > 1) return NULL;
     int A[CMAXK][CMAXK];
     memset(A, 0, sizeof(A));
     int dq[CMAXK] = {0};
@@ -212,7 +218,28 @@ ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int
         free(keep); free(haspar);
     }
 
-    /* matching order: DFS preorder, children by (|C|, id) */
+    /* matching order, rule 1: greedy by edges to the placed vertices */
+    if (order_rule == 1) {
+        int placed[CMAXK] = {0};
+        c->order[0] = r;
+        placed[r] = 1;
+        for (int no = 1; no < k; no++) {
+            int best = -1, bb = -1;
+            for (int u = 0; u < k; u++) {
+                if (placed[u] || !placed[c->parent[u]]) continue;
+                int b = 0;
+                for (int w = 0; w < k; w++) if (placed[w] && A[u][w]) b++;
+                if (best < 0 || b > bb ||
+                    (b == bb && (c->cand[u].n < c->cand[best].n || (c->cand[u].n == c->cand[best].n && u < best)))) {
+                    best = u;
+                    bb = b;
+                }
+            }
+            c->order[no] = best;
+            placed[best] = 1;
+        }
+    } else
+    /* matching order, rule 0: DFS preorder, children by (|C|, id) */
     {
         int stack[CMAXK], sp = 0, no = 0;
         stack[sp++] = r;

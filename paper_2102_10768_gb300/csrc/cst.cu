@@ -462,6 +462,8 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
     if (!g) return set_error(FAST_ERR_INVALID, "fast_build_cst: graph is NULL");
     int A[kMaxK][kMaxK], dq[kMaxK];
     FAST_TRY(validate_query(q, A, dq));
+    if (cfg_in && (cfg_in->order_rule < 0 || cfg_in->order_rule > 1))
+        return set_error(FAST_ERR_INVALID, "fast_build_cst: order_rule %d (0 path-based, 1 greedy)", cfg_in->order_rule);
     const int k = q->n;
     fast_cst* c = new fast_cst();
     memset(c->cand, 0, sizeof(c->cand)); memset(c->t_off, 0, sizeof(c->t_off)); memset(c->t_idx, 0, sizeof(c->t_idx));
@@ -654,7 +656,29 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         }
 
         // ------------------------------------------------ matching order
-        {
+        if (c->cfg.order_rule == 1) {
+            // greedy: the unplaced vertex whose t_q parent is placed, with the
+            // most query edges to placed vertices (then fewer candidates, then id)
+            bool placed[kMaxK] = {false};
+            c->order[0] = r;
+            placed[r] = true;
+            for (int no = 1; no < k; no++) {
+                int best = -1, bb = -1;
+                for (int u = 0; u < k; u++) {
+                    if (placed[u] || !placed[c->parent[u]]) continue;
+                    int b = 0;
+                    for (int w = 0; w < k; w++) b += (placed[w] && A[u][w]) ? 1 : 0;
+                    if (best < 0 || b > bb ||
+                        (b == bb && (c->ncand[u] < c->ncand[best] || (c->ncand[u] == c->ncand[best] && u < best)))) {
+                        best = u;
+                        bb = b;
+                    }
+                }
+                c->order[no] = best;
+                placed[best] = true;
+            }
+            for (int i = 0; i < k; i++) c->pos[c->order[i]] = i;
+        } else {
             int stack[kMaxK], sp = 0, no = 0;
             stack[sp++] = r;
             while (sp) {

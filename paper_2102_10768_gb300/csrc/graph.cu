@@ -56,6 +56,7 @@ extern "C" void fast_config_default(fast_config* cfg) {
     cfg->time_budget_s = 0.0;
     cfg->limit = 0;
     cfg->queue_cells = 0;
+    cfg->order_rule = 0;
 }
 
 namespace {

@@ -67,9 +67,14 @@ struct MatchPlan {
 
 enum : int { kStatusTimeout = 1, kStatusOverflow = 2, kStatusLimit = 4 };
 // shared words per warp: survivors [32 depths][32], m and data vertex per
-// position, then one 8-byte cursor per non-tree edge of the query
-constexpr int kWarpBaseWords = kMaxK * 32 + 2 * kMaxK;
+// position, the generator list of each depth, an 8-byte tree-list cursor per
+// depth, then one 8-byte cursor per non-tree edge of the query
+constexpr int kWarpBaseWords = kMaxK * 32 + 3 * kMaxK + 2 * kMaxK;
+// Chunk.pad: bit 0 = a donated run; bits 1-6 = the list the run belongs to
+// (0: the tree list of position j; s: the s-th non-tree edge into j); the
+// query of a batch from bit 8 up.
 constexpr uint32_t kDonated = 1;
+__device__ __forceinline__ int run_source(uint32_t pad) { return (int)((pad >> 1) & 63u); }
 constexpr unsigned long long kIdleNs = 5ull * 1000 * 1000 * 1000;     // an idle warp gives up waiting
 
 struct MatchOut {
@@ -265,7 +270,9 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
     uint32_t* sbuf = smem + (size_t)warp * warp_words;                   // [depth][32]
     uint32_t* sm = sbuf + kMaxK * 32;                                   // m[position]
     int32_t* sg = (int32_t*)(sm + kMaxK);                               // data vertex per position
-    int64_t* ncur = (int64_t*)(sg + kMaxK);                              // per non-tree edge: list cursor
+    int32_t* gsrc = sg + kMaxK;                                          // per depth: generator list (as Chunk.pad)
+    int64_t* tcur = (int64_t*)(gsrc + kMaxK);                            // per depth: tree-list cursor
+    int64_t* ncur = tcur + kMaxK;                                        // per non-tree edge: list cursor
     unsigned long long iter = 0;
     const unsigned long long deadline = *O.deadline;
     unsigned long long lb = 0;             // this lane's bytes requested (entries of 4 B, offsets of 8 B)
@@ -343,14 +350,27 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
             int64_t seg_next = 0, seg_end = 0, seg_base = 0;   // lane d: depth d's list scan
             uint32_t bcnt = 0, bcur = 0;                        // lane d: buffered survivors
             {
+                // the run [a, b) is of the tree list of position j, or of a non-tree
+                // list into j (a donated run of a depth that generated from it)
+                const int src = run_source(ch_pad);
                 int64_t base = 0;
-                if (j > 0) {
-                    uint32_t mp = __shfl_sync(0xffffffffu, m_reg, P.par[j]);
-                    base = P.t_off[j][mp];
+                if (src == 0) {
+                    if (j > 0) {
+                        uint32_t mp = __shfl_sync(0xffffffffu, m_reg, P.par[j]);
+                        base = P.t_off[j][mp];
+                    }
+                } else {
+                    const int e = P.nt_begin[j] + src - 1;
+                    uint32_t mf = __shfl_sync(0xffffffffu, m_reg, P.nt_from[e]);
+                    base = P.n_off[e][mf];
                 }
                 int64_t lo = base + ch_a, hi = base + ch_b;
                 if (lane == d) { seg_next = lo; seg_end = hi; seg_base = base; }
-                if (lane == 0) lb += (j > 0 ? 16 : 0) + 16ull * (P.nt_begin[j + 1] - P.nt_begin[j]);
+                if (lane == 0) {
+                    gsrc[j] = src;
+                    tcur[j] = 0;
+                    lb += (j > 0 ? 16 : 0) + 16ull * (P.nt_begin[j + 1] - P.nt_begin[j]);
+                }
                 for (int e = P.nt_begin[j] + lane; e < P.nt_begin[j + 1]; e += 32) ncur[e] = 0;
                 __syncwarp();
             }
@@ -408,7 +428,7 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                                     dst->j = dd;
                                     dst->a = (uint32_t)(mid - sb_);
                                     dst->b = (uint32_t)(se_ - sb_);
-                                    dst->pad = kDonated | (q << 8);
+                                    dst->pad = kDonated | ((uint32_t)gsrc[dd] << 1) | (q << 8);
                                     dst->w = 0;
                                     dst->id = 0;
                                 }
@@ -431,8 +451,38 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                     d++;
                     uint32_t mp = __shfl_sync(0xffffffffu, m_reg, P.par[d]);
                     int64_t lo = P.t_off[d][mp], hi = P.t_off[d][mp + 1];
+                    // Generator list: the candidates of depth d are the intersection of
+                    // the tree list and every non-tree list into d, all sorted over
+                    // C(u_d).  Scan the shortest and check the others (the same set; the
+                    // counting pass keeps the tree list, whose bytes the oracle pins).
+                    int src = 0;
+                    if (!STATS) {
+                        const int e0 = P.nt_begin[d], ne = P.nt_begin[d + 1] - e0;
+                        if (ne > 0) {
+                            uint32_t mf = __shfl_sync(0xffffffffu, m_reg, lane < ne ? P.nt_from[e0 + lane] : 0);
+                            int64_t elo = 0, elen = 0;
+                            uint32_t key = 0xFFFFFFFFu;           // (length, lane), lists shorter than the tree list
+                            if (lane < ne) {
+                                elo = P.n_off[e0 + lane][mf];
+                                elen = P.n_off[e0 + lane][mf + 1] - elo;
+                                if (elen < hi - lo)
+                                    key = ((uint32_t)(elen < (1 << 26) ? elen : (1 << 26) - 1) << 5) | (uint32_t)lane;
+                            }
+                            uint32_t best = __reduce_min_sync(0xffffffffu, key);
+                            if (best != 0xFFFFFFFFu) {
+                                int bi = (int)(best & 31u);
+                                src = bi + 1;
+                                lo = __shfl_sync(0xffffffffu, elo, bi);
+                                hi = lo + __shfl_sync(0xffffffffu, elen, bi);
+                            }
+                        }
+                    }
                     if (lane == d) { seg_next = lo; seg_end = hi; seg_base = lo; bcnt = 0; bcur = 0; }
-                    if (lane == 0) lb += 16 + 16ull * (P.nt_begin[d + 1] - P.nt_begin[d]);
+                    if (lane == 0) {
+                        gsrc[d] = src;
+                        tcur[d] = 0;
+                        lb += 16 + 16ull * (P.nt_begin[d + 1] - P.nt_begin[d]);
+                    }
                     for (int e = P.nt_begin[d] + lane; e < P.nt_begin[d + 1]; e += 32) ncur[e] = 0;
                     __syncwarp();
                     continue;
@@ -444,12 +494,25 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                     int64_t idx = sn + lane;
                     bool ok = idx < se;
                     uint32_t cnd = 0;
+                    const int src = gsrc[d];
+                    const int gen_e = P.nt_begin[d] + src - 1;          // the generating non-tree edge (src > 0)
                     if (ok) {
-                        cnd = (d == 0) ? (uint32_t)idx : __ldg(P.t_idx[d] + idx);
+                        cnd = (d == 0) ? (uint32_t)idx : __ldg((src == 0 ? P.t_idx[d] : P.n_idx[gen_e]) + idx);
                         if (d > 0) lb += 4;
+                    }
+                    // a non-tree list generates: the tree list is checked like the others
+                    if (src != 0 && __any_sync(0xffffffffu, ok)) {
+                        uint32_t mp = __shfl_sync(0xffffffffu, m_reg, P.par[d]);
+                        int64_t lo = P.t_off[d][mp], hi = P.t_off[d][mp + 1];
+                        int64_t cur = lo + tcur[d];
+                        ok = warp_member(P.t_idx[d], lo, hi, &cur, cnd, ok, &lb);
+                        __syncwarp();
+                        if (lane == 0) tcur[d] = cur - lo;
+                        __syncwarp();
                     }
                     // EdgeValidator (most selective edge first; stop once no lane is pending)
                     for (int e = P.nt_begin[d]; e < P.nt_begin[d + 1]; e++) {
+                        if (e == gen_e) continue;
                         if (!__any_sync(0xffffffffu, ok)) break;
                         uint32_t mf = __shfl_sync(0xffffffffu, m_reg, P.nt_from[e]);
                         int64_t lo = P.n_off[e][mf], hi = P.n_off[e][mf + 1];

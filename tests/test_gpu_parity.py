@@ -203,6 +203,66 @@ def test_degenerate_queries(er):
     _check_match(g, o, [2, 2, 2], [[0, 1], [1, 2], [0, 2]])
 
 
+# ------------------------------------------- matching order: greedy rule
+
+GREEDY = dict(order_rule=1)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_cst_random_greedy_order(seed):
+    """The greedy order (fast_config.order_rule = 1) against the oracle's
+    restatement of the same rule: root, t_q, order, candidate sets, tree and
+    non-tree lists (their direction follows the order), workload."""
+    n, e, lab, ql, qe = rand_case(1000 + seed)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    compare_cst(F.Cst(g, ql, qe, F.default_config(**GREEDY)), oracle.Cst(o, ql, qe, order="greedy"), len(ql))
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_match_random_greedy_order(seed):
+    """Counts and embedding sets do not depend on the order."""
+    n, e, lab, ql, qe = rand_case(2000 + seed)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    cst = F.Cst(g, ql, qe, F.default_config(**GREEDY))
+    want = oracle.match(o, ql, qe, max_emb=1 << 20)
+    r = F.match(cst)
+    assert r["count"] == want["count"]
+    if want["count"] <= 200_000:
+        r2 = F.match(cst, k=want["count"] + 3)
+        assert np.array_equal(sorted_rows(r2["emb"][:r2["written"]].astype(np.int32)), want["emb"])
+
+
+def test_er_queries_greedy_order(er):
+    w, g, o = er
+    for q in w.queries:
+        gc = F.Cst(g, q.labels, q.edges, F.default_config(**GREEDY))
+        compare_cst(gc, oracle.Cst(o, q.labels, q.edges, order="greedy"), q.k)
+        assert F.match(gc)["count"] == oracle.count(o, q.labels, q.edges)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_partition_matches_oracle_greedy_order(seed):
+    n, e, lab, ql, qe = rand_case(4000 + seed, n_lo=60, n_hi=250, k_hi=6, L_hi=3)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    gc, oc = F.Cst(g, ql, qe, F.default_config(**GREEDY)), oracle.Cst(o, ql, qe, order="greedy")
+    if gc.W == 0:
+        return
+    total = oracle.count(o, ql, qe)
+    for div in (7, 50):
+        delta = max(1, gc.W // div)
+        ch = F.Chunks(gc, F.default_config(delta_w=delta, sample_seed=seed, **GREEDY))
+        assert gpu_chunks_global(gc, ch) == oc.partition(delta, 0.0, 0.0, seed)
+        assert F.match(gc, ch)["count"] == total
+
+
+def test_order_rule_rejected_when_unknown(er):
+    w, g, o = er
+    q = w.queries[0]
+    with pytest.raises(F.FastError) as ei:
+        F.Cst(g, q.labels, q.edges, F.default_config(order_rule=2))
+    assert ei.value.code == F.FAST_ERR_INVALID
+
+
 # --------------------------------------------------------------- partition
 
 @pytest.mark.parametrize("seed", range(15))

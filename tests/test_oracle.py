@@ -460,3 +460,55 @@ def test_partition_cap_keeps_chunks_disjoint_and_complete(seed):
             assert len(chunks) == cap
             assert all(j == 0 for (j, pre, a, b, w, i) in chunks)
             assert sorted((a, b) for (j, pre, a, b, w, i) in chunks)[0][0] == 0
+
+
+# ------------------------------------------------- matching order (greedy)
+
+def _tree_par(c):
+    """Per position of c.order, the position of its t_q parent (0 at the root)."""
+    pos = {int(u): i for i, u in enumerate(c.order)}
+    return [pos[int(c.parent[int(u)])] if c.parent[int(u)] >= 0 else 0 for u in c.order]
+
+
+def test_greedy_order_house_in_k6():
+    """Hand-worked: the 'house' query (square 0-1-2-3 plus roof 4 on 0 and
+    1) in K6.  Every C0 is all six vertices, so the root is 0 (ties with 1
+    at 6/3, smaller id) and t_q is 0 -> {1, 3, 4}, 1 -> {2}.  Path-based:
+    0, then its children by (|C|, id) with 1's subtree first: 0 1 2 3 4.
+    Greedy: after 0 the frontier 1, 3, 4 has one edge each (1 by id); then
+    4 has two edges to {0, 1} against one for 2 and 3; then 2 before 3 by
+    id: 0 1 4 2 3.  Either order finds 6!/1! = 720 embeddings."""
+    n = 6
+    edges = [[a, b] for a in range(n) for b in range(a + 1, n)]
+    g = oracle.Graph(n, edges, [0] * n)
+    ql, qe = [0] * 5, [[0, 1], [1, 2], [2, 3], [3, 0], [0, 4], [1, 4]]
+    path = oracle.Cst(g, ql, qe)
+    greedy = oracle.Cst(g, ql, qe, order="greedy")
+    assert path.root == greedy.root == 0
+    assert path.parent.tolist() == greedy.parent.tolist() == [-1, 0, 1, 0, 0]
+    assert path.order.tolist() == [0, 1, 2, 3, 4]
+    assert greedy.order.tolist() == [0, 1, 4, 2, 3]
+    for c in (path, greedy):
+        assert oracle.count(g, ql, qe, order=c.order.tolist(), par=_tree_par(c)) == 720
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_greedy_order_is_connected_and_count_invariant(seed):
+    """Every vertex follows its t_q parent (so the CST's tree lists apply);
+    matching in the greedy order finds the same embeddings, and the CST is
+    the same one but for the direction of the non-tree lists."""
+    n, edges, labels, ql, qe = _cst_case(seed)
+    g = oracle.Graph(n, edges, labels)
+    path = oracle.Cst(g, ql, qe)
+    greedy = oracle.Cst(g, ql, qe, order="greedy")
+    k = len(ql)
+    pos = {int(u): i for i, u in enumerate(greedy.order)}
+    assert sorted(pos) == list(range(k)) and int(greedy.order[0]) == greedy.root
+    for u in range(k):
+        if greedy.parent[u] >= 0:
+            assert pos[int(greedy.parent[u])] < pos[u]
+    for u in range(k):
+        assert np.array_equal(path.cand(u), greedy.cand(u))
+    want = oracle.count(g, ql, qe)
+    assert oracle.count(g, ql, qe, order=greedy.order.tolist(), par=_tree_par(greedy)) == want
+    assert greedy.workload()[1] == path.workload()[1]
