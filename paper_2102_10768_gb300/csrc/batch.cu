@@ -83,6 +83,7 @@ struct fast_batch {
     uint64_t g_cells = 0;
     unsigned char* g_chunks = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<ScratchPool*> pools;      // per build thread: scratch of its CSTs and partitions
     double last_build_ms = 0.0, last_match_ms = 0.0;
     uint64_t last_bytes = 0;
     int64_t last_chunks = 0;
@@ -115,6 +116,7 @@ void batch_release(fast_batch* b) {
     if (b->h_qtotal) cudaFreeHost(b->h_qtotal);
     if (b->h_ctr) cudaFreeHost(b->h_ctr);
     for (auto st : b->ws) cudaStreamDestroy(st);
+    for (auto p : b->pools) pool_delete(p);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     delete b;
@@ -139,6 +141,7 @@ int batch_create(const fast_graph* g, const fast_config* cfg, int32_t max_q, int
         for (auto& st : b->ws)
             if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "stream create"); break; }
         if (rc) break;
+        for (int w = 0; w < b->nthreads; w++) b->pools.push_back(pool_new());
         rc = dalloc(&b->d_plans, (size_t)max_q * b->psize, s); if (rc) break;
         rc = dalloc(&b->d_off, max_q + 1, s); if (rc) break;
         rc = dalloc(&b->d_nchunks, 1, s); if (rc) break;
@@ -218,6 +221,7 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
         for (int w = 0; w < T; w++) {
             pool.emplace_back([&, w]() {
                 cudaSetDevice(b->device);
+                PoolScope scratch(b->ws[w], b->pools[w]);
                 for (;;) {
                     int i = next.fetch_add(1);
                     if (i >= nq) break;
@@ -289,9 +293,11 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
         b->last_match_ms = ms;
     } while (0);
     int gst = match_status_of(b->h_ctr, &b->last_bytes);
+    cudaStreamSynchronize(s);               // no gather copy may still read a chunk list
     for (int i = 0; i < nq; i++) {
-        if (chs[i]) fast_free_chunks(chs[i]);
-        if (csts[i]) fast_free_cst(csts[i]);
+        // the matcher is done (or never ran); the builders' streams stay ordered
+        chunks_release_nosync(chs[i]);
+        cst_release_nosync(csts[i]);
     }
     if (rc != FAST_OK) return rc;
     uint64_t limit = b->base.limit;

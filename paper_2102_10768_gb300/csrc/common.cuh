@@ -3,6 +3,8 @@
 // device utilities.  Nothing here is part of the C ABI (see include/fast.h).
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -34,10 +36,43 @@ int cuda_status(cudaError_t e, const char* what, const char* file, int line);
         if (_rc != FAST_OK) return _rc;   \
     } while (0)
 
-// Stream-ordered device allocation; n == 0 yields a valid 256-byte block so
-// that kernels may always receive a non-null pointer.
+// ------------------------------------------------------- device memory
+//
+// dalloc/dfree: temporaries.  Inside a PoolScope they come from the bound
+// ScratchPool (pool.cu); elsewhere from the stream-ordered allocator.
+// dalloc_direct/dfree_direct: memory that outlives the call (always the
+// stream-ordered allocator).  Arena: a CST's own arrays, bump-allocated from
+// a few large blocks and returned together.
+struct ScratchPool;
+ScratchPool* pool_new();
+void pool_delete(ScratchPool* p);
+ScratchPool* pool_active();                                  // bound to this thread, or null
+int pool_alloc(ScratchPool* p, void** out, size_t bytes);
+bool pool_free(ScratchPool* p, void* ptr);                   // false: not from this pool
+
+// Binds a pool to this thread for a scope: `p`, else the one already bound,
+// else this thread's default pool for the current device.  On exit, if the
+// pool handed out memory meanwhile, synchronises `s`: a region freed in the
+// scope may still be read by work queued on `s`, and must be idle before the
+// pool serves any other call.
+class PoolScope {
+  public:
+    explicit PoolScope(cudaStream_t s, ScratchPool* p = nullptr);
+    ~PoolScope();
+    PoolScope(const PoolScope&) = delete;
+    PoolScope& operator=(const PoolScope&) = delete;
+
+  private:
+    ScratchPool* prev_;
+    ScratchPool* cur_;
+    cudaStream_t s_;
+    uint64_t mark_;
+};
+
+// n == 0 yields a valid 256-byte block so that kernels may always receive a
+// non-null pointer.
 template <class T>
-inline int dalloc(T** p, size_t n, cudaStream_t s) {
+inline int dalloc_direct(T** p, size_t n, cudaStream_t s) {
     size_t bytes = n * sizeof(T);
     if (bytes == 0) bytes = 256;
     cudaError_t e = cudaMallocAsync((void**)p, bytes, s);
@@ -51,10 +86,60 @@ inline int dalloc(T** p, size_t n, cudaStream_t s) {
 }
 
 template <class T>
-inline void dfree(T*& p, cudaStream_t s) {
+inline void dfree_direct(T*& p, cudaStream_t s) {
     if (p) cudaFreeAsync((void*)p, s);
     p = nullptr;
 }
+
+template <class T>
+inline int dalloc(T** p, size_t n, cudaStream_t s) {
+    if (ScratchPool* sp = pool_active()) {
+        size_t bytes = n * sizeof(T);
+        return pool_alloc(sp, (void**)p, bytes ? bytes : 256);
+    }
+    return dalloc_direct(p, n, s);
+}
+
+template <class T>
+inline void dfree(T*& p, cudaStream_t s) {
+    if (p) {
+        ScratchPool* sp = pool_active();
+        if (!sp || !pool_free(sp, (void*)p)) cudaFreeAsync((void*)p, s);
+    }
+    p = nullptr;
+}
+
+class Arena {
+  public:
+    template <class T>
+    int alloc(T** p, size_t n, cudaStream_t s) {
+        size_t bytes = n * sizeof(T);
+        bytes = bytes ? (bytes + 255) / 256 * 256 : 256;
+        if (bytes > left_) {
+            int rc = grow(bytes, s);
+            if (rc != FAST_OK) { *p = nullptr; return rc; }
+        }
+        *p = (T*)cur_;
+        cur_ += bytes;
+        left_ -= bytes;
+        return FAST_OK;
+    }
+    // one block of exactly `bytes` (256-byte multiple) when the arena is empty
+    template <class T>
+    int alloc_exact(T** p, size_t bytes, cudaStream_t s) {
+        if (blocks_.empty() && bytes > 0) next_ = (bytes + 255) / 256 * 256;
+        *p = nullptr;
+        return alloc((unsigned char**)p, bytes, s);
+    }
+    void release(cudaStream_t s);
+
+  private:
+    int grow(size_t bytes, cudaStream_t s);
+    std::vector<void*> blocks_;
+    char* cur_ = nullptr;
+    size_t left_ = 0;
+    size_t next_ = 16ull << 20;
+};
 
 inline int num_sms() {
     static int sms = 0;

@@ -126,6 +126,7 @@ struct TopDownF {
     }
     __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? row : -1; }
     __device__ void at(int64_t r, int64_t rank) const { t_off[r] = rank; }
+    __device__ int64_t end() const { return *E; }
 };
 
 // Non-tree: flattened neighbour lists of C(u_j); keeps members of C(u_i)
@@ -160,6 +161,7 @@ struct NonTreeF {
     }
     __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? row : -1; }
     __device__ void at(int64_t r, int64_t rank_) const { n_off[r] = rank_; }
+    __device__ int64_t end() const { return *E; }
 };
 
 // candidate ids from a bitmap, in id order
@@ -180,6 +182,8 @@ struct KeepRowsF {
     using value_type = int32_t;
     const int32_t* ids;
     const uint8_t* valid;
+    const int64_t* nrows;      // rows really present (the index space is a bound)
+    __device__ int64_t end() const { return *nrows; }
     __device__ void begin(int64_t) {}
     __device__ bool eval(int64_t i, int32_t& v) const {
         v = ids[i];
@@ -289,6 +293,7 @@ struct WriteAliveF {
     }
     __device__ int64_t tag(int64_t i) const { return (i < e_end && i == off[row] && valid[row]) ? row : -1; }
     __device__ void at(int64_t r, int64_t rk) const { new_off[newrow[r]] = rk; }
+    __device__ int64_t end() const { return off[*nrows]; }
 };
 
 __device__ __forceinline__ uint64_t warp_sat_sum(uint64_t v) {
@@ -415,12 +420,7 @@ struct Bits {
 
 void cst_release(fast_cst* c) {
     if (!c) return;
-    cudaStream_t s = c->stream;
-    for (int u = 0; u < kMaxK; u++) {
-        dfree(c->cand[u], s); dfree(c->t_off[u], s); dfree(c->t_idx[u], s);
-        dfree(c->cval[u], s); dfree(c->cvalf[u], s); dfree(c->ssum[u], s);
-    }
-    for (int e = 0; e < c->nnt; e++) { dfree(c->n_off[e], s); dfree(c->n_idx[e], s); }
+    c->arena.release(c->stream);
     delete c;
 }
 
@@ -449,6 +449,103 @@ int validate_query(const fast_query_desc* q, int A[kMaxK][kMaxK], int* dq) {
     }
     if (cnt != k) return set_error(FAST_ERR_INVALID, "query graph is disconnected");
     return FAST_OK;
+}
+
+// ------------------------------------------------ exact-size CST storage
+
+// One flat copy list: descriptor d moves bytes [0, n_d) from src_d to dst_d;
+// piece_off[d] is the first 64 KB piece of d in a flat piece space.
+struct CopyDesc {
+    const unsigned char* src;
+    unsigned char* dst;
+    uint64_t bytes;
+    uint64_t piece_off;
+};
+constexpr uint64_t kPiece = 64 << 10;
+
+__global__ void k_copy_many(const CopyDesc* __restrict__ d, int nd, uint64_t npieces) {
+    for (uint64_t p = blockIdx.x; p < npieces; p += gridDim.x) {
+        int lo = 0, hi = nd;                                  // last d with piece_off <= p
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (d[mid].piece_off <= p) lo = mid; else hi = mid;
+        }
+        const CopyDesc& c = d[lo];
+        uint64_t a = (p - c.piece_off) * kPiece, b = a + kPiece < c.bytes ? a + kPiece : c.bytes;
+        // both ends are 256-byte aligned and a is a multiple of kPiece: 16-byte words, then a byte tail
+        uint64_t a16 = a / 16, b16 = b / 16;
+        const uint4* s4 = (const uint4*)c.src;
+        uint4* d4 = (uint4*)c.dst;
+        for (uint64_t i = a16 + threadIdx.x; i < b16; i += blockDim.x) d4[i] = s4[i];
+        for (uint64_t i = b16 * 16 + threadIdx.x; i < b; i += blockDim.x) c.dst[i] = c.src[i];
+    }
+}
+
+// After the last round trip every size is known: copy the CST's arrays into
+// one exact-size block of its arena with one kernel.  The build buffers stay
+// with the caller, who frees them.
+int cst_to_arena(fast_cst* c, cudaStream_t s) {
+    struct Item { void** slot; uint64_t bytes; };
+    std::vector<Item> items;
+    const int k = c->k;
+    for (int u = 0; u < k; u++) {
+        const uint64_t nc = (uint64_t)c->ncand[u];
+        items.push_back({(void**)&c->cand[u], nc * 4});
+        items.push_back({(void**)&c->cval[u], nc * 8});
+        items.push_back({(void**)&c->cvalf[u], nc * 8});
+        if (c->parent[u] >= 0) {
+            const uint64_t np = (uint64_t)c->ncand[c->parent[u]];
+            items.push_back({(void**)&c->t_off[u], (np + 1) * 8});
+            items.push_back({(void**)&c->t_idx[u], (uint64_t)c->t_entries[u] * 4});
+            items.push_back({(void**)&c->ssum[u], np * 8});
+        }
+    }
+    for (int e = 0; e < c->nnt; e++) {
+        const uint64_t nf = (uint64_t)c->ncand[c->nt_from[e]];
+        items.push_back({(void**)&c->n_off[e], (nf + 1) * 8});
+        items.push_back({(void**)&c->n_idx[e], (uint64_t)c->n_entries[e] * 4});
+    }
+    uint64_t total = 0;
+    for (auto& it : items) total += (std::max<uint64_t>(it.bytes, 1) + 255) / 256 * 256;
+    unsigned char* base = nullptr;
+    FAST_TRY(c->arena.alloc_exact(&base, total, s));
+    std::vector<CopyDesc> h;
+    uint64_t at = 0, pieces = 0;
+    for (auto& it : items) {
+        unsigned char* dst = base + at;
+        at += (std::max<uint64_t>(it.bytes, 1) + 255) / 256 * 256;
+        if (it.bytes) {
+            h.push_back({(const unsigned char*)*it.slot, dst, it.bytes, pieces});
+            pieces += (it.bytes + kPiece - 1) / kPiece;
+        }
+        c->build_tmp.push_back(*it.slot);
+        *it.slot = dst;
+    }
+    if (h.empty()) return FAST_OK;
+    CopyDesc* d = nullptr;
+    FAST_TRY(dalloc(&d, h.size(), s));
+    FAST_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(CopyDesc), cudaMemcpyHostToDevice, s));
+    unsigned grid = (unsigned)std::min<uint64_t>(pieces, (uint64_t)num_sms() * 8);
+    k_copy_many<<<grid, 256, 0, s>>>(d, (int)h.size(), pieces);
+    note_launch();
+    int rc = cudaGetLastError() == cudaSuccess ? FAST_OK : set_error(FAST_ERR_CUDA, "CST copy launch");
+    dfree(d, s);
+    return rc;
+}
+
+// Frees the build's buffers of the CST arrays: those cst_to_arena replaced
+// (kept in build_tmp), or, if it did not run, the arrays themselves.
+void free_build_arrays(fast_cst* c, cudaStream_t s) {
+    if (!c->build_tmp.empty()) {
+        for (void* p : c->build_tmp) dfree(p, s);
+        c->build_tmp.clear();
+        return;
+    }
+    for (int u = 0; u < kMaxK; u++) {
+        dfree(c->cand[u], s); dfree(c->t_off[u], s); dfree(c->t_idx[u], s);
+        dfree(c->cval[u], s); dfree(c->cvalf[u], s); dfree(c->ssum[u], s);
+    }
+    for (int e = 0; e < kMaxNT; e++) { dfree(c->n_off[e], s); dfree(c->n_idx[e], s); }
 }
 
 // Lists whose upper bound exceeds this many entries are sized exactly (one
@@ -617,7 +714,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
                 if (rows > 0) { k_valid_rows_n<<<grid_for(rows, 256), 256, 0, s>>>(cf, n_u, rows, valid, newrow); note_launch(); }
                 rc = scan_exclusive<int64_t>(newrow, newrow, rows, newrow + rows, s); if (rc) break;
                 rc = dalloc(&c->cand[u], rows, s); if (rc) break;
-                KeepRowsF kf{td_cand[u], valid};
+                KeepRowsF kf{td_cand[u], valid, n_u};
                 rc = compact(kf, rows, c->cand[u], sz + kMaxK + u, s); if (rc) break;
                 for (int i = 0; i < nch && rc == FAST_OK; i++) {
                     int w = ch[i];
@@ -773,9 +870,12 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
             k_total_w<<<1, 1024, 0, s>>>(c->cval[r], c->cvalf[r], c->ncand[r], w_d, (double*)(w_d + 1));
             note_launch();
             int64_t hs[kSzWords];
+            int lb_err = 0;
             cudaError_t e1 = cudaMemcpyAsync(hs, sz, sizeof(hs), cudaMemcpyDeviceToHost, s);
+            if (e1 == cudaSuccess) e1 = cudaMemcpyFromSymbolAsync(&lb_err, g_lookback_err, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
             cudaError_t e2 = cudaStreamSynchronize(s);
             if (e1 != cudaSuccess || e2 != cudaSuccess) { rc = cuda_status(e2 != cudaSuccess ? e2 : e1, "fast_build_cst", __FILE__, __LINE__); break; }
+            if (lb_err) { rc = set_error(FAST_ERR_CUDA, "fast_build_cst: a compaction's look-back wait ran out"); break; }
             for (int u = 0; u < k; u++) c->t_entries[u] = c->parent[u] < 0 ? 0 : hs[2 * kMaxK + u];
             for (int e = 0; e < c->nnt; e++) c->n_entries[e] = hs[3 * kMaxK + e];
             memcpy(&c->W, &hs[3 * kMaxK + kMaxNT + 1], sizeof(uint64_t));
@@ -788,6 +888,9 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         dfree(bits[u].alive, s); dfree(bits[u].rank, s);
     }
     dfree(e_off, s); dfree(cnt_d, s); dfree(dq_d, s); dfree(lo_d, s); dfree(sz, s);
+    // The lists were built in buffers sized by bounds; keep exact copies.
+    if (rc == FAST_OK) rc = cst_to_arena(c, s);
+    free_build_arrays(c, s);
     if (rc != FAST_OK) {
         cst_release(c);
         return rc;
@@ -802,6 +905,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
 
 extern "C" int fast_build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* cfg, void* stream,
                               fast_cst** out) {
+    PoolScope scratch((cudaStream_t)stream);
     return build_cst(g, q, cfg, (cudaStream_t)stream, out);
 }
 
@@ -875,6 +979,10 @@ extern "C" int fast_cst_workload(const fast_cst* c, int32_t u, uint64_t* out, vo
     FAST_CUDA(cudaStreamSynchronize(s));
     return FAST_OK;
 }
+
+namespace fast {
+void cst_release_nosync(fast_cst* c) { cst_release(c); }
+}  // namespace fast
 
 extern "C" void fast_free_cst(fast_cst* c) {
     if (!c) return;

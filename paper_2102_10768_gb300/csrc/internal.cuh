@@ -55,6 +55,8 @@ struct fast_cst {
     double Wf = 0.0;
     fast_config cfg;
     cudaStream_t stream = nullptr;
+    fast::Arena arena;         // every array above lives in it (exact sizes)
+    std::vector<void*> build_tmp;   // during fast_build_cst: bounded buffers replaced by exact copies
 };
 
 // One chunk of a partitioned CST (Sec. IV-B): positions 0..j-1 fixed to one
@@ -76,3 +78,10 @@ struct fast_chunks {
     uint64_t w_sum = 0;
     cudaStream_t stream = nullptr;
 };
+
+namespace fast {
+// Stream-ordered release without the synchronisation of the public free
+// calls, for callers whose streams are already idle or stay ordered.
+void cst_release_nosync(fast_cst* c);
+void chunks_release_nosync(fast_chunks* ch);
+}  // namespace fast

@@ -661,6 +661,7 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
     if (!c) return set_error(FAST_ERR_INVALID, "fast_match: cst is NULL");
     if (kemb > 0 && !emb_out) return set_error(FAST_ERR_INVALID, "fast_match: k > 0 needs emb_out");
     if (chunks && chunks->c != c) return set_error(FAST_ERR_INVALID, "fast_match: chunks belong to another CST");
+    PoolScope scratch(s);                        // counters, donation ring, staging: temporaries
     fast_config cfg = cfg_in ? *cfg_in : c->cfg;
     int warps = cfg.warps_per_block > 0 ? cfg.warps_per_block : 8;
     if (warps > 8) warps = 8;

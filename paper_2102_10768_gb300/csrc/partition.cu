@@ -372,7 +372,7 @@ int partition(const fast_cst* c, const fast_config* cfg_in, cudaStream_t s, fast
     if (rc == FAST_OK) {
         ch = new fast_chunks();
         ch->c = c; ch->n = total; ch->stream = s;
-        rc = dalloc(&ch->d, total, s);
+        rc = dalloc_direct(&ch->d, total, s);            // outlives the call
         int64_t o = 0;
         for (auto& lv : levels) {
             if (rc != FAST_OK) break;
@@ -393,7 +393,7 @@ int partition(const fast_cst* c, const fast_config* cfg_in, cudaStream_t s, fast
         if (ch) ch->w_sum = ws;
     }
     if (rc != FAST_OK) {
-        if (ch) { dfree(ch->d, s); delete ch; }
+        if (ch) { dfree_direct(ch->d, s); delete ch; }
         return rc;
     }
     *out = ch;
@@ -403,6 +403,7 @@ int partition(const fast_cst* c, const fast_config* cfg_in, cudaStream_t s, fast
 }  // namespace
 
 extern "C" int fast_partition(const fast_cst* c, const fast_config* cfg, void* stream, fast_chunks** out) {
+    PoolScope scratch((cudaStream_t)stream);
     return partition(c, cfg, (cudaStream_t)stream, out);
 }
 
@@ -432,10 +433,18 @@ extern "C" int fast_chunks_copy(const fast_chunks* ch, int32_t* j, int32_t* pref
     return FAST_OK;
 }
 
+namespace fast {
+void chunks_release_nosync(fast_chunks* ch) {
+    if (!ch) return;
+    dfree_direct(ch->d, ch->stream);
+    delete ch;
+}
+}  // namespace fast
+
 extern "C" void fast_free_chunks(fast_chunks* ch) {
     if (!ch) return;
     cudaStream_t s = ch->stream;
-    dfree(ch->d, s);
+    dfree_direct(ch->d, s);
     delete ch;
     cudaStreamSynchronize(s);
 }

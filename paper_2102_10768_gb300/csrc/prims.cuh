@@ -4,6 +4,7 @@
 // with cudaMallocAsync on the caller's stream.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 #include <utility>
 
@@ -177,30 +178,125 @@ __global__ void k_compact_write(F f, int64_t n, const int64_t* __restrict__ offs
 }
 
 // Runs the two passes; *count_dev receives the kept count (device memory).
+// A functor may know, on the device, where its index space really ends (the
+// host passes a bound): `__device__ int64_t end() const`.
+template <class F, class = void>
+struct has_end : std::false_type {};
+template <class F>
+struct has_end<F, std::void_t<decltype(std::declval<const F&>().end())>> : std::true_type {};
+
+template <class F>
+__device__ __forceinline__ int64_t index_end(const F& f, int64_t n) {
+    if constexpr (has_end<F>::value) {
+        int64_t e = f.end();
+        return e < n ? e : n;
+    } else {
+        return n;
+    }
+}
+
+// Single-pass ordered compaction with decoupled look-back.  Blocks take
+// tiles of kCompTile indices in order from a counter and stop at the index
+// space's real end.  Each tile publishes its kept count (flag AGG), finds
+// its exclusive offset by summing predecessors back to the first one whose
+// inclusive prefix is known (flag PRE), publishes its own prefix, then
+// writes.  A tile only waits on tiles taken before it, by blocks that are
+// already running, so the wait ends; it is still bounded, and running out
+// sets g_lookback_err (never expected), which the caller turns into an error.
+constexpr unsigned long long kLbAgg = 1ull << 62, kLbPre = 2ull << 62, kLbVal = (1ull << 62) - 1;
+constexpr int kLbSpins = 1 << 24;
+static __device__ int g_lookback_err;
+
+__device__ __forceinline__ int64_t lookback_prefix(unsigned long long* st, int64_t t) {
+    int64_t excl = 0;
+    for (int64_t p = t - 1; p >= 0; p--) {
+        unsigned long long w = 0;
+        int spins = 0;
+        for (;;) {
+            w = *(volatile unsigned long long*)(st + p);
+            if (w >> 62) break;
+            if (++spins > kLbSpins) { atomicExch(&g_lookback_err, 1); return excl; }
+            __nanosleep(32);
+        }
+        excl += (int64_t)(w & kLbVal);
+        if ((w >> 62) == 2) break;
+    }
+    return excl;
+}
+
+template <class F>
+__global__ void __launch_bounds__(kCompBlock) k_compact_1p(F f, int64_t n, typename F::value_type* __restrict__ out,
+                                                           int64_t* __restrict__ count, unsigned long long* __restrict__ st,
+                                                           unsigned int* __restrict__ tile_ctr) {
+    __shared__ int64_t tmp[kCompBlock / 32 + 1];
+    __shared__ int64_t s_t, s_excl, s_end;
+    if (threadIdx.x == 0) s_end = index_end(f, n);
+    for (;;) {
+        if (threadIdx.x == 0) s_t = (int64_t)atomicAdd(tile_ctr, 1u);
+        __syncthreads();
+        const int64_t t = s_t, end = s_end;
+        const int64_t tb = t * kCompTile;
+        if (tb >= end) {
+            if (t == 0 && threadIdx.x == 0 && count) *count = 0;     // empty index space
+            break;
+        }
+        const int64_t base = tb + (int64_t)threadIdx.x * kCompItems;
+        int64_t v[kCompItems];
+        typename F::value_type val[kCompItems];
+        int64_t tg[kCompItems];
+        F g = f;
+        g.begin(base);
+#pragma unroll
+        for (int i = 0; i < kCompItems; i++) {
+            v[i] = (base + i < end && g.eval(base + i, val[i])) ? 1 : 0;
+            tg[i] = (base + i < end) ? g.tag(base + i) : -1;
+        }
+        int64_t hit[kCompItems];
+#pragma unroll
+        for (int i = 0; i < kCompItems; i++) hit[i] = v[i];
+        const int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kCompItems>(v, tmp);
+        if (threadIdx.x == 0) {
+            int64_t excl = 0;
+            if (t == 0) {
+                atomicExch(st, kLbPre | (unsigned long long)tot);
+            } else {
+                atomicExch(st + t, kLbAgg | (unsigned long long)tot);
+                excl = lookback_prefix(st, t);
+                atomicExch(st + t, kLbPre | (unsigned long long)(excl + tot));
+            }
+            s_excl = excl;
+            if (tb + kCompTile >= end && count) *count = excl + tot;   // the last tile
+        }
+        __syncthreads();
+        const int64_t off = s_excl;
+#pragma unroll
+        for (int i = 0; i < kCompItems; i++) {
+            if (tg[i] >= 0) g.at(tg[i], off + v[i]);
+            if (hit[i]) out[off + v[i]] = val[i];
+        }
+        __syncthreads();
+    }
+}
+
 template <class F>
 int compact(const F& f, int64_t n, typename F::value_type* out, int64_t* count_dev, cudaStream_t s) {
     if (n <= 0) {
         if (count_dev) FAST_CUDA(cudaMemsetAsync(count_dev, 0, sizeof(int64_t), s));
         return FAST_OK;
     }
-    int64_t nb = ceil_div(n, kCompTile);
-    int64_t* offs = nullptr;
-    FAST_TRY(dalloc(&offs, nb, s));
-    k_compact_count<F><<<(unsigned)nb, kCompBlock, 0, s>>>(f, n, offs);
+    const int64_t nt = ceil_div(n, kCompTile);
+    unsigned long long* st = nullptr;                     // [nt] tile status, then the tile counter
+    FAST_TRY(dalloc(&st, nt + 1, s));
+    cudaMemsetAsync(st, 0, (nt + 1) * sizeof(unsigned long long), s);
+    const int64_t grid = std::min<int64_t>(nt, (int64_t)num_sms() * 4);
+    k_compact_1p<F><<<(unsigned)grid, kCompBlock, 0, s>>>(f, n, out, count_dev, st, (unsigned int*)(st + nt));
     note_launch();
-    int rc = cudaGetLastError() == cudaSuccess ? FAST_OK : set_error(FAST_ERR_CUDA, "compact count launch");
-    if (rc == FAST_OK) rc = scan_exclusive<int64_t>(offs, offs, nb, (int64_t*)nullptr, s);
-    if (rc == FAST_OK) {
-        k_compact_write<F><<<(unsigned)nb, kCompBlock, 0, s>>>(f, n, offs, out, count_dev);
-        note_launch();
-        if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "compact write launch");
-    }
-    dfree(offs, s);
+    int rc = cudaGetLastError() == cudaSuccess ? FAST_OK : set_error(FAST_ERR_CUDA, "compaction launch");
+    dfree(st, s);
     return rc;
 }
 
-// Size query for a compaction whose output size is not known in advance:
-// runs the counting pass only and returns the kept count on the host.
+
 template <class F>
 int compact_size(const F& f, int64_t n, int64_t* kept_host, cudaStream_t s) {
     *kept_host = 0;

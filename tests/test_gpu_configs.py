@@ -1,0 +1,147 @@
+"""Full-size parity on the batching, serving and billion-edge configurations.
+
+- Batching: 1,000 queries of 4/8/16/24/32 vertices (200 each, dense and
+  sparse mixed) on the power-law graph (Chung-Lu, exponent 2.1, 1M vertices,
+  16M edges, 16 Zipf labels), all in one batched matcher launch.
+- Serving: a Poisson stream of queries of 4 to 32 vertices into the request
+  loop over an RMAT graph (a = 0.57, b = c = 0.19) of scale 23 (8.4M
+  vertices, 134M edges, 32 Zipf labels) with a 120 GB admission budget.
+- Billion-edge: RMAT scale 26 (67M vertices, 1.07B edges, 64 labels), 50
+  queries each of 8, 12 and 16 vertices; set FAST_BILLION=1 to run it (it
+  needs several minutes of host time to generate the graph).
+
+Every query is limited to L embeddings (2^16 on the power-law graph, 2^12
+on the RMAT graphs), so each count is exactly min(total, L).  The oracle's own search, limited to L and to a node budget,
+gives that number for every query it finishes; those must match exactly.
+For the few it does not finish, its partial count is a lower bound.
+"""
+import os
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2102_10768_gb300 as F
+import synth
+
+pytestmark = pytest.mark.gpu
+
+L = 1 << 16              # batching (1M/16M power-law graph)
+L_RMAT = 1 << 12         # RMAT graphs: heavier hubs, so a smaller limit keeps the oracle's searches short
+BUDGET = 20_000_000
+
+
+def kinds_for(k):
+    return ("induced", "sparse") if k == 4 else ("dense", "sparse")
+
+
+def draw(wg, lab, sizes, per_size, seed):
+    qs = []
+    for k in sizes:
+        kinds = kinds_for(k)
+        for j in range(per_size):
+            q = wg.query(lab, k, kinds[j % 2], seed, 100_000 * k + j)
+            qs.append((q.labels, q.edges))
+    return qs
+
+
+def check_against_oracle(o, qs, counts, status, lim):
+    assert status.tolist() == [0] * len(qs)
+    compared = 0
+    for (ql, qe), c in zip(qs, counts.tolist()):
+        r = oracle.match(o, ql, qe, limit=lim, budget=BUDGET)
+        assert c <= lim
+        if r["complete"]:
+            assert c == r["count"]
+            compared += 1
+        else:
+            assert c >= min(r["count"], lim)
+    return compared
+
+
+@pytest.fixture(scope="module")
+def powerlaw_1m():
+    F.build()
+    n, e, lab = synth.powerlaw_graph(seed=2000)
+    return n, e, lab, F.Graph(n, e, lab), oracle.Graph(n, e, lab), synth.WalkGraph(n, e)
+
+
+def test_batched_1000_mixed_queries(powerlaw_1m):
+    n, e, lab, g, o, wg = powerlaw_1m
+    qs = draw(wg, lab, (4, 8, 16, 24, 32), 200, 3000)
+    assert len(qs) == 1000
+    b = F.Batch(g, len(qs), F.default_config(limit=L, order_rule=1, time_budget_s=120.0))
+    counts, status = b.run(qs)
+    compared = check_against_oracle(o, qs, counts, status, L)
+    assert compared >= 900, compared
+    # the same batch in the paper's path-based order gives the same counts
+    b0 = F.Batch(g, len(qs), F.default_config(limit=L, order_rule=0, time_budget_s=120.0))
+    c0, s0 = b0.run(qs)
+    assert s0.tolist() == status.tolist() and c0.tolist() == counts.tolist()
+
+
+@pytest.fixture(scope="module")
+def rmat23():
+    F.build()
+    n, e, lab = synth.rmat_graph(23, 16, 32, 4000)
+    return n, e, lab, F.Graph(n, e, lab), oracle.Graph(n, e, lab), synth.WalkGraph(n, e)
+
+
+def test_served_poisson_stream_rmat23(rmat23):
+    n, e, lab, g, o, wg = rmat23
+    assert g.info()["nadj"] == 2 * e.shape[0]
+    qs = draw(wg, lab, (4, 8, 12, 16, 20, 24, 28, 32), 60, 4000)
+    rng = np.random.default_rng(4000)
+    order = rng.permutation(len(qs))
+    qs = [qs[i] for i in order]
+    srv = F.Server(g, budget_bytes=120 << 30,
+                   cfg=F.default_config(limit=L_RMAT, order_rule=1, blocks_per_sm=1, time_budget_s=30.0), workers=4)
+    gaps = rng.exponential(1.0 / 200.0, size=len(qs))            # 200 queries/s offered
+    ids, done = {}, []
+    t0 = time.perf_counter()
+    nxt = 0.0
+    for i, ((ql, qe), gap) in enumerate(zip(qs, gaps)):
+        nxt += gap
+        dt = nxt - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids[srv.submit(ql, qe)] = i
+        done += srv.poll(256)
+    while len(done) < len(qs):
+        done += srv.poll(256, wait_ms=100)
+    srv.close()
+    assert sorted(ids[r["id"]] for r in done) == list(range(len(qs)))
+    for r in done:
+        assert r["t_arrive_ns"] <= r["t_start_ns"] <= r["t_done_ns"]
+    by = {ids[r["id"]]: r for r in done}
+    counts = np.array([by[i]["count"] for i in range(len(qs))], np.int64)
+    status = np.array([by[i]["status"] for i in range(len(qs))], np.int32)
+    compared = check_against_oracle(o, qs, counts, status, L_RMAT)
+    assert compared >= int(0.8 * len(qs)), compared
+
+
+@pytest.mark.skipif(not os.environ.get("FAST_BILLION"), reason="billion-edge graph: set FAST_BILLION=1")
+def test_billion_edge_rmat26():
+    F.build()
+    n, e, lab = synth.rmat_graph(26, 16, 64, 5000)
+    g = F.Graph(n, e, lab)
+    info = g.info()
+    assert info["n"] == n and info["nadj"] == 2 * e.shape[0]
+    wg = synth.WalkGraph(n, e)
+    qs = draw(wg, lab, (8, 12, 16), 50, 5000)
+    del wg
+    o = oracle.Graph(n, e, lab)
+    del e
+    cfg = F.default_config(limit=L_RMAT, order_rule=1, time_budget_s=60.0)
+    counts, status = [], []
+    for ql, qe in qs:
+        cst = F.Cst(g, ql, qe, cfg)
+        ch = F.Chunks(cst, cfg)
+        r = F.match(cst, ch, cfg=cfg, check=False)
+        counts.append(r["count"])
+        status.append(r["status"])
+        ch.close()
+        cst.close()
+    compared = check_against_oracle(o, qs, np.array(counts), np.array(status, np.int32), L_RMAT)
+    assert compared >= int(0.8 * len(qs)), compared
