@@ -120,11 +120,14 @@ const char* fast_last_error(void);
 /*
  * Build the device-resident data graph G (Sec. II-A: undirected, labelled,
  * simple).  edges: [m][2] vertex ids in 0..n-1; both directions are stored,
- * self loops and repeated edges are dropped, every neighbour list is sorted
- * ascending.  labels: [n], >= 0 and below 2^23.  Host pointers unless flags
- * has FAST_PTR_DEVICE.  n <= 2^31 - 1 and 2m < 2^32.  Layout on the device:
- * int64 row offsets [n+1], int32 neighbour ids, int32 labels, and a label
- * index (vertices grouped by label, ascending id within a label).
+ * self loops and repeated edges are dropped.  labels: [n], >= 0 and below
+ * 2^23.  Host pointers unless flags has FAST_PTR_DEVICE.  n <= 2^31 - 1 and
+ * 2m < 2^32.  Layout on the device: int64 row offsets [n+1], int32 neighbour
+ * ids, int32 labels, and a label index (vertices grouped by label, ascending
+ * id within a label).  Each neighbour list is sorted by (label of the
+ * neighbour, id) -- with a directory of its label runs, so that the CST
+ * build (Alg. 1) reads only the neighbours with the label it keeps -- when
+ * 2 * bits(n - 1) + bits(labels - 1) <= 64; otherwise by id alone.
  * Errors: FAST_ERR_INVALID for ids or labels out of range.
  */
 int fast_load_graph(int64_t n, int64_t m, const int32_t* edges, const int32_t* labels, int flags,
@@ -134,7 +137,8 @@ int fast_load_graph(int64_t n, int64_t m, const int32_t* edges, const int32_t* l
  * (max label + 1) and maximum degree D_G. */
 int fast_graph_info(const fast_graph* g, int64_t* n, int64_t* nadj, int32_t* num_labels, int64_t* max_degree);
 
-/* Copy the CSR to host arrays row_ptr[n+1] and col[nadj] (a test aid). */
+/* Copy the CSR to host arrays row_ptr[n+1] and col[nadj], rows in the
+ * layout above (a test aid). */
 int fast_graph_copy_csr(const fast_graph* g, int64_t* row_ptr, int32_t* col, void* stream);
 
 void fast_free_graph(fast_graph* g);

@@ -4,7 +4,8 @@
 // Steps (each a handful of kernels; the host only sequences them and reads
 // candidate counts, which decide the root and the matching order):
 //   filter     |C0(u)| for every u in one launch over the label buckets.
-//   top-down   per tree edge (u_p -> u): the neighbour lists of C(u_p) are
+//   top-down   per tree edge (u_p -> u): the neighbour lists of C(u_p) -- only
+//              their run of u's label when the graph groups rows by label -- are
 //              flattened into one edge space (prefix sum of degrees); an
 //              ordered compaction keeps neighbours that pass u's filter,
 //              writing N^{u_p}_u(v_p) in place and marking the reached
@@ -61,23 +62,26 @@ struct FilterF {
     __device__ void at(int64_t, int64_t) const {}
 };
 
-__global__ void k_cand_degree(const int32_t* __restrict__ cand, int64_t nc, const int64_t* __restrict__ row_ptr,
-                              int64_t* __restrict__ out) {
+// Per candidate row: where its neighbours with label l start in col (beg)
+// and how many there are (len) -- the label's run of a grouped graph, or the
+// whole row otherwise.
+__global__ void k_cand_segment(const int32_t* __restrict__ cand, int64_t nc, GraphRuns G, int32_t l,
+                               int64_t* __restrict__ beg, int64_t* __restrict__ len) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nc) out[i] = row_ptr[cand[i] + 1] - row_ptr[cand[i]];
+    if (i < nc) label_segment(G, cand[i], l, beg + i, len + i);
 }
 
-// degrees of the first *n candidates, zero up to the bound `cap`
-__global__ void k_cand_degree_n(const int32_t* __restrict__ cand, const int64_t* __restrict__ n, int64_t cap,
-                                const int64_t* __restrict__ row_ptr, int64_t* __restrict__ out) {
+// the same for the first *n candidates, zero length up to the bound `cap`
+__global__ void k_cand_segment_n(const int32_t* __restrict__ cand, const int64_t* __restrict__ n, int64_t cap,
+                                 GraphRuns G, int32_t l, int64_t* __restrict__ beg, int64_t* __restrict__ len) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cap) return;
-    out[i] = i < *n ? row_ptr[cand[i] + 1] - row_ptr[cand[i]] : 0;
+    if (i < *n) label_segment(G, cand[i], l, beg + i, len + i);
+    else { beg[i] = 0; len[i] = 0; }
 }
 
 // off[*n] = *val (closing offset of a list set whose row count is on the device)
 __global__ void k_set_tail(int64_t* off, const int64_t* n, const int64_t* val) { off[*n] = *val; }
-__global__ void k_set_tail_at(int64_t* off, int64_t n, const int64_t* val) { off[n] = *val; }
 
 __device__ __forceinline__ int64_t row_of(const int64_t* e_off, int64_t rows, int64_t i) {
     // last r with e_off[r] <= i
@@ -89,14 +93,38 @@ __device__ __forceinline__ int64_t row_of(const int64_t* e_off, int64_t rows, in
     return lo;
 }
 
+// The first of the rows whose lists start at index i (row is the last one,
+// the row holding entry i; the others before it are empty).
+__device__ __forceinline__ int64_t first_row_at(const int64_t* e_off, int64_t row, int64_t i) {
+    while (row > 0 && e_off[row - 1] == i) row--;
+    return row;
+}
+
+// new_off[x] = rank for row r and every following row that starts at the
+// same index (empty rows, up to the first row with an entry)
+__device__ __forceinline__ void set_rows_at(const int64_t* e_off, int64_t rows, int64_t r, int64_t* new_off,
+                                            int64_t rank) {
+    const int64_t i = e_off[r];
+    for (int64_t x = r; x < rows && e_off[x] == i; x++) new_off[x] = rank;
+}
+
+// Rows after the last entry (and the closing offset): new_off[r] = total for
+// r <= n with e_off[r] == e_off[n].  n on the device (n_dev) or given.
+__global__ void k_fill_tail(const int64_t* __restrict__ e_off, const int64_t* __restrict__ n_dev, int64_t n_host,
+                            int64_t cap, const int64_t* __restrict__ total, int64_t* __restrict__ new_off) {
+    const int64_t n = n_dev ? *n_dev : n_host;
+    const int64_t end = e_off[n];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= n && r <= cap; r += (int64_t)gridDim.x * blockDim.x)
+        if (e_off[r] == end) new_off[r] = *total;
+}
+
 // Top-down: flattened neighbour lists of C(u_p); keeps neighbours passing
 // u's filter (label and degree), marks them reached, writes list offsets.
 struct TopDownF {
     using value_type = int32_t;
     const int64_t* e_off;      // [rows+1]
     int64_t rows;
-    const int32_t* cp;         // C(u_p)
-    const int64_t* row_ptr;
+    const int64_t* seg;        // per row of C(u_p): start in col of its neighbours with u's label
     const int32_t* col;
     const int32_t* key;
     int32_t want_key_hi;       // label
@@ -112,11 +140,11 @@ struct TopDownF {
         e_end = *E;
         if (i0 >= e_end) return;
         row = row_of(e_off, rows, i0);
-        nbase = row_ptr[cp[row]] - e_off[row];
+        nbase = seg[row] - e_off[row];
     }
     __device__ bool eval(int64_t i, int32_t& v) {
         if (i >= e_end) { v = 0; return false; }
-        while (i >= e_off[row + 1]) { row++; nbase = row_ptr[cp[row]] - e_off[row]; }
+        while (i >= e_off[row + 1]) { row++; nbase = seg[row] - e_off[row]; }
         int32_t x = col[nbase + i];
         v = x;
         int32_t kk = key[x];
@@ -124,8 +152,11 @@ struct TopDownF {
         if (hit && !counting) atomicOr(&reached[x >> 5], 1u << (x & 31));
         return hit;
     }
-    __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? row : -1; }
-    __device__ void at(int64_t r, int64_t rank) const { t_off[r] = rank; }
+    // rows start at their first entry; a row with no entry (no neighbour of
+    // the label) starts where the next one does, so the first entry of a
+    // row tags it and every empty row just before it
+    __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? first_row_at(e_off, row, i) : -1; }
+    __device__ void at(int64_t r, int64_t rank) const { set_rows_at(e_off, rows, r, t_off, rank); }
     __device__ int64_t end() const { return *E; }
 };
 
@@ -135,8 +166,7 @@ struct NonTreeF {
     using value_type = uint32_t;
     const int64_t* e_off;
     int64_t rows;
-    const int32_t* cj;
-    const int64_t* row_ptr;
+    const int64_t* seg;        // per row of C(u_j): start in col of its neighbours with u_i's label
     const int32_t* col;
     const uint32_t* alive;     // bitmap of C(u_i)
     const uint32_t* rank;      // prefix popcounts of alive
@@ -149,18 +179,18 @@ struct NonTreeF {
         e_end = *E;
         if (i0 >= e_end) return;
         row = row_of(e_off, rows, i0);
-        nbase = row_ptr[cj[row]] - e_off[row];
+        nbase = seg[row] - e_off[row];
     }
     __device__ bool eval(int64_t i, uint32_t& v) {
         if (i >= e_end) { v = 0; return false; }
-        while (i >= e_off[row + 1]) { row++; nbase = row_ptr[cj[row]] - e_off[row]; }
+        while (i >= e_off[row + 1]) { row++; nbase = seg[row] - e_off[row]; }
         int32_t x = col[nbase + i];
         uint32_t w = alive[x >> 5], bit = 1u << (x & 31);
         v = rank[x >> 5] + __popc(w & (bit - 1));
         return (w & bit) != 0;
     }
-    __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? row : -1; }
-    __device__ void at(int64_t r, int64_t rank_) const { n_off[r] = rank_; }
+    __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? first_row_at(e_off, row, i) : -1; }
+    __device__ void at(int64_t r, int64_t rank_) const { set_rows_at(e_off, rows, r, n_off, rank_); }
     __device__ int64_t end() const { return *E; }
 };
 
@@ -583,6 +613,8 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
     int64_t cap_l[kMaxK] = {0};             // bound on the entries of the tree lists into u
     Bits bits[kMaxK];
     int64_t* e_off = nullptr;
+    int64_t* seg = nullptr;                 // per candidate row: start of its label segment in col
+    const GraphRuns G = graph_runs(g);
     unsigned long long* cnt_d = nullptr;
     int32_t* dq_d = nullptr;
     int64_t* lo_d = nullptr;
@@ -658,7 +690,11 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
             int64_t rows = cap_c[p];                          // bound on |C_td(p)|
             int64_t* n_p = sz + p;                            // |C_td(p)| on the device
             rc = dalloc(&e_off, rows + 1, s); if (rc) break;
-            if (rows > 0) { k_cand_degree_n<<<grid_for(rows, 256), 256, 0, s>>>(td_cand[p], n_p, rows, g->row_ptr, e_off); note_launch(); }
+            rc = dalloc(&seg, rows, s); if (rc) break;
+            if (rows > 0) {
+                k_cand_segment_n<<<grid_for(rows, 256), 256, 0, s>>>(td_cand[p], n_p, rows, G, q->labels[u], seg, e_off);
+                note_launch();
+            }
             rc = scan_exclusive<int64_t>(e_off, e_off, rows, e_off + rows, s); if (rc) break;
             int64_t E = degsum(q->labels[p]);                 // bound on the edge space
             if (E > kBoundedListCap) {                        // too loose: size it exactly
@@ -671,14 +707,15 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
             rc = dalloc(&td_off[u], rows + 1, s); if (rc) break;
             rc = dalloc(&td_list[u], E, s); if (rc) break;
             TopDownF f{};
-            f.e_off = e_off; f.rows = rows; f.cp = td_cand[p]; f.row_ptr = g->row_ptr; f.col = g->col; f.key = g->key;
+            f.e_off = e_off; f.rows = rows; f.seg = seg; f.col = g->col; f.key = g->key;
             f.want_key_hi = q->labels[u]; f.want_dq = dq[u]; f.reached = bits[u].alive; f.t_off = td_off[u];
             f.E = e_off + rows;
             int64_t* kept = sz + 3 * kMaxK + kMaxNT;          // scratch word
             rc = compact(f, E, td_list[u], kept, s); if (rc) break;
-            k_set_tail<<<1, 1, 0, s>>>(td_off[u], n_p, kept);
+            k_fill_tail<<<grid_for(rows + 1, 256), 256, 0, s>>>(e_off, n_p, 0, rows, kept, td_off[u]);
             note_launch();
             dfree(e_off, s);
+            dfree(seg, s);
             rc = dalloc(&td_cand[u], cap_c[u], s); if (rc) break;
             BitsF bf{bits[u].alive};
             rc = compact(bf, n, td_cand[u], sz + u, s); if (rc) break;
@@ -802,7 +839,11 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
                 c->nt_from[e] = uj; c->nt_to[e] = ui;
                 int64_t rows = c->ncand[uj];
                 rc = dalloc(&e_off, rows + 1, s); if (rc) break;
-                if (rows > 0) { k_cand_degree<<<grid_for(rows, 256), 256, 0, s>>>(c->cand[uj], rows, g->row_ptr, e_off); note_launch(); }
+                rc = dalloc(&seg, rows, s); if (rc) break;
+                if (rows > 0) {
+                    k_cand_segment<<<grid_for(rows, 256), 256, 0, s>>>(c->cand[uj], rows, G, q->labels[ui], seg, e_off);
+                    note_launch();
+                }
                 rc = scan_exclusive<int64_t>(e_off, e_off, rows, e_off + rows, s); if (rc) break;
                 int64_t E = degsum(q->labels[uj]);
                 if (E > kBoundedListCap) {
@@ -812,14 +853,15 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
                 rc = dalloc(&c->n_off[e], rows + 1, s); if (rc) break;
                 rc = dalloc(&c->n_idx[e], E, s); if (rc) break;
                 NonTreeF f{};
-                f.e_off = e_off; f.rows = rows; f.cj = c->cand[uj]; f.row_ptr = g->row_ptr; f.col = g->col;
+                f.e_off = e_off; f.rows = rows; f.seg = seg; f.col = g->col;
                 f.alive = bits[ui].alive; f.rank = bits[ui].rank; f.n_off = c->n_off[e];
                 f.E = e_off + rows;
                 int64_t* kept = sz + 3 * kMaxK + e;
                 rc = compact(f, E, c->n_idx[e], kept, s); if (rc) break;
-                k_set_tail_at<<<1, 1, 0, s>>>(c->n_off[e], rows, kept);
+                k_fill_tail<<<grid_for(rows + 1, 256), 256, 0, s>>>(e_off, nullptr, rows, rows, kept, c->n_off[e]);
                 note_launch();
                 dfree(e_off, s);
+                dfree(seg, s);
             }
         }
         if (rc) break;
@@ -887,7 +929,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         dfree(td_list[u], s); dfree(td_off[u], s); dfree(td_cand[u], s);
         dfree(bits[u].alive, s); dfree(bits[u].rank, s);
     }
-    dfree(e_off, s); dfree(cnt_d, s); dfree(dq_d, s); dfree(lo_d, s); dfree(sz, s);
+    dfree(e_off, s); dfree(seg, s); dfree(cnt_d, s); dfree(dq_d, s); dfree(lo_d, s); dfree(sz, s);
     // The lists were built in buffers sized by bounds; keep exact copies.
     if (rc == FAST_OK) rc = cst_to_arena(c, s);
     free_build_arrays(c, s);

@@ -142,10 +142,94 @@ __global__ void k_label_degsum(const int64_t* __restrict__ row_ptr, const int32_
     if (v < n) atomicAdd(&sum[lab[v]], (unsigned long long)(row_ptr[v + 1] - row_ptr[v]));
 }
 
+// ------------------------------------------------------------ label runs
+
+// kept holds (src << 32 | dst), sorted; rewrite each as (src, label(dst),
+// dst) packed into sh_src / sh_lab / 0 bit offsets
+__global__ void k_group_keys(uint64_t* __restrict__ kept, int64_t nadj, const int32_t* __restrict__ label,
+                             int sh_lab, int sh_src) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nadj) return;
+    uint64_t k = kept[i];
+    uint64_t src = k >> 32, dst = k & 0xFFFFFFFFull;
+    kept[i] = (src << sh_src) | ((uint64_t)(uint32_t)label[dst] << sh_lab) | dst;
+}
+
+// back to (src << 32 | dst), now in (src, label, dst) order
+__global__ void k_ungroup_keys(uint64_t* __restrict__ kept, int64_t nadj, int sh_src, uint64_t dst_mask) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nadj) return;
+    uint64_t k = kept[i];
+    kept[i] = ((k >> sh_src) << 32) | (k & dst_mask);
+}
+
+// warp per row: number of label runs (write = 0), or the runs themselves
+template <bool WRITE>
+__global__ void k_row_runs(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ label, int64_t n, int64_t* __restrict__ cnt,
+                           const int64_t* __restrict__ run_ptr, int32_t* __restrict__ run_lab,
+                           int64_t* __restrict__ run_beg) {
+    const int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w; v < n; v += nw) {
+        const int64_t a = row_ptr[v], b = row_ptr[v + 1];
+        int64_t r = WRITE ? run_ptr[v] : 0;
+        int64_t c = 0;
+        for (int64_t base = a; base < b; base += 32) {
+            int64_t i = base + lane;
+            bool head = false;
+            int32_t l = 0;
+            if (i < b) {
+                l = label[col[i]];
+                head = (i == a) || label[col[i - 1]] != l;
+            }
+            uint32_t m = __ballot_sync(0xffffffffu, head);
+            if (WRITE && head) {
+                int64_t at = r + __popc(m & lanemask_lt());
+                run_lab[at] = l;
+                run_beg[at] = i;
+            }
+            r += __popc(m);
+            c += __popc(m);
+        }
+        if (!WRITE && lane == 0) cnt[v] = c;
+    }
+}
+
+int build_label_runs(fast_graph* g, cudaStream_t s) {
+    const int64_t n = g->n;
+    int64_t* cnt = nullptr;
+    FAST_TRY(dalloc(&g->run_ptr, n + 1, s));
+    FAST_TRY(dalloc(&cnt, n, s));
+    unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(n, 8), (int64_t)num_sms() * 32);
+    k_row_runs<false><<<blocks, 256, 0, s>>>(g->row_ptr, g->col, g->label, n, cnt, nullptr, nullptr, nullptr);
+    note_launch();
+    int rc = scan_exclusive<int64_t>(cnt, g->run_ptr, n, g->run_ptr + n, s);
+    int64_t R = 0;
+    if (rc == FAST_OK) {
+        cudaError_t e = cudaMemcpyAsync(&R, g->run_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_status(e, "label runs", __FILE__, __LINE__);
+    }
+    dfree(cnt, s);
+    if (rc == FAST_OK) rc = dalloc(&g->run_lab, R, s);
+    if (rc == FAST_OK) rc = dalloc(&g->run_beg, R, s);
+    if (rc == FAST_OK) {
+        k_row_runs<true><<<blocks, 256, 0, s>>>(g->row_ptr, g->col, g->label, n, nullptr, g->run_ptr, g->run_lab,
+                                                g->run_beg);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "label runs launch");
+    }
+    if (rc == FAST_OK) g->grouped = true;
+    return rc;
+}
+
 void graph_release(fast_graph* g, cudaStream_t s) {
     if (!g) return;
     dfree(g->row_ptr, s); dfree(g->col, s); dfree(g->label, s); dfree(g->key, s);
     dfree(g->lab_ptr, s); dfree(g->lab_vtx, s);
+    dfree(g->run_ptr, s); dfree(g->run_lab, s); dfree(g->run_beg, s);
     delete g;
 }
 
@@ -204,11 +288,24 @@ int load_graph(int64_t n, int64_t m, const int32_t* edges, const int32_t* labels
         g->nadj = nadj;
         dfree(keys, s);
         dfree(d_edges, s);
+        // group each row by neighbour label: (src, label, dst) keys, a stable
+        // sort on the src and label digits keeps dst ascending within a group
+        const int lbits = bits_for(g->num_labels - 1 > 0 ? g->num_labels - 1 : 1);
+        const bool group = 2 * nb + lbits <= 64 && nadj > 0;
+        if (group) {
+            k_group_keys<<<(unsigned)ceil_div(nadj, 256), 256, 0, s>>>(kept, nadj, g->label, nb, nb + lbits);
+            note_launch();
+            np = digit_shifts(nb, 2 * nb + lbits, shifts, 16);
+            rc = radix_sort_u64(kept, nadj, shifts, np, s); if (rc) break;
+            k_ungroup_keys<<<(unsigned)ceil_div(nadj, 256), 256, 0, s>>>(kept, nadj, nb + lbits, mask);
+            note_launch();
+        }
         rc = dalloc(&g->row_ptr, n + 1, s); if (rc) break;
         rc = dalloc(&g->col, nadj, s); if (rc) break;
         k_row_bounds<<<(unsigned)ceil_div(nadj + 1, 256), 256, 0, s>>>(kept, nadj, n, g->row_ptr, g->col);
         note_launch();
         dfree(kept, s);
+        if (group) { rc = build_label_runs(g, s); if (rc) break; }
         rc = dalloc(&g->key, n, s); if (rc) break;
         rc = dalloc(&lkeys, n, s); if (rc) break;
         rc = dalloc(&maxdeg_d, 1, s); if (rc) break;

@@ -24,7 +24,51 @@ struct fast_graph {
     int32_t* lab_vtx = nullptr;   // [n] vertices grouped by label, ascending id
     std::vector<int64_t> lab_ptr_host;
     std::vector<int64_t> lab_degsum_host;   // per label: sum of degrees (bounds CST list sizes)
+    // Label runs: when `grouped`, each row of col is sorted by (label of the
+    // neighbour, id), and row v's runs are run_ptr[v] .. run_ptr[v+1]-1: run
+    // r holds the neighbours with label run_lab[r], from col position
+    // run_beg[r] to the next run's start (or the row's end).
+    bool grouped = false;
+    int64_t* run_ptr = nullptr;   // [n+1]
+    int32_t* run_lab = nullptr;   // [R]
+    int64_t* run_beg = nullptr;   // [R]
 };
+
+// The neighbours of v with label l: col[*beg .. *beg + *len), ascending id.
+// An ungrouped graph gives the whole row (the caller still tests labels).
+struct GraphRuns {
+    const int64_t* row_ptr;
+    const int64_t* run_ptr;       // null: ungrouped
+    const int32_t* run_lab;
+    const int64_t* run_beg;
+};
+
+__device__ __forceinline__ void label_segment(const GraphRuns& G, int32_t v, int32_t l, int64_t* beg, int64_t* len) {
+    const int64_t a = G.row_ptr[v], b = G.row_ptr[v + 1];
+    if (!G.run_ptr) { *beg = a; *len = b - a; return; }
+    int64_t lo = G.run_ptr[v], hi = G.run_ptr[v + 1];
+    const int64_t r1 = hi;
+    while (lo < hi) {                              // first run with label >= l
+        int64_t mid = (lo + hi) >> 1;
+        if (G.run_lab[mid] < l) lo = mid + 1; else hi = mid;
+    }
+    if (lo < r1 && G.run_lab[lo] == l) {
+        *beg = G.run_beg[lo];
+        *len = (lo + 1 < r1 ? G.run_beg[lo + 1] : b) - *beg;
+    } else {
+        *beg = a;
+        *len = 0;
+    }
+}
+
+inline GraphRuns graph_runs(const fast_graph* g) {
+    GraphRuns G;
+    G.row_ptr = g->row_ptr;
+    G.run_ptr = g->grouped ? g->run_ptr : nullptr;
+    G.run_lab = g->run_lab;
+    G.run_beg = g->run_beg;
+    return G;
+}
 
 // Candidate search tree (Sec. IV-A) of one query.  Indexed by query vertex
 // unless noted; lists hold candidate-local indices.

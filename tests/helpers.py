@@ -63,3 +63,14 @@ def sorted_rows(a):
     if a.shape[0] == 0:
         return a
     return a[np.lexsort(a.T[::-1])]
+
+
+def csr_by_label(off, col, labels):
+    """The CSR's rows reordered by (label of the neighbour, neighbour id): the
+    library's layout when its ids and labels fit one 64-bit sort key."""
+    off = np.asarray(off, np.int64)
+    col = np.asarray(col)
+    labels = np.asarray(labels)
+    row = np.repeat(np.arange(off.shape[0] - 1), np.diff(off))
+    order = np.lexsort((col, labels[col], row))
+    return off, col[order]

@@ -10,7 +10,7 @@ import pytest
 import oracle
 import paper_2102_10768_gb300 as F
 import synth
-from helpers import compare_cst, gpu_chunks_global, sorted_rows
+from helpers import compare_cst, csr_by_label, gpu_chunks_global, sorted_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,7 @@ def _csr_equal(n, edges, labels):
     g = F.Graph(n, edges, labels)
     o = oracle.Graph(n, edges, labels)
     goff, gcol = g.csr()
-    ooff, ocol = o.csr()
+    ooff, ocol = csr_by_label(*o.csr(), labels)
     assert np.array_equal(goff, ooff)
     assert np.array_equal(gcol, ocol)
     inf = g.info()
@@ -65,7 +65,7 @@ def _csr_equal(n, edges, labels):
 def test_loader_er(er):
     w, g, o = er
     goff, gcol = g.csr()
-    ooff, ocol = o.csr()
+    ooff, ocol = csr_by_label(*o.csr(), w.labels)
     assert np.array_equal(goff, ooff) and np.array_equal(gcol, ocol)
 
 
@@ -417,7 +417,7 @@ def powerlaw():
 def test_powerlaw_loader(powerlaw):
     n, e, lab, qs, g, o = powerlaw
     goff, gcol = g.csr()
-    ooff, ocol = o.csr()
+    ooff, ocol = csr_by_label(*o.csr(), lab)
     assert np.array_equal(goff, ooff) and np.array_equal(gcol, ocol)
 
 
