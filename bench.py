@@ -61,13 +61,32 @@ def parse():
     return p.parse_args()
 
 
+def query_stream0(rank: int, k: int, kind: str) -> int:
+    """First random-walk stream of a (rank, size, kind) class: every rank draws
+    its own queries (replicas, weak scaling), at most 500 per class."""
+    return 100_000 * rank + 1000 * k + (0 if kind == "dense" else 500)
+
+
+def reduce_over_ranks(values, dist, device):
+    """values = [t_s, embeddings, t_e2e, e2e embeddings] of this rank ->
+    (max t_s, sum of embeddings, max t_e2e, sum of e2e embeddings) over the
+    ranks: whole-job throughput is all ranks' work over the slowest rank."""
+    import torch
+    t = torch.tensor([float(x) for x in values], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(mx[2]), float(sm[3])
+
+
 def workload(args, rank: int):
     import synth
     n, e, lab = synth.powerlaw_graph(seed=args.seed)
     qs = []
     for k in (8, 16):
         for kind in ("dense", "sparse"):
-            stream0 = 100_000 * rank + 1000 * k + (0 if kind == "dense" else 500)
+            stream0 = query_stream0(rank, k, kind)
             qs += synth.walk_queries(n, e, lab, k, args.queries, kind, seed=args.seed, stream0=stream0)
     desc = (f"Chung-Lu gamma=2.1, n=1,000,000, m=16,000,000, 16 Zipf(1.0) labels; "
             f"{len(qs)} random-walk queries (8/16 vertices x dense/sparse); per query: CST, Alg. 2 partition "
@@ -397,10 +416,7 @@ def run_ours(args):
     steps = max(args.steps, 1)
     t_s = tot_ms / 1000.0
     if dist:
-        stats = torch.tensor([t_s, float(tot_emb), t_e2e, float(e2e_emb)], dtype=torch.float64, device="cuda")
-        mx = stats.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = stats.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        t_s, tot_all, t_e2e_max, e2e_all = float(mx[0]), float(sm[1]), float(mx[2]), float(sm[3])
+        t_s, tot_all, t_e2e_max, e2e_all = reduce_over_ranks([t_s, tot_emb, t_e2e, e2e_emb], dist, "cuda")
     else:
         tot_all, t_e2e_max, e2e_all = float(tot_emb), t_e2e, float(e2e_emb)
     if rank != 0:
