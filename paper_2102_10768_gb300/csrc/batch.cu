@@ -1,13 +1,13 @@
 // Batched matching: many queries in one matcher launch.
 //
 // A fast_batch owns fixed device buffers (per-query plans, the concatenated
-// chunk list, counters, the donation queue), so that its matcher launch can
-// be captured once as a CUDA graph and replayed for every batch.  A batch
-// run has three phases:
-//   1. a pool of host threads, each with its own CUDA stream, builds the CST
-//      (Alg. 1) and the partition (Alg. 2) of the queries concurrently --
-//      their device work overlaps and their host round trips hide each
-//      other's latency;
+// chunk list, counters, the ring of donated runs), so that its matcher
+// launch can be captured once as a CUDA graph and replayed for every batch.
+// A batch run has three phases:
+//   1. a pool of host threads, each with its own CUDA stream and scratch
+//      pool, builds the CST (Alg. 1) and the partition (Alg. 2) of the
+//      queries concurrently -- their device work overlaps and their host
+//      round trips hide each other's latency;
 //   2. plans and chunks are gathered into the fixed buffers, every chunk
 //      tagged with its query;
 //   3. the captured graph runs one persistent matcher launch over all

@@ -1,6 +1,6 @@
 // Internal helpers shared by the library's translation units: status
-// handling, the last-error message, stream-ordered allocation and small
-// device utilities.  Nothing here is part of the C ABI (see include/fast.h).
+// handling, the last-error message, device memory (stream-ordered
+// allocation, scratch pools, arenas) and small device utilities.  Nothing here is part of the C ABI (see include/fast.h).
 #pragma once
 
 #include <vector>

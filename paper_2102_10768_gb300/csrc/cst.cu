@@ -6,7 +6,7 @@
 //   filter     |C0(u)| for every u in one launch over the label buckets.
 //   top-down   per tree edge (u_p -> u): the neighbour lists of C(u_p) -- only
 //              their run of u's label when the graph groups rows by label -- are
-//              flattened into one edge space (prefix sum of degrees); an
+//              flattened into one edge space (prefix sum of their lengths); an
 //              ordered compaction keeps neighbours that pass u's filter,
 //              writing N^{u_p}_u(v_p) in place and marking the reached
 //              vertices in a bitmap, whose compaction is C(u).
@@ -21,6 +21,9 @@
 //   workload   children first: the saturating sum of c over each child
 //              list (entry-parallel, one atomic per row segment), then their
 //              product per candidate.
+// Buffers are sized by host-known bounds and taken from the scratch pool;
+// the last round trip gives every exact size, and one kernel copies the
+// CST's arrays into one exact-size block that the CST owns.
 #include <algorithm>
 #include <cstring>
 #include <vector>

@@ -4,7 +4,11 @@
 // undirected graph: both directions of every edge become 64-bit keys
 // (src << 32 | dst), a stable LSD radix sort orders them, an ordered
 // compaction drops self loops and repeats, and a boundary pass writes the row
-// offsets.  A second radix sort on (label << 32 | id) builds the label index.
+// offsets.  When ids and labels fit one 64-bit key, the adjacency entries are
+// re-sorted stably on (row, label of the neighbour), so that each row holds
+// its neighbours grouped by label (ascending id within a label), and a
+// per-row directory of label runs is built for the CST build.  A radix sort
+// on (label << 32 | id) builds the label index.
 #include <stdarg.h>
 
 #include <atomic>

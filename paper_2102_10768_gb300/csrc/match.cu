@@ -2,10 +2,17 @@
 //
 // One warp owns one work item at a time -- a chunk of the partition, or a
 // run another warp gave away -- and walks its search space depth first.  Per
-// depth the warp scans the candidate list of the parent position's image 32
-// entries at a time (the Generator) and each lane tests its candidate:
-//   EdgeValidator    binary search of the candidate in the CST list of every
-//                    earlier non-tree neighbour's image;
+// depth the warp scans a candidate list 32 entries at a time (the
+// Generator) and each lane tests its candidate:
+//   Generator        the candidates of depth d are the intersection of the
+//                    tree list from the parent's image and the CST list from
+//                    every earlier non-tree neighbour's image, all sorted
+//                    over C(u_d); the warp scans the shortest of them (the
+//                    tree list in the counting pass, whose bytes are pinned);
+//   EdgeValidator    membership in each other list by a warp-cooperative
+//                    merge (a cursor per list, coalesced 32-entry tiles, a
+//                    shuffle search, galloping), shortest lists first,
+//                    stopping once no candidate is left;
 //   VisitedValidator the candidate's data vertex against the images of the
 //                    earlier positions with the same label (distinct labels
 //                    cannot collide);
@@ -20,7 +27,8 @@
 // idle; a busy warp that sees idle warps gives away the second half of the
 // unscanned list at its shallowest depth with at least two entries left --
 // a run of a list with a fixed prefix, i.e. again a chunk.  An outstanding-
-// work counter ends the launch.  Every wait is bounded and reports a status.
+// work counter ends the launch.  No warp waits on another: the only wait, an
+// idle warp looking for work, is bounded by %globaltimer.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -131,10 +139,10 @@ __device__ __forceinline__ bool bsearch_u32(const uint32_t* __restrict__ a, int6
 
 // Warp-cooperative membership test.  Each lane with `act` holds a candidate
 // c; over those lanes the candidates ascend with the lane index (they come
-// from one sorted tree list).  L[lo, hi) is a sorted non-tree list and *pos a
-// cursor into it that never passes the lower bound of any candidate still to
-// come, so successive 32-entry segments of the tree list walk the non-tree
-// list once, merge-style:
+// from the generator list, sorted).  L[lo, hi) is another sorted list over
+// the same candidate set and *pos a cursor into it that never passes the
+// lower bound of any candidate still to come, so successive 32-entry
+// segments of the generator walk L once, merge-style:
 //   - load the tile L[pos, pos+32) with one coalesced read;
 //   - every pending lane whose candidate is <= the tile's last entry finds
 //     its lower bound inside the tile by a 5-step shuffle search;

@@ -9,8 +9,10 @@
 // which equals the workload DP evaluated on the partitioned tree: restricting
 // a candidate set to the part leaves c unchanged for every candidate still
 // reachable, and every position after j hangs below a prefix position.
-// One level = three kernels (decide and count parts, write parts, sum the
-// parts' estimates); the host reads two sizes per level.
+// One level = decide and count parts, write the chunks that are done (and
+// the parts of sampled splits), then one warp per part sums its estimate
+// (an unsampled part is derived from its item and index); the host reads the
+// level's sizes.
 #include <vector>
 
 #include "internal.cuh"

@@ -1,7 +1,8 @@
 // Device-wide building blocks written for this library: exclusive scan,
-// ordered predicate compaction over an index space, and a stable LSD radix
-// sort of 64-bit keys.  All are stream-ordered and allocate their scratch
-// with cudaMallocAsync on the caller's stream.
+// ordered predicate compaction over an index space (single pass, decoupled
+// look-back; a two-pass form where the output size is needed first), and a
+// stable LSD radix sort of 64-bit keys.  All are stream-ordered and take
+// their scratch through dalloc on the caller's stream.
 #pragma once
 
 #include <algorithm>
