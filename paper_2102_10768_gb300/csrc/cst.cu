@@ -132,6 +132,7 @@ struct TopDownF {
     const int32_t* key;
     int32_t want_key_hi;       // label
     int32_t want_dq;
+    bool label_known;          // grouped graph: a segment holds only that label
     uint32_t* reached;         // bitmap over V(G)
     int64_t* t_off;            // out: [rows+1]
     const int64_t* E;          // edge-space size on the device (index space may be a bound)
@@ -150,8 +151,13 @@ struct TopDownF {
         while (i >= e_off[row + 1]) { row++; nbase = seg[row] - e_off[row]; }
         int32_t x = col[nbase + i];
         v = x;
-        int32_t kk = key[x];
-        bool hit = (kk >> 8) == want_key_hi && (kk & 255) >= want_dq;
+        bool hit;
+        if (label_known && want_dq <= 1) {
+            hit = true;                        // the label is the segment's; a neighbour has degree >= 1
+        } else {
+            int32_t kk = key[x];
+            hit = (kk >> 8) == want_key_hi && (kk & 255) >= want_dq;
+        }
         if (hit && !counting) atomicOr(&reached[x >> 5], 1u << (x & 31));
         return hit;
     }
@@ -712,6 +718,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
             TopDownF f{};
             f.e_off = e_off; f.rows = rows; f.seg = seg; f.col = g->col; f.key = g->key;
             f.want_key_hi = q->labels[u]; f.want_dq = dq[u]; f.reached = bits[u].alive; f.t_off = td_off[u];
+            f.label_known = G.run_ptr != nullptr;
             f.E = e_off + rows;
             int64_t* kept = sz + 3 * kMaxK + kMaxNT;          // scratch word
             rc = compact(f, E, td_list[u], kept, s); if (rc) break;
