@@ -299,33 +299,6 @@ int compact(const F& f, int64_t n, typename F::value_type* out, int64_t* count_d
 
 
 template <class F>
-int compact_size(const F& f, int64_t n, int64_t* kept_host, cudaStream_t s) {
-    *kept_host = 0;
-    if (n <= 0) return FAST_OK;
-    int64_t nb = ceil_div(n, kCompTile);
-    int64_t* offs = nullptr;
-    int64_t* tot = nullptr;
-    FAST_TRY(dalloc(&offs, nb, s));
-    int rc = dalloc(&tot, 1, s);
-    if (rc == FAST_OK) {
-        k_compact_count<F><<<(unsigned)nb, kCompBlock, 0, s>>>(f, n, offs);
-        note_launch();
-        if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "compact count launch");
-    }
-    if (rc == FAST_OK) rc = scan_exclusive<int64_t>(offs, offs, nb, tot, s);
-    if (rc == FAST_OK) {
-        cudaError_t e = cudaMemcpyAsync(kept_host, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) rc = cuda_status(e, "compact_size readback", __FILE__, __LINE__);
-    }
-    dfree(offs, s);
-    dfree(tot, s);
-    return rc;
-}
-
-// Count, allocate the output (stream-ordered), then write: one host sync to
-// learn the size.  *out is left null when nothing is kept.
-template <class F>
 int compact_alloc(const F& f, int64_t n, typename F::value_type** out, int64_t* kept_host, cudaStream_t s) {
     *out = nullptr;
     *kept_host = 0;
