@@ -8,8 +8,12 @@
  * readings below; it shares no code with the CUDA library.
  *
  * Readings of points the paper leaves open (each gives the same embeddings):
- *   filter   C0(u) = { v : l_G(v) = l_q(u), d_G(v) >= d_q(u) }  ("local
- *            features", Sec. IV-A: labels and degrees).
+ *   filter   rule 0: C0(u) = { v : l_G(v) = l_q(u), d_G(v) >= d_q(u) }
+ *            ("local features", Sec. IV-A: labels and degrees).
+ *            rule 1 (neighbour label frequency, a stronger local feature):
+ *            also, for every label l, v has at least as many neighbours
+ *            labelled l as u has.  Sound: an embedding maps u's neighbours
+ *            labelled l injectively onto neighbours of v labelled l.
  *   root     argmin over u of |C0(u)| / d_q(u), ties to the smaller id
  *            (k = 1: vertex 0).
  *   t_q      breadth-first from the root, neighbours in increasing id.
@@ -103,8 +107,9 @@ void oracle_cst_free(ocst* c) {
  * Build the CST of q over G (Algorithm 1 with the readings above).
  * Returns a handle, or NULL on invalid or disconnected input.
  */
-ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int32_t* qe, int order_rule) {
-    if (k < 1 || k > CMAXK || order_rule < 0 || order_rule > 1) return NULL;
+ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int32_t* qe, int order_rule,
+                       int filter_rule) {
+    if (k < 1 || k > CMAXK || order_rule < 0 || order_rule > 1 || filter_rule < 0 || filter_rule > 1) return NULL;
     int A[CMAXK][CMAXK];
     memset(A, 0, sizeof(A));
     int dq[CMAXK] = {0};
@@ -120,8 +125,29 @@ ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int
     ivec c0[CMAXK];
     memset(c0, 0, sizeof(c0));
     for (int u = 0; u < k; u++) {
-        for (int64_t v = 0; v < g->n; v++)
-            if (g->lab[v] == ql[u] && g->off[v + 1] - g->off[v] >= dq[u]) iv_push(&c0[u], (int32_t)v);
+        /* rule 1: the labels of u's query neighbours and how often each occurs */
+        int32_t nl[CMAXK];
+        int need[CMAXK], nn = 0;
+        for (int w = 0; w < k; w++) {
+            if (!A[u][w]) continue;
+            int t = 0;
+            while (t < nn && nl[t] != ql[w]) t++;
+            if (t == nn) { nl[nn] = ql[w]; need[nn] = 0; nn++; }
+            need[t]++;
+        }
+        for (int64_t v = 0; v < g->n; v++) {
+            if (g->lab[v] != ql[u] || g->off[v + 1] - g->off[v] < dq[u]) continue;
+            if (filter_rule == 1) {
+                int have[CMAXK] = {0}, ok = 1;
+                for (int64_t i = g->off[v]; i < g->off[v + 1]; i++)
+                    for (int t = 0; t < nn; t++)
+                        if (g->lab[g->adj[i]] == nl[t]) have[t]++;
+                for (int t = 0; t < nn; t++)
+                    if (have[t] < need[t]) ok = 0;
+                if (!ok) continue;
+            }
+            iv_push(&c0[u], (int32_t)v);
+        }
         c->c0n[u] = c0[u].n;
     }
 

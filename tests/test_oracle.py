@@ -512,3 +512,42 @@ def test_greedy_order_is_connected_and_count_invariant(seed):
     want = oracle.count(g, ql, qe)
     assert oracle.count(g, ql, qe, order=greedy.order.tolist(), par=_tree_par(greedy)) == want
     assert greedy.workload()[1] == path.workload()[1]
+
+
+# --------------------------------------- candidate filter: label frequencies
+
+def test_nlf_filter_hand_case():
+    """Query: centre u0 (label 0) joined to u1, u2 (label 1).  Data vertex 0
+    (label 0) has neighbours 1 (label 1) and 2 (label 2); vertex 3 (label 0)
+    has neighbours 4, 5 (label 1).  The degree filter keeps 0 and 3 for u0;
+    the label-frequency filter needs two neighbours labelled 1 and keeps only
+    3.  Either way there are 2 embeddings (u1, u2 onto 4, 5 in both orders)."""
+    g = oracle.Graph(6, [[0, 1], [0, 2], [3, 4], [3, 5]], [0, 1, 2, 0, 1, 1])
+    ql, qe = [0, 1, 1], [[0, 1], [0, 2]]
+    ldf = oracle.Cst(g, ql, qe)
+    nlf = oracle.Cst(g, ql, qe, filter="nlf")
+    assert ldf.c0_count.tolist() == [2, 3, 3]
+    assert nlf.c0_count.tolist() == [1, 3, 3]
+    assert nlf.cand(0).tolist() == [3]
+    assert 0 in ldf.cand(0).tolist()
+    assert oracle.count(g, ql, qe) == 2
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_nlf_filter_is_sound_and_stronger(seed):
+    """Every embedding maps u into the label-frequency CST's C(u), and each
+    of its candidate sets lies inside the degree filter's."""
+    n, edges, labels, ql, qe = _cst_case(seed)
+    g = oracle.Graph(n, edges, labels)
+    ldf = oracle.Cst(g, ql, qe)
+    nlf = oracle.Cst(g, ql, qe, filter="nlf")
+    k = len(ql)
+    r = oracle.match(g, ql, qe, max_emb=1 << 18)
+    cand = [set(nlf.cand(u).tolist()) for u in range(k)]
+    for row in r["emb"].tolist():
+        for u in range(k):
+            assert row[u] in cand[u]
+    assert all(a <= b for a, b in zip(nlf.c0_count.tolist(), ldf.c0_count.tolist()))
+    for u in range(k):
+        # with the same root (so the same t_q) the refined sets shrink too
+        assert set(nlf.cand(u).tolist()) <= set(ldf.cand(u).tolist()) or nlf.root != ldf.root
