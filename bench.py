@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--threads", type=int, default=8, help="host threads building CSTs in a batched step")
     p.add_argument("--batch-budget", type=float, default=60.0, help="seconds for one batched matcher launch")
     p.add_argument("--no-serve", dest="serve", action="store_false", help="skip the serving sweep")
+    p.add_argument("--filter", choices=["ldf", "nlf"], default="nlf",
+                   help="candidate filter: label frequencies (nlf, default) or label and degree only (ldf)")
     p.add_argument("--order", choices=["path", "greedy"], default="greedy",
                    help="matching order: the greedy rule (default) or the paper's path-based order "
                         "(also reported beside the headline as path_order)")
@@ -90,7 +92,8 @@ def workload(args, rank: int):
             qs += synth.walk_queries(n, e, lab, k, args.queries, kind, seed=args.seed, stream0=stream0)
     desc = (f"Chung-Lu gamma=2.1, n=1,000,000, m=16,000,000, 16 Zipf(1.0) labels; "
             f"{len(qs)} random-walk queries (8/16 vertices x dense/sparse); per query: CST, Alg. 2 partition "
-            f"(delta_w={args.delta_w}, max_chunks={args.max_chunks}), {args.order} matching order, match until limit={args.limit} "
+            f"(delta_w={args.delta_w}, max_chunks={args.max_chunks}), {args.order} matching order, "
+            f"{args.filter} candidate filter, match until limit={args.limit} "
             f"embeddings (count = min(total, limit)), budget {args.budget} s; seed={args.seed}")
     return n, e, lab, qs, desc
 
@@ -273,7 +276,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     g = F.Graph(n, e, lab)
     cfg = F.default_config(delta_w=args.delta_w, max_chunks=args.max_chunks, limit=args.limit,
-                           time_budget_s=args.budget, order_rule=1 if args.order == "greedy" else 0)
+                           time_budget_s=args.budget, order_rule=1 if args.order == "greedy" else 0,
+                           filter_rule=1 if args.filter == "nlf" else 0)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
     bq = [(q.labels, q.edges) for q in qs]
 
@@ -434,7 +438,7 @@ def run_ours(args):
         "config": {"workload": desc, "queries_per_step": len(qs),
                    "mode": f"batched: fast_batch_run, {args.threads} build threads, one graph-replayed matcher "
                            f"launch per step (budget {args.batch_budget} s)",
-                   "order": args.order,
+                   "order": args.order, "filter": args.filter,
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}, queries per rank"},
         "queries_per_sec": len(qs) * steps * world / t_s,
         "embeddings_per_step": tot_emb / steps,

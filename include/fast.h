@@ -106,6 +106,11 @@ typedef struct {
      * (ties: smaller |C(u)|, then smaller u).  The paper's method takes any
      * connected order; embeddings and counts never depend on it. */
     int32_t order_rule;
+    /* Candidate filter of fast_build_cst (Sec. IV-A, local features).  0:
+     * label and degree, C0(u) = { v : l(v) = l_q(u), d(v) >= d_q(u) }.  1:
+     * also neighbour label frequencies: for every label, v has at least as
+     * many neighbours with it as u has (smaller CSTs; the same embeddings). */
+    int32_t filter_rule;
 } fast_config;
 
 /* Default tunables: delta_w = 2^20, no sampling, max_chunks = 2^16,

@@ -56,9 +56,11 @@ struct FilterF {
     const int32_t* bucket;
     const int32_t* key;
     int dq;
+    const uint32_t* pass;      // label-frequency rule: the vertices that passed (null: degree rule)
     __device__ void begin(int64_t) {}
     __device__ bool eval(int64_t i, int32_t& v) const {
         v = bucket[i];
+        if (pass) return (pass[v >> 5] >> (v & 31)) & 1u;
         return (key[v] & 255) >= dq;
     }
     __device__ int64_t tag(int64_t) const { return -1; }
@@ -68,6 +70,52 @@ struct FilterF {
 // Per candidate row: where its neighbours with label l start in col (beg)
 // and how many there are (len) -- the label's run of a grouped graph, or the
 // whole row otherwise.
+// Label-frequency filter (filter_rule 1).  For every query vertex u
+// (blockIdx.y) and every vertex v of u's label bucket: v passes if
+// d(v) >= d_q(u) and, for each label that n_u of u's query neighbours carry,
+// v has at least n_u neighbours with that label (its label run, or a count
+// along the row when the graph is not grouped).  Passing vertices get a bit
+// in u's bitmap; cnt[u] counts them.
+struct NlfReq {
+    int nn[kMaxK];                 // distinct labels among u's query neighbours
+    int32_t lab[kMaxK][kMaxK];
+    int32_t need[kMaxK][kMaxK];
+};
+
+__device__ __forceinline__ int64_t neighbours_with_label(const GraphRuns& G, const int32_t* __restrict__ col,
+                                                         const int32_t* __restrict__ label, int32_t v, int32_t l) {
+    int64_t b, len;
+    label_segment(G, v, l, &b, &len);
+    if (G.run_ptr) return len;
+    int64_t c = 0;                                 // ungrouped: the whole row, count it
+    for (int64_t i = b; i < b + len; i++) c += label[col[i]] == l;
+    return c;
+}
+
+__global__ void k_filter_nlf(const int32_t* __restrict__ lab_vtx, const int32_t* __restrict__ key,
+                             const int64_t* __restrict__ lo, const int64_t* __restrict__ hi,
+                             const int32_t* __restrict__ dq, const __grid_constant__ NlfReq R, GraphRuns G,
+                             const int32_t* __restrict__ col, const int32_t* __restrict__ label,
+                             uint32_t* __restrict__ bits, int64_t nw, unsigned long long* __restrict__ cnt) {
+    const int u = blockIdx.y;
+    const int64_t a = lo[u], b = hi[u];
+    const int want = dq[u];
+    uint32_t* bu = bits + (int64_t)u * nw;
+    unsigned long long c = 0;
+    for (int64_t i = a + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = lab_vtx[i];
+        bool ok = (key[v] & 255) >= want;
+        for (int t = 0; ok && t < R.nn[u]; t++)
+            ok = neighbours_with_label(G, col, label, v, R.lab[u][t]) >= R.need[u][t];
+        if (ok) {
+            atomicOr(&bu[v >> 5], 1u << (v & 31));
+            c++;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt[u], c);
+}
+
 __global__ void k_cand_segment(const int32_t* __restrict__ cand, int64_t nc, GraphRuns G, int32_t l,
                                int64_t* __restrict__ beg, int64_t* __restrict__ len) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -133,6 +181,7 @@ struct TopDownF {
     int32_t want_key_hi;       // label
     int32_t want_dq;
     bool label_known;          // grouped graph: a segment holds only that label
+    const uint32_t* pass;      // label-frequency rule: u's filter as a bitmap (null: label and degree)
     uint32_t* reached;         // bitmap over V(G)
     int64_t* t_off;            // out: [rows+1]
     const int64_t* E;          // edge-space size on the device (index space may be a bound)
@@ -152,7 +201,9 @@ struct TopDownF {
         int32_t x = col[nbase + i];
         v = x;
         bool hit;
-        if (label_known && want_dq <= 1) {
+        if (pass) {
+            hit = (pass[x >> 5] >> (x & 31)) & 1u;  // label, degree and frequencies at once
+        } else if (label_known && want_dq <= 1) {
             hit = true;                        // the label is the segment's; a neighbour has degree >= 1
         } else {
             int32_t kk = key[x];
@@ -600,6 +651,9 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
     FAST_TRY(validate_query(q, A, dq));
     if (cfg_in && (cfg_in->order_rule < 0 || cfg_in->order_rule > 1))
         return set_error(FAST_ERR_INVALID, "fast_build_cst: order_rule %d (0 path-based, 1 greedy)", cfg_in->order_rule);
+    if (cfg_in && (cfg_in->filter_rule < 0 || cfg_in->filter_rule > 1))
+        return set_error(FAST_ERR_INVALID, "fast_build_cst: filter_rule %d (0 label and degree, 1 label frequencies)",
+                         cfg_in->filter_rule);
     const int k = q->n;
     fast_cst* c = new fast_cst();
     memset(c->cand, 0, sizeof(c->cand)); memset(c->t_off, 0, sizeof(c->t_off)); memset(c->t_idx, 0, sizeof(c->t_idx));
@@ -624,6 +678,8 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
     int64_t* e_off = nullptr;
     int64_t* seg = nullptr;                 // per candidate row: start of its label segment in col
     const GraphRuns G = graph_runs(g);
+    const bool nlf = c->cfg.filter_rule == 1;
+    uint32_t* nlf_bits = nullptr;           // label-frequency rule: [k][nw] bitmaps of C0
     unsigned long long* cnt_d = nullptr;
     int32_t* dq_d = nullptr;
     int64_t* lo_d = nullptr;
@@ -662,7 +718,24 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         cudaMemcpyAsync(lo_d + k, hi, k * sizeof(int64_t), cudaMemcpyHostToDevice, s);
         {
             dim3 grid((unsigned)std::min<int64_t>(ceil_div(maxb, 256), 1024), (unsigned)k);
-            k_filter_count<<<grid, 256, 0, s>>>(g->lab_vtx, g->key, lo_d, lo_d + k, dq_d, cnt_d);
+            if (nlf) {
+                NlfReq R;
+                memset(&R, 0, sizeof(R));
+                for (int u = 0; u < k; u++)
+                    for (int w = 0; w < k; w++) {
+                        if (!A[u][w]) continue;
+                        int t = 0;
+                        while (t < R.nn[u] && R.lab[u][t] != q->labels[w]) t++;
+                        if (t == R.nn[u]) { R.lab[u][t] = q->labels[w]; R.need[u][t] = 0; R.nn[u]++; }
+                        R.need[u][t]++;
+                    }
+                rc = dalloc(&nlf_bits, (size_t)k * nw, s); if (rc) break;
+                cudaMemsetAsync(nlf_bits, 0, (size_t)k * nw * sizeof(uint32_t), s);
+                k_filter_nlf<<<grid, 256, 0, s>>>(g->lab_vtx, g->key, lo_d, lo_d + k, dq_d, R, G, g->col, g->label,
+                                                  nlf_bits, nw, cnt_d);
+            } else {
+                k_filter_count<<<grid, 256, 0, s>>>(g->lab_vtx, g->key, lo_d, lo_d + k, dq_d, cnt_d);
+            }
             note_launch();
         }
         unsigned long long hc[kMaxK];
@@ -689,7 +762,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         // ------------------------------------------------ C(root) = C0(root)
         rc = dalloc(&td_cand[r], cap_c[r], s); if (rc) break;
         {
-            FilterF f{g->lab_vtx + lo[r], g->key, dq[r]};
+            FilterF f{g->lab_vtx + lo[r], g->key, dq[r], nlf ? nlf_bits + (int64_t)r * nw : nullptr};
             rc = compact(f, hi[r] - lo[r], td_cand[r], sz + r, s); if (rc) break;
         }
 
@@ -719,6 +792,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
             f.e_off = e_off; f.rows = rows; f.seg = seg; f.col = g->col; f.key = g->key;
             f.want_key_hi = q->labels[u]; f.want_dq = dq[u]; f.reached = bits[u].alive; f.t_off = td_off[u];
             f.label_known = G.run_ptr != nullptr;
+            f.pass = nlf ? nlf_bits + (int64_t)u * nw : nullptr;
             f.E = e_off + rows;
             int64_t* kept = sz + 3 * kMaxK + kMaxNT;          // scratch word
             rc = compact(f, E, td_list[u], kept, s); if (rc) break;
@@ -940,6 +1014,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         dfree(bits[u].alive, s); dfree(bits[u].rank, s);
     }
     dfree(e_off, s); dfree(seg, s); dfree(cnt_d, s); dfree(dq_d, s); dfree(lo_d, s); dfree(sz, s);
+    dfree(nlf_bits, s);
     // The lists were built in buffers sized by bounds; keep exact copies.
     if (rc == FAST_OK) rc = cst_to_arena(c, s);
     free_build_arrays(c, s);

@@ -35,5 +35,5 @@ def test_binding_covers_every_declared_symbol():
 def test_config_default_without_gpu():
     c = F.default_config()
     assert c.delta_w == 1 << 20 and c.warps_per_block == 8 and c.max_chunks == 1 << 16 and c.limit == 0
-    assert c.queue_cells == 0 and c.order_rule == 0
+    assert c.queue_cells == 0 and c.order_rule == 0 and c.filter_rule == 0
     assert F.lib().fast_last_error() == b""

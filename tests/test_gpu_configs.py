@@ -75,10 +75,12 @@ def test_batched_1000_mixed_queries(powerlaw_1m):
     counts, status = b.run(qs)
     compared = check_against_oracle(o, qs, counts, status, L)
     assert compared >= 900, compared
-    # the same batch in the paper's path-based order gives the same counts
-    b0 = F.Batch(g, len(qs), F.default_config(limit=L, order_rule=0, time_budget_s=120.0))
-    c0, s0 = b0.run(qs)
-    assert s0.tolist() == status.tolist() and c0.tolist() == counts.tolist()
+    # the same batch in the paper's path-based order, and with the
+    # label-frequency filter, gives the same counts
+    for extra in (dict(order_rule=0), dict(order_rule=1, filter_rule=1)):
+        b0 = F.Batch(g, len(qs), F.default_config(limit=L, time_budget_s=120.0, **extra))
+        c0, s0 = b0.run(qs)
+        assert s0.tolist() == status.tolist() and c0.tolist() == counts.tolist(), extra
 
 
 @pytest.fixture(scope="module")

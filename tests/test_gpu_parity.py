@@ -263,6 +263,64 @@ def test_order_rule_rejected_when_unknown(er):
     assert ei.value.code == F.FAST_ERR_INVALID
 
 
+# ------------------------------------ candidate filter: label frequencies
+
+NLF = dict(filter_rule=1)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_cst_random_label_frequency_filter(seed):
+    """filter_rule 1 against the oracle's restatement: every CST array (the
+    root may change, since it follows the filtered counts), in both orders."""
+    n, e, lab, ql, qe = rand_case(1000 + seed)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    compare_cst(F.Cst(g, ql, qe, F.default_config(**NLF)), oracle.Cst(o, ql, qe, filter="nlf"), len(ql))
+    compare_cst(F.Cst(g, ql, qe, F.default_config(order_rule=1, **NLF)),
+                oracle.Cst(o, ql, qe, order="greedy", filter="nlf"), len(ql))
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_match_random_label_frequency_filter(seed):
+    n, e, lab, ql, qe = rand_case(2000 + seed)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    cst = F.Cst(g, ql, qe, F.default_config(order_rule=1, **NLF))
+    want = oracle.match(o, ql, qe, max_emb=1 << 20)
+    assert F.match(cst)["count"] == want["count"]
+    if want["count"] <= 200_000:
+        r2 = F.match(cst, k=want["count"] + 3)
+        assert np.array_equal(sorted_rows(r2["emb"][:r2["written"]].astype(np.int32)), want["emb"])
+
+
+def test_er_queries_label_frequency_filter(er):
+    w, g, o = er
+    for q in w.queries:
+        gc = F.Cst(g, q.labels, q.edges, F.default_config(**NLF))
+        compare_cst(gc, oracle.Cst(o, q.labels, q.edges, filter="nlf"), q.k)
+        assert F.match(gc)["count"] == oracle.count(o, q.labels, q.edges)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_partition_matches_oracle_label_frequency_filter(seed):
+    n, e, lab, ql, qe = rand_case(4000 + seed, n_lo=60, n_hi=250, k_hi=6, L_hi=3)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    gc, oc = F.Cst(g, ql, qe, F.default_config(**NLF)), oracle.Cst(o, ql, qe, filter="nlf")
+    if gc.W == 0:
+        return
+    total = oracle.count(o, ql, qe)
+    delta = max(1, gc.W // 20)
+    ch = F.Chunks(gc, F.default_config(delta_w=delta, sample_seed=seed, **NLF))
+    assert gpu_chunks_global(gc, ch) == oc.partition(delta, 0.0, 0.0, seed)
+    assert F.match(gc, ch)["count"] == total
+
+
+def test_filter_rule_rejected_when_unknown(er):
+    w, g, o = er
+    q = w.queries[0]
+    with pytest.raises(F.FastError) as ei:
+        F.Cst(g, q.labels, q.edges, F.default_config(filter_rule=2))
+    assert ei.value.code == F.FAST_ERR_INVALID
+
+
 # --------------------------------------------------------------- partition
 
 @pytest.mark.parametrize("seed", range(15))
