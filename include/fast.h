@@ -34,8 +34,12 @@
  *   - Handles (fast_graph, fast_cst, fast_chunks) are opaque, owned by the
  *     library and released with their fast_free_* function.  Input arrays
  *     are copied; the caller keeps ownership of everything it passes in.
- *   - All device memory the library needs is allocated stream-ordered
- *     (cudaMallocAsync) on the current CUDA device.
+ *   - Device memory is on the current CUDA device.  Graphs and chunk lists
+ *     are allocated stream-ordered (cudaMallocAsync); a CST holds one
+ *     exact-size stream-ordered block; the temporaries of a call come from
+ *     a scratch pool of cached device blocks (one per calling thread, and
+ *     one per batch or server worker), kept until that thread, batch or
+ *     server ends.  fast_match_noalloc allocates nothing.
  */
 #ifndef FAST_GB300_H
 #define FAST_GB300_H
@@ -249,10 +253,12 @@ void fast_free_chunks(fast_chunks* ch);
 /*
  * Enumerate the embeddings in `chunks` (NULL: the whole CST as one chunk)
  * -- the semantics of Algorithms 4-8 (Sec. V-A): every partial result is
- * extended by the tree list of its parent position's candidate (Generator),
- * kept only if the new vertex is not already used (VisitedValidator) and is
- * adjacent to the images of its earlier non-tree neighbours in the CST
- * (EdgeValidator), and reported once complete (Synchronizer).
+ * extended by the candidates of the next position in the tree list of its
+ * parent's image (Generator), kept only if the new vertex is not already
+ * used (VisitedValidator) and is adjacent to the images of its earlier
+ * non-tree neighbours in the CST (EdgeValidator), and reported once complete
+ * (Synchronizer).  The Generator may scan whichever of those lists is
+ * shortest (their intersection is the same set).
  *   k:           embeddings to write (0: count only).
  *   emb_out:     device buffer of k rows x |V(q)| uint32 data-vertex ids,
  *                column u = M(u) (query vertex id order); any k embeddings
@@ -393,7 +399,7 @@ uint64_t fast_now_ns(void);
  * cudaFree, no host staging buffer.
  *
  * Scratch: one file-scope device array of fast_match_noalloc_scratch_bytes()
- * bytes (about 5.9 MB: the counter block, a queue of 4096 donated runs and
+ * bytes (about 5.9 MB: the counter block, a ring of 4096 donated runs and
  * up to 32768 root-run descriptors) that every GPU loading the library keeps
  * until the process exits.  The first call on a device looks up its address
  * (cudaGetSymbolAddress, with that device current); make that first call
@@ -423,8 +429,9 @@ double fast_last_match_ms(void);
 
 /* Bytes the last fast_match on this host thread requested from memory:
  * 16 B of offsets per list opened (a tree list per extended partial result,
- * a non-tree list per earlier non-tree neighbour), 4 B per tree-list entry
- * scanned, 4 B per entry a binary search reads, 4 B per data-vertex id
+ * a non-tree list per earlier non-tree neighbour), 4 B per generator-list
+ * entry scanned, 4 B per list entry the membership checks read (merge tiles,
+ * gallops, the prefix checks' binary searches), 4 B per data-vertex id
  * gathered, and 4|V(q)| B per embedding written.  Counted by every lane of
  * the search itself, whichever level of the memory hierarchy serves it. */
 uint64_t fast_last_match_bytes(void);
