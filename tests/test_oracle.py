@@ -551,3 +551,23 @@ def test_nlf_filter_is_sound_and_stronger(seed):
     for u in range(k):
         # with the same root (so the same t_q) the refined sets shrink too
         assert set(nlf.cand(u).tolist()) <= set(ldf.cand(u).tolist()) or nlf.root != ldf.root
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("order,filt", [("greedy", "ldf"), ("path", "nlf"), ("greedy", "nlf")])
+def test_partition_complete_for_every_order_and_filter(seed, order, filt):
+    """Alg. 2 over the CST of either matching order and either candidate
+    filter: the chunks' counts add up to the embeddings of the plain
+    definition (disjoint and complete), with and without the chunk cap."""
+    n, edges, labels, ql, qe = _cst_case(930 + seed)
+    g = oracle.Graph(n, edges, labels)
+    c = oracle.Cst(g, ql, qe, order=order, filter=filt)
+    wf, wi, _, _ = c.workload()
+    total = oracle.count(g, ql, qe)
+    if wi == 0:
+        assert total == 0
+        return
+    for cap in (1 << 16, 5):
+        chunks = c.partition(max(1, wi // 30), max_chunks=cap)
+        s = sum(oracle.count(g, ql, qe, allow=c.chunk_allow(j, pre, a, b)) for (j, pre, a, b, w, i) in chunks)
+        assert s == total
