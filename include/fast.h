@@ -298,7 +298,9 @@ typedef struct fast_batch fast_batch;
  * 8), and, once run, a CUDA graph of the matcher launch that later runs
  * replay.  cfg (NULL: defaults) seeds every query-size class's configuration
  * (classes: |V(q)| <= 4, 8, 16, 24, 32); cfg->limit and time_budget_s apply
- * to every query of a run.  Uses the current CUDA device.
+ * to every query of a run.  Uses the current CUDA device.  One call at a
+ * time per fast_batch (its buffers, graph and per-worker scratch pools are
+ * shared by its runs); separate fast_batch objects may run concurrently.
  */
 int fast_batch_create(const fast_graph* g, const fast_config* cfg, int32_t max_queries, int32_t threads,
                       fast_batch** out);
