@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--threads", type=int, default=8, help="host threads building CSTs in a batched step")
     p.add_argument("--batch-budget", type=float, default=60.0, help="seconds for one batched matcher launch")
     p.add_argument("--no-serve", dest="serve", action="store_false", help="skip the serving sweep")
+    p.add_argument("--autotune", action="store_true",
+                   help="before timing, autotune the batch (delta_w, max_chunks, launch shape per size class) "
+                        "on a separate sample of queries (seed + 1)")
     p.add_argument("--filter", choices=["ldf", "nlf"], default="nlf",
                    help="candidate filter: label frequencies (nlf, default) or label and degree only (ldf)")
     p.add_argument("--order", choices=["path", "greedy"], default="greedy",
@@ -287,6 +290,20 @@ def run_ours(args):
     bcfg = F.Config.from_buffer_copy(cfg)
     bcfg.time_budget_s = args.batch_budget
     bt = F.Batch(g, len(bq), bcfg, threads=args.threads)
+    tuned = None
+    if args.autotune:
+        import synth
+        wg = synth.WalkGraph(n, e)
+        sample = []
+        for k in (8, 16):
+            for kind in ("dense", "sparse"):
+                for j in range(10):
+                    q = wg.query(lab, k, kind, args.seed + 1, query_stream0(rank, k, kind) + j)
+                    sample.append((q.labels, q.edges))
+        wg.close()
+        bt.autotune(sample, stream=stream.cuda_stream)
+        tuned = {str(k): {f: getattr(bt.config(k), f) for f in ("delta_w", "max_chunks", "warps_per_block", "blocks_per_sm")}
+                 for k in (8, 16)}
 
     def bstep():
         flush.zero_()
@@ -438,7 +455,7 @@ def run_ours(args):
         "config": {"workload": desc, "queries_per_step": len(qs),
                    "mode": f"batched: fast_batch_run, {args.threads} build threads, one graph-replayed matcher "
                            f"launch per step (budget {args.batch_budget} s)",
-                   "order": args.order, "filter": args.filter,
+                   "order": args.order, "filter": args.filter, "autotuned": tuned,
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}, queries per rank"},
         "queries_per_sec": len(qs) * steps * world / t_s,
         "embeddings_per_step": tot_emb / steps,
