@@ -273,6 +273,10 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        F.build()                      # one rank compiles (if anything is stale); the others then load
+    if dist:
+        dist.barrier()
     F.build()
     F.lib()
     n, e, lab, qs, desc = workload(args, rank)
