@@ -373,11 +373,17 @@ typedef struct {
 int fast_server_create(const fast_graph* g, const fast_config* cfg, uint64_t budget_bytes, int32_t workers,
                        fast_server** out);
 
-/* Queue one query (its arrays are copied); *id_out (nullable) gets its id. */
+/* Queue one query (its arrays are copied); *id_out (nullable) gets its id.
+ * FAST_ERR_INVALID here only for a NULL server or query, a vertex count
+ * outside 1..32, NULL arrays or a negative edge count; any other malformed
+ * query (an edge endpoint out of range, a loop, a negative label, a
+ * disconnected graph) is queued and comes back with status FAST_ERR_INVALID
+ * in its result. */
 int fast_server_submit(fast_server* s, const fast_query_desc* q, uint64_t* id_out);
 
-/* Move up to max_results finished requests into out (any order), waiting
- * up to wait_ms for the first one when none is ready; *n_out = how many. */
+/* Move up to max_results (>= 0) finished requests into out (any order),
+ * waiting up to wait_ms for the first one when none is ready; *n_out = how
+ * many. */
 int fast_server_poll(fast_server* s, int32_t max_results, fast_result* out, int32_t* n_out, int32_t wait_ms);
 
 /* Requests queued, requests running, projected bytes admitted. */

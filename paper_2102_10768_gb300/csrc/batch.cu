@@ -253,8 +253,9 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
     match_plan_set_stride(b->h_plans, nq, warp_words);
     do {
         if (total > b->chunk_cap) {
-            dfree(b->d_chunks, s);
             int64_t cap = std::max<int64_t>(total, 2 * b->chunk_cap);
+            dfree(b->d_chunks, s);
+            b->chunk_cap = 0;                     // stays 0 if the allocation below fails
             rc = dalloc(&b->d_chunks, (size_t)cap * match_chunk_bytes(), s); if (rc) break;
             b->chunk_cap = cap;
         }
@@ -267,11 +268,9 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
             }
         }
         if (rc) break;
-        if (nq > 0) {
-            FAST_CUDA(cudaMemcpyAsync(b->d_plans, b->h_plans, (size_t)nq * b->psize, cudaMemcpyHostToDevice, s));
-            FAST_CUDA(cudaMemcpyAsync(b->d_off, b->h_off, (size_t)(nq + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        }
-        FAST_CUDA(cudaMemcpyAsync(b->d_nchunks, &b->h_off[nq], sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        if (nq > 0) FAST_CUDA_BREAK(rc, cudaMemcpyAsync(b->d_plans, b->h_plans, (size_t)nq * b->psize, cudaMemcpyHostToDevice, s));
+        if (nq > 0) FAST_CUDA_BREAK(rc, cudaMemcpyAsync(b->d_off, b->h_off, (size_t)(nq + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        FAST_CUDA_BREAK(rc, cudaMemcpyAsync(b->d_nchunks, &b->h_off[nq], sizeof(int64_t), cudaMemcpyHostToDevice, s));
         if (total > 0) {
             k_tag_chunks<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 4096), 256, 0, s>>>((Chunk*)b->d_chunks, b->d_off, nq);
             note_launch();
@@ -281,11 +280,11 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
         lc.warps_per_block = b->cls[0].warps_per_block;
         lc.blocks_per_sm = b->cls[0].blocks_per_sm;
         rc = batch_graph(b, warp_words, lc, s); if (rc) break;
-        FAST_CUDA(cudaEventRecord(b->ev0, s));
-        FAST_CUDA(cudaGraphLaunch(b->exec, s));
-        FAST_CUDA(cudaEventRecord(b->ev1, s));
-        if (nq > 0) FAST_CUDA(cudaMemcpyAsync(b->h_qtotal, b->d_qtotal, (size_t)nq * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        FAST_CUDA(cudaMemcpyAsync(b->h_ctr, b->d_ctr, match_counter_words() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        FAST_CUDA_BREAK(rc, cudaEventRecord(b->ev0, s));
+        FAST_CUDA_BREAK(rc, cudaGraphLaunch(b->exec, s));
+        FAST_CUDA_BREAK(rc, cudaEventRecord(b->ev1, s));
+        if (nq > 0) FAST_CUDA_BREAK(rc, cudaMemcpyAsync(b->h_qtotal, b->d_qtotal, (size_t)nq * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        FAST_CUDA_BREAK(rc, cudaMemcpyAsync(b->h_ctr, b->d_ctr, match_counter_words() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { rc = cuda_status(e, "fast_batch_run", __FILE__, __LINE__); break; }
         float ms = 0.f;

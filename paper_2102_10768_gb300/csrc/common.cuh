@@ -30,6 +30,14 @@ int cuda_status(cudaError_t e, const char* what, const char* file, int line);
         if (_e != cudaSuccess) return ::fast::cuda_status(_e, #call, __FILE__, __LINE__); \
     } while (0)
 
+// For a `do { ... } while (0)` block with cleanup after it: on a CUDA error,
+// stores the status in rc and leaves the block instead of returning.
+#define FAST_CUDA_BREAK(rc, call)                                                          \
+    {                                                                                      \
+        cudaError_t _e = (call);                                                           \
+        if (_e != cudaSuccess) { (rc) = ::fast::cuda_status(_e, #call, __FILE__, __LINE__); break; } \
+    }
+
 #define FAST_TRY(call)                    \
     do {                                  \
         int _rc = (call);                 \

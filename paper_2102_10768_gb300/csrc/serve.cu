@@ -62,21 +62,25 @@ namespace {
 // Projected device bytes of a query's CST: for every query vertex, its label
 // bucket (candidate ids, two bitmaps with ranks over V(G)); for every query
 // edge, the neighbour lists of the bucket of one end (the top-down and
-// non-tree lists are at most that), and the matcher's fixed scratch.
+// non-tree lists are at most that), and the matcher's fixed scratch.  The
+// query is not validated yet (its build does that and reports a malformed
+// query in the result's status), so labels outside G's range count as empty
+// buckets and edges with an endpoint outside the query are skipped.
 uint64_t projected_bytes(const fast_server* S, const Req& r) {
     const fast_graph* g = S->g;
-    int k = (int)r.labels.size();
+    const int k = (int)r.labels.size();
     double b = 16.0 * 1024 * 1024;               // matcher counters, queue, chunk lists
+    auto known = [&](int32_t l) { return l >= 0 && l < g->num_labels; };
     auto bucket = [&](int32_t l) -> double {
-        if (l < 0 || l >= g->num_labels) return 0.0;
-        return (double)(g->lab_ptr_host[l + 1] - g->lab_ptr_host[l]);
+        return known(l) ? (double)(g->lab_ptr_host[l + 1] - g->lab_ptr_host[l]) : 0.0;
     };
+    auto lists = [&](int32_t l) -> double { return known(l) ? S->label_deg[l] * bucket(l) : 0.0; };
     for (int u = 0; u < k; u++) b += 4.0 * bucket(r.labels[u]) + 2.0 * (double)g->n / 8.0 + 8.0 * bucket(r.labels[u]);
     for (size_t e = 0; e + 1 < r.edges.size(); e += 2) {
-        int32_t la = r.labels[r.edges[e]], lb = r.labels[r.edges[e + 1]];
-        double da = la < (int)S->label_deg.size() ? S->label_deg[la] * bucket(la) : 0.0;
-        double db = lb < (int)S->label_deg.size() ? S->label_deg[lb] * bucket(lb) : 0.0;
-        b += 4.0 * std::max(da, db) + 12.0 * (bucket(la) + bucket(lb));
+        int32_t a = r.edges[e], c = r.edges[e + 1];
+        if (a < 0 || a >= k || c < 0 || c >= k) continue;
+        int32_t la = r.labels[a], lb = r.labels[c];
+        b += 4.0 * std::max(lists(la), lists(lb)) + 12.0 * (bucket(la) + bucket(lb));
     }
     return (uint64_t)b;
 }
@@ -216,7 +220,8 @@ extern "C" int fast_server_submit(fast_server* S, const fast_query_desc* q, uint
 
 extern "C" int fast_server_poll(fast_server* S, int32_t max_results, fast_result* out, int32_t* n_out,
                                 int32_t wait_ms) {
-    if (!S || !n_out || (max_results > 0 && !out)) return set_error(FAST_ERR_INVALID, "fast_server_poll: bad arguments");
+    if (!S || !n_out || max_results < 0 || (max_results > 0 && !out))
+        return set_error(FAST_ERR_INVALID, "fast_server_poll: bad arguments");
     std::unique_lock<std::mutex> lk(S->mu);
     if (S->done.empty() && wait_ms > 0)
         S->cv.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !S->done.empty(); });

@@ -84,6 +84,33 @@ def test_request_beyond_the_budget_is_rejected(env):
     assert res[0]["id"] == rid and res[0]["status"] == F.FAST_ERR_OOM
 
 
+def test_malformed_requests_come_back_invalid(env):
+    import ctypes
+    w, g, qs, alone = env
+    bad = [
+        (np.array([0, 1, 2], np.int32), np.array([[0, 1], [1, 7]], np.int32)),    # endpoint out of range
+        (np.array([0, -3, 2], np.int32), np.array([[0, 1], [1, 2]], np.int32)),   # negative label
+        (np.array([0, 1, 2], np.int32), np.array([[0, 1], [-1, 2]], np.int32)),   # negative endpoint
+        (np.array([0, 1, 2], np.int32), np.array([[0, 1]], np.int32)),            # disconnected
+        (np.array([0, 1], np.int32), np.array([[0, 0], [0, 1]], np.int32)),       # loop
+    ]
+    s = F.Server(g, budget_bytes=1 << 40, workers=2)
+    ids = {s.submit(*q): ("bad", i) for i, q in enumerate(bad)}
+    ids.update({s.submit(*q): ("good", i) for i, q in enumerate(qs[:4])})
+    res = drain(s, len(ids))
+    n = ctypes.c_int32(-1)
+    rc = F.lib().fast_server_poll(s._h, -1, None, ctypes.byref(n), 0)
+    s.close()
+    assert rc == F.FAST_ERR_INVALID
+    assert len(res) == len(ids)
+    for r in res:
+        kind, i = ids[r["id"]]
+        if kind == "bad":
+            assert r["status"] == F.FAST_ERR_INVALID and r["count"] == 0, (i, r)
+        else:
+            assert r["status"] == 0 and r["count"] == alone[i]
+
+
 def test_limit_in_the_mix_matches_oracle():
     n, e, lab = synth.powerlaw_graph(seed=2000, n=200_000, m=3_200_000)
     g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
