@@ -1066,7 +1066,8 @@ extern "C" int fast_cst_tree_size(const fast_cst* c, int32_t u, int64_t* entries
 }
 
 extern "C" int fast_cst_tree_lists(const fast_cst* c, int32_t u, int64_t* off, uint32_t* idx, void* stream) {
-    if (!c || u < 0 || u >= c->k || c->parent[u] < 0 || !off) return set_error(FAST_ERR_INVALID, "fast_cst_tree_lists: bad argument");
+    if (!c || u < 0 || u >= c->k || c->parent[u] < 0 || !off || (!idx && c->t_entries[u]))
+        return set_error(FAST_ERR_INVALID, "fast_cst_tree_lists: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t rows = c->ncand[c->parent[u]];
     FAST_CUDA(cudaMemcpyAsync(off, c->t_off[u], (rows + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1090,7 +1091,8 @@ extern "C" int fast_cst_nontree_edge(const fast_cst* c, int32_t e, int32_t* from
 }
 
 extern "C" int fast_cst_nontree_lists(const fast_cst* c, int32_t e, int64_t* off, uint32_t* idx, void* stream) {
-    if (!c || e < 0 || e >= c->nnt || !off) return set_error(FAST_ERR_INVALID, "fast_cst_nontree_lists: bad argument");
+    if (!c || e < 0 || e >= c->nnt || !off || (!idx && c->n_entries[e]))
+        return set_error(FAST_ERR_INVALID, "fast_cst_nontree_lists: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t rows = c->ncand[c->nt_from[e]];
     FAST_CUDA(cudaMemcpyAsync(off, c->n_off[e], (rows + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
