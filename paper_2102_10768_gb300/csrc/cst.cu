@@ -30,6 +30,7 @@
 
 #include "internal.cuh"
 #include "prims.cuh"
+#include "cst_funcs.cuh"
 
 using namespace fast;
 
@@ -50,47 +51,12 @@ __global__ void k_filter_count(const int32_t* __restrict__ lab_vtx, const int32_
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt[u], c);
 }
 
-// C0(root): the label bucket filtered by degree (bucket order = id order)
-struct FilterF {
-    using value_type = int32_t;
-    const int32_t* bucket;
-    const int32_t* key;
-    int dq;
-    const uint32_t* pass;      // label-frequency rule: the vertices that passed (null: degree rule)
-    __device__ void begin(int64_t) {}
-    __device__ bool eval(int64_t i, int32_t& v) const {
-        v = bucket[i];
-        if (pass) return (pass[v >> 5] >> (v & 31)) & 1u;
-        return (key[v] & 255) >= dq;
-    }
-    __device__ int64_t tag(int64_t) const { return -1; }
-    __device__ void at(int64_t, int64_t) const {}
-};
-
-// Per candidate row: where its neighbours with label l start in col (beg)
-// and how many there are (len) -- the label's run of a grouped graph, or the
-// whole row otherwise.
 // Label-frequency filter (filter_rule 1).  For every query vertex u
 // (blockIdx.y) and every vertex v of u's label bucket: v passes if
 // d(v) >= d_q(u) and, for each label that n_u of u's query neighbours carry,
 // v has at least n_u neighbours with that label (its label run, or a count
 // along the row when the graph is not grouped).  Passing vertices get a bit
 // in u's bitmap; cnt[u] counts them.
-struct NlfReq {
-    int nn[kMaxK];                 // distinct labels among u's query neighbours
-    int32_t lab[kMaxK][kMaxK];
-    int32_t need[kMaxK][kMaxK];
-};
-
-__device__ __forceinline__ int64_t neighbours_with_label(const GraphRuns& G, const int32_t* __restrict__ col,
-                                                         const int32_t* __restrict__ label, int32_t v, int32_t l) {
-    int64_t b, len;
-    label_segment(G, v, l, &b, &len);
-    if (G.run_ptr) return len;
-    int64_t c = 0;                                 // ungrouped: the whole row, count it
-    for (int64_t i = b; i < b + len; i++) c += label[col[i]] == l;
-    return c;
-}
 
 __global__ void k_filter_nlf(const int32_t* __restrict__ lab_vtx, const int32_t* __restrict__ key,
                              const int64_t* __restrict__ lo, const int64_t* __restrict__ hi,
@@ -116,6 +82,9 @@ __global__ void k_filter_nlf(const int32_t* __restrict__ lab_vtx, const int32_t*
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt[u], c);
 }
 
+// Per candidate row: where its neighbours with label l start in col (beg)
+// and how many there are (len) -- the label's run of a grouped graph, or the
+// whole row otherwise.
 __global__ void k_cand_segment(const int32_t* __restrict__ cand, int64_t nc, GraphRuns G, int32_t l,
                                int64_t* __restrict__ beg, int64_t* __restrict__ len) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,31 +103,6 @@ __global__ void k_cand_segment_n(const int32_t* __restrict__ cand, const int64_t
 // off[*n] = *val (closing offset of a list set whose row count is on the device)
 __global__ void k_set_tail(int64_t* off, const int64_t* n, const int64_t* val) { off[*n] = *val; }
 
-__device__ __forceinline__ int64_t row_of(const int64_t* e_off, int64_t rows, int64_t i) {
-    // last r with e_off[r] <= i
-    int64_t lo = 0, hi = rows;
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (e_off[mid] <= i) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-// The first of the rows whose lists start at index i (row is the last one,
-// the row holding entry i; the others before it are empty).
-__device__ __forceinline__ int64_t first_row_at(const int64_t* e_off, int64_t row, int64_t i) {
-    while (row > 0 && e_off[row - 1] == i) row--;
-    return row;
-}
-
-// new_off[x] = rank for row r and every following row that starts at the
-// same index (empty rows, up to the first row with an entry)
-__device__ __forceinline__ void set_rows_at(const int64_t* e_off, int64_t rows, int64_t r, int64_t* new_off,
-                                            int64_t rank) {
-    const int64_t i = e_off[r];
-    for (int64_t x = r; x < rows && e_off[x] == i; x++) new_off[x] = rank;
-}
-
 // Rows after the last entry (and the closing offset): new_off[r] = total for
 // r <= n with e_off[r] == e_off[n].  n on the device (n_dev) or given.
 __global__ void k_fill_tail(const int64_t* __restrict__ e_off, const int64_t* __restrict__ n_dev, int64_t n_host,
@@ -168,121 +112,6 @@ __global__ void k_fill_tail(const int64_t* __restrict__ e_off, const int64_t* __
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= n && r <= cap; r += (int64_t)gridDim.x * blockDim.x)
         if (e_off[r] == end) new_off[r] = *total;
 }
-
-// Top-down: flattened neighbour lists of C(u_p); keeps neighbours passing
-// u's filter (label and degree), marks them reached, writes list offsets.
-struct TopDownF {
-    using value_type = int32_t;
-    const int64_t* e_off;      // [rows+1]
-    int64_t rows;
-    const int64_t* seg;        // per row of C(u_p): start in col of its neighbours with u's label
-    const int32_t* col;
-    const int32_t* key;
-    int32_t want_key_hi;       // label
-    int32_t want_dq;
-    bool label_known;          // grouped graph: a segment holds only that label
-    const uint32_t* pass;      // label-frequency rule: u's filter as a bitmap (null: label and degree)
-    uint32_t* reached;         // bitmap over V(G)
-    int64_t* t_off;            // out: [rows+1]
-    const int64_t* E;          // edge-space size on the device (index space may be a bound)
-    bool counting;             // set in the compaction's count pass: mark nothing then
-    int64_t row;
-    int64_t nbase;
-    int64_t e_end;
-    __device__ void begin(int64_t i0) {
-        e_end = *E;
-        if (i0 >= e_end) return;
-        row = row_of(e_off, rows, i0);
-        nbase = seg[row] - e_off[row];
-    }
-    __device__ bool eval(int64_t i, int32_t& v) {
-        if (i >= e_end) { v = 0; return false; }
-        while (i >= e_off[row + 1]) { row++; nbase = seg[row] - e_off[row]; }
-        int32_t x = col[nbase + i];
-        v = x;
-        bool hit;
-        if (pass) {
-            hit = (pass[x >> 5] >> (x & 31)) & 1u;  // label, degree and frequencies at once
-        } else if (label_known && want_dq <= 1) {
-            hit = true;                        // the label is the segment's; a neighbour has degree >= 1
-        } else {
-            int32_t kk = key[x];
-            hit = (kk >> 8) == want_key_hi && (kk & 255) >= want_dq;
-        }
-        if (hit && !counting) atomicOr(&reached[x >> 5], 1u << (x & 31));
-        return hit;
-    }
-    // rows start at their first entry; a row with no entry (no neighbour of
-    // the label) starts where the next one does, so the first entry of a
-    // row tags it and every empty row just before it
-    __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? first_row_at(e_off, row, i) : -1; }
-    __device__ void at(int64_t r, int64_t rank) const { set_rows_at(e_off, rows, r, t_off, rank); }
-    __device__ int64_t end() const { return *E; }
-};
-
-// Non-tree: flattened neighbour lists of C(u_j); keeps members of C(u_i)
-// (bitmap) and writes their rank in C(u_i).
-struct NonTreeF {
-    using value_type = uint32_t;
-    const int64_t* e_off;
-    int64_t rows;
-    const int64_t* seg;        // per row of C(u_j): start in col of its neighbours with u_i's label
-    const int32_t* col;
-    const uint32_t* alive;     // bitmap of C(u_i)
-    const uint32_t* rank;      // prefix popcounts of alive
-    int64_t* n_off;
-    const int64_t* E;
-    int64_t row;
-    int64_t nbase;
-    int64_t e_end;
-    __device__ void begin(int64_t i0) {
-        e_end = *E;
-        if (i0 >= e_end) return;
-        row = row_of(e_off, rows, i0);
-        nbase = seg[row] - e_off[row];
-    }
-    __device__ bool eval(int64_t i, uint32_t& v) {
-        if (i >= e_end) { v = 0; return false; }
-        while (i >= e_off[row + 1]) { row++; nbase = seg[row] - e_off[row]; }
-        int32_t x = col[nbase + i];
-        uint32_t w = alive[x >> 5], bit = 1u << (x & 31);
-        v = rank[x >> 5] + __popc(w & (bit - 1));
-        return (w & bit) != 0;
-    }
-    __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? first_row_at(e_off, row, i) : -1; }
-    __device__ void at(int64_t r, int64_t rank_) const { set_rows_at(e_off, rows, r, n_off, rank_); }
-    __device__ int64_t end() const { return *E; }
-};
-
-// candidate ids from a bitmap, in id order
-struct BitsF {
-    using value_type = int32_t;
-    const uint32_t* bits;
-    __device__ void begin(int64_t) {}
-    __device__ bool eval(int64_t i, int32_t& v) const {
-        v = (int32_t)i;
-        return (bits[i >> 5] >> (i & 31)) & 1u;
-    }
-    __device__ int64_t tag(int64_t) const { return -1; }
-    __device__ void at(int64_t, int64_t) const {}
-};
-
-// rows kept by a validity mask
-struct KeepRowsF {
-    using value_type = int32_t;
-    const int32_t* ids;
-    const uint8_t* valid;
-    const int64_t* nrows;      // rows really present (the index space is a bound)
-    __device__ int64_t end() const { return *nrows; }
-    __device__ void begin(int64_t) {}
-    __device__ bool eval(int64_t i, int32_t& v) const {
-        v = ids[i];
-        return valid[i] != 0;
-    }
-    __device__ int64_t tag(int64_t) const { return -1; }
-    __device__ void at(int64_t, int64_t) const {}
-};
-
 
 __global__ void k_popc_words(const uint32_t* __restrict__ bits, int64_t nw, uint32_t* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -302,9 +131,6 @@ __global__ void k_set_bits_n(const int32_t* __restrict__ ids, const int64_t* __r
 // entries, so these kernels split the entry space, not the rows: a block
 // takes tiles of kTileItems entries (grid-stride), each thread kItems
 // consecutive entries, finds its first row by binary search and advances it.
-
-constexpr int kItems = 8;
-constexpr int kTileItems = 256 * kItems;
 
 inline unsigned tile_grid(int64_t entries_bound) {
     int64_t t = ceil_div(entries_bound, (int64_t)kTileItems);
@@ -334,11 +160,6 @@ __global__ void __launch_bounds__(256) k_any_alive(const int64_t* __restrict__ o
     }
 }
 
-struct ChildFlags {
-    const uint8_t* has[kMaxK];
-    int nch;
-};
-
 // valid[r] = r < *nrows and every child list of row r keeps an entry
 __global__ void k_valid_rows_n(ChildFlags cf, const int64_t* __restrict__ nrows, int64_t cap,
                                uint8_t* __restrict__ valid, int64_t* __restrict__ vflag) {
@@ -348,52 +169,6 @@ __global__ void k_valid_rows_n(ChildFlags cf, const int64_t* __restrict__ nrows,
     for (int c = 0; c < cf.nch && ok; c++) ok &= cf.has[c][r];
     valid[r] = ok;
     vflag[r] = ok;
-}
-
-// Bottom-up rewrite: the entries of valid rows still alive in the child's
-// bitmap, as candidate-local indices (bitmap rank), rows renumbered by
-// newrow; each kept row's new offset comes from the compaction's rank.
-struct WriteAliveF {
-    using value_type = uint32_t;
-    const int64_t* off;
-    const int64_t* nrows;
-    const int32_t* list;
-    const uint32_t* alive;
-    const uint32_t* rank;
-    const uint8_t* valid;
-    const int64_t* newrow;
-    int64_t* new_off;
-    int64_t rows;
-    int64_t row;
-    int64_t e_end;
-    __device__ void begin(int64_t i0) {
-        rows = *nrows;
-        e_end = off[rows];
-        if (i0 < e_end) row = row_of(off, rows, i0);
-    }
-    __device__ bool eval(int64_t i, uint32_t& v) {
-        v = 0;
-        if (i >= e_end) return false;
-        while (i >= off[row + 1]) row++;
-        if (!valid[row]) return false;
-        int32_t x = list[i];
-        uint32_t wd = alive[x >> 5], bit = 1u << (x & 31);
-        v = rank[x >> 5] + __popc(wd & (bit - 1));
-        return (wd & bit) != 0;
-    }
-    __device__ int64_t tag(int64_t i) const { return (i < e_end && i == off[row] && valid[row]) ? row : -1; }
-    __device__ void at(int64_t r, int64_t rk) const { new_off[newrow[r]] = rk; }
-    __device__ int64_t end() const { return off[*nrows]; }
-};
-
-__device__ __forceinline__ uint64_t warp_sat_sum(uint64_t v) {
-    for (int o = 16; o > 0; o >>= 1) v = sat_add(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-__device__ __forceinline__ double warp_sum_f(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 // Workload, first half (Sec. IV-C): per row r of C(u) and one child c, the
@@ -438,13 +213,6 @@ __global__ void __launch_bounds__(256) k_child_sums(const int64_t* __restrict__ 
         flush();
     }
 }
-
-struct ChildSums {
-    uint64_t* ssum[kMaxK];
-    const double* sumf[kMaxK];
-    const uint32_t* ovf[kMaxK];
-    int nch;
-};
 
 // Workload, second half: c_u(v) = product over children of those sums
 // (saturating), and the float64 twin; the saturated sums are kept for the
@@ -500,7 +268,6 @@ inline unsigned grid_for(int64_t n, int threads) {
     return (unsigned)(b < 1 ? 1 : (b > 0x7FFFFFFF ? 0x7FFFFFFF : b));
 }
 
-
 // ----------------------------------------------------------------- build
 
 struct Bits {
@@ -514,62 +281,7 @@ void cst_release(fast_cst* c) {
     delete c;
 }
 
-int validate_query(const fast_query_desc* q, int A[kMaxK][kMaxK], int* dq) {
-    if (!q) return set_error(FAST_ERR_INVALID, "query is NULL");
-    int k = q->n;
-    if (k < 1 || k > kMaxK) return set_error(FAST_ERR_INVALID, "query has %d vertices (1..%d)", k, kMaxK);
-    if (!q->labels || (q->m > 0 && !q->edges) || q->m < 0) return set_error(FAST_ERR_INVALID, "query arrays are NULL");
-    memset(A, 0, sizeof(int) * kMaxK * kMaxK);
-    for (int u = 0; u < k; u++) {
-        dq[u] = 0;
-        if (q->labels[u] < 0) return set_error(FAST_ERR_INVALID, "query label < 0");
-    }
-    for (int e = 0; e < q->m; e++) {
-        int a = q->edges[2 * e], b = q->edges[2 * e + 1];
-        if (a < 0 || b < 0 || a >= k || b >= k) return set_error(FAST_ERR_INVALID, "query edge (%d,%d) out of range", a, b);
-        if (a == b) return set_error(FAST_ERR_INVALID, "query edge (%d,%d) is a loop", a, b);
-        if (!A[a][b]) { A[a][b] = A[b][a] = 1; dq[a]++; dq[b]++; }
-    }
-    // connected?
-    int seen[kMaxK] = {0}, st[kMaxK], sp = 0, cnt = 1;
-    st[sp++] = 0; seen[0] = 1;
-    while (sp) {
-        int u = st[--sp];
-        for (int w = 0; w < k; w++) if (A[u][w] && !seen[w]) { seen[w] = 1; st[sp++] = w; cnt++; }
-    }
-    if (cnt != k) return set_error(FAST_ERR_INVALID, "query graph is disconnected");
-    return FAST_OK;
-}
-
 // ------------------------------------------------ exact-size CST storage
-
-// One flat copy list: descriptor d moves bytes [0, n_d) from src_d to dst_d;
-// piece_off[d] is the first 64 KB piece of d in a flat piece space.
-struct CopyDesc {
-    const unsigned char* src;
-    unsigned char* dst;
-    uint64_t bytes;
-    uint64_t piece_off;
-};
-constexpr uint64_t kPiece = 64 << 10;
-
-__global__ void k_copy_many(const CopyDesc* __restrict__ d, int nd, uint64_t npieces) {
-    for (uint64_t p = blockIdx.x; p < npieces; p += gridDim.x) {
-        int lo = 0, hi = nd;                                  // last d with piece_off <= p
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (d[mid].piece_off <= p) lo = mid; else hi = mid;
-        }
-        const CopyDesc& c = d[lo];
-        uint64_t a = (p - c.piece_off) * kPiece, b = a + kPiece < c.bytes ? a + kPiece : c.bytes;
-        // both ends are 256-byte aligned and a is a multiple of kPiece: 16-byte words, then a byte tail
-        uint64_t a16 = a / 16, b16 = b / 16;
-        const uint4* s4 = (const uint4*)c.src;
-        uint4* d4 = (uint4*)c.dst;
-        for (uint64_t i = a16 + threadIdx.x; i < b16; i += blockDim.x) d4[i] = s4[i];
-        for (uint64_t i = b16 * 16 + threadIdx.x; i < b; i += blockDim.x) c.dst[i] = c.src[i];
-    }
-}
 
 // After the last round trip every size is known: copy the CST's arrays into
 // one exact-size block of its arena with one kernel.  The build buffers stay
