@@ -182,6 +182,22 @@ int fast_build_cst(const fast_graph* g, const fast_query_desc* q, const fast_con
                    fast_cst** out);
 
 /*
+ * The CSTs of nq queries built together (Sec. IV-A, Algorithm 1, and the
+ * workload estimate of Sec. IV-C, as fast_build_cst): the steps go over BFS
+ * positions, and each step is one launch for the vertex at that position of
+ * every query, with one or two host round trips per position for the whole
+ * batch instead of a few per query.  outs[i] receives query i's CST, which
+ * is the same, array for array, as fast_build_cst gives; the caller frees
+ * each with fast_free_cst.  status[i] is FAST_OK, or FAST_ERR_INVALID for a
+ * bad query (outs[i] is then NULL).  Queries are built in groups of up to
+ * 1024.  qs, outs and status are host arrays of nq entries.
+ * Returns FAST_ERR_INVALID for bad arguments, FAST_ERR_OOM or FAST_ERR_CUDA
+ * when a group fails (every outs[i] is then NULL), else FAST_OK.
+ */
+int fast_build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, const fast_config* cfg,
+                         void* stream, fast_cst** outs, int32_t* status);
+
+/*
  * Shape of a CST: k = |V(q)|; root; order[k] (position -> query vertex);
  * parent[k] (query vertex -> parent in t_q, -1 for the root); cand[k]
  * (query vertex -> |C(u)|); W as saturating uint64 and float64.  Any output

@@ -63,6 +63,7 @@ _SIGS = {
     "fast_graph_copy_csr": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "fast_free_graph": (None, [_vp]),
     "fast_build_cst": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fast_build_cst_batch": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
     "fast_cst_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fast_cst_candidates": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
     "fast_cst_tree_size": (ctypes.c_int, [_vp, _i32, _vp]),
@@ -229,6 +230,22 @@ class Cst:
         _check(lib().fast_build_cst(graph.handle, ctypes.byref(q), ctypes.byref(cfg) if cfg else None,
                                     self.stream, ctypes.byref(h)))
         self._h = h
+        self._load_info()
+
+    @classmethod
+    def _adopt(cls, graph: Graph, ql, qe, h, stream):
+        """Wraps a CST handle that the library built (fast_build_cst_batch)."""
+        self = cls.__new__(cls)
+        self.graph = graph
+        self.k = int(ql.shape[0])
+        self._ql, self._qe = ql, qe
+        self.stream = stream
+        self._h = h
+        self._load_info()
+        return self
+
+    def _load_info(self):
+        h = self._h
         k = self.k
         kk, root = _i32(), _i32()
         order = np.empty(k, np.int32); parent = np.empty(k, np.int32); cand = np.empty(k, np.int64)
@@ -356,6 +373,25 @@ def _query_descs(queries):
         arr[i] = QueryDesc(ql.shape[0], qe.shape[0], ql.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                            qe.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     return arr, keep
+
+
+def build_csts(graph: Graph, queries, cfg: Config | None = None, stream=None):
+    """CSTs of many queries built together (fast_build_cst_batch): a list with
+    a Cst per query (None where the query is invalid) and the status array."""
+    arr, keep = _query_descs(queries)
+    nq = len(queries)
+    outs = (_vp * max(nq, 1))()
+    status = np.zeros(max(nq, 1), np.int32)
+    st = stream if stream is not None else default_stream()
+    _check(lib().fast_build_cst_batch(graph.handle, nq, arr, ctypes.byref(cfg) if cfg else None, st, outs,
+                                      _p(status)))
+    csts = []
+    for i in range(nq):
+        if status[i] != 0 or not outs[i]:
+            csts.append(None)
+            continue
+        csts.append(Cst._adopt(graph, keep[2 * i], keep[2 * i + 1], _vp(outs[i]), st))
+    return csts, status[:nq]
 
 
 class Batch:

@@ -128,4 +128,9 @@ namespace fast {
 // calls, for callers whose streams are already idle or stay ordered.
 void cst_release_nosync(fast_cst* c);
 void chunks_release_nosync(fast_chunks* ch);
+
+// The CSTs of nq queries built together (cst_batch.cu), query i with
+// cfgs[i] (NULL: defaults); outs[i] and status[i] as fast_build_cst_batch.
+int build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, const fast_config* const* cfgs,
+                    cudaStream_t s, fast_cst** outs, int32_t* status);
 }  // namespace fast

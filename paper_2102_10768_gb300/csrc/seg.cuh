@@ -1,0 +1,265 @@
+// Segmented twins of the single-pass ordered compaction and exclusive scan
+// (prims.cuh): many independent index spaces ("segments": one per query of a
+// batch, or per query edge) in one launch.
+//
+// The tiles of all segments form one global tile sequence: segment s owns
+// tiles tile_off[s] .. tile_off[s+1]-1 (at least one, so that an empty
+// segment still reports a zero count).  Blocks of a persistent grid take
+// tiles in that order from one counter.  A tile publishes its aggregate and
+// looks back over the earlier tiles of its own segment only, stopping at the
+// segment's first tile; every tile it waits on was taken before it by a
+// block that is already running, so the wait ends.  It is still bounded by
+// the same spin limit as the single-segment form, and running out sets the
+// translation unit's look-back error flag.
+#pragma once
+
+#include <vector>
+
+#include "prims.cuh"
+
+namespace fast {
+
+// last s with tile_off[s] <= t (the segment owning tile t; the empty
+// segments before it share its offset)
+__device__ __forceinline__ int seg_of_tile(const int64_t* __restrict__ tile_off, int nseg, int64_t t) {
+    int lo = 0, hi = nseg;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (tile_off[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Host side: tile_off[0..nseg] for segments of n_s indices, tiles of `tile`
+// indices, at least one tile per segment.
+inline std::vector<int64_t> seg_tile_offsets(const std::vector<int64_t>& n, int64_t tile) {
+    std::vector<int64_t> off(n.size() + 1, 0);
+    for (size_t i = 0; i < n.size(); i++) off[i + 1] = off[i] + std::max<int64_t>(1, ceil_div(n[i], tile));
+    return off;
+}
+
+// One scratch block holding, in order: the descriptors, the tile offsets,
+// the tile status words and the tile counter.  Uploads the first two with
+// one copy and zeroes the rest with one memset.
+struct SegBlock {
+    unsigned char* base = nullptr;
+    size_t desc_bytes = 0, off_at = 0, st_at = 0, bytes = 0;
+    int64_t tiles = 0;
+};
+
+template <class D>
+int seg_block_upload(const std::vector<D>& desc, const std::vector<int64_t>& tile_off, SegBlock* b, cudaStream_t s) {
+    const size_t nd = desc.size();
+    b->tiles = tile_off.back();
+    b->desc_bytes = nd * sizeof(D);
+    b->off_at = (b->desc_bytes + 15) / 16 * 16;
+    b->st_at = (b->off_at + tile_off.size() * sizeof(int64_t) + 15) / 16 * 16;
+    b->bytes = b->st_at + (size_t)(b->tiles + 1) * sizeof(unsigned long long);
+    FAST_TRY(dalloc(&b->base, b->bytes, s));
+    std::vector<unsigned char> h(b->st_at, 0);
+    memcpy(h.data(), desc.data(), b->desc_bytes);
+    memcpy(h.data() + b->off_at, tile_off.data(), tile_off.size() * sizeof(int64_t));
+    FAST_CUDA(cudaMemcpyAsync(b->base, h.data(), b->st_at, cudaMemcpyHostToDevice, s));
+    FAST_CUDA(cudaMemsetAsync(b->base + b->st_at, 0, b->bytes - b->st_at, s));
+    return FAST_OK;
+}
+
+// ------------------------------------------------------------- compaction
+
+template <class F>
+struct CompactSeg {
+    F f;
+    int64_t n;                                // index space [0, n) (a bound when F has end())
+    typename F::value_type* out;
+    int64_t* count;                           // device, nullable: kept indices
+};
+
+template <class F>
+__global__ void __launch_bounds__(kCompBlock) k_compact_seg(const CompactSeg<F>* __restrict__ segs,
+                                                            const int64_t* __restrict__ tile_off, int nseg,
+                                                            unsigned long long* __restrict__ st,
+                                                            unsigned int* __restrict__ tile_ctr) {
+    __shared__ int64_t tmp[kCompBlock / 32 + 1];
+    __shared__ int64_t s_t, s_excl, s_end, s_first;
+    __shared__ int s_seg;
+    const int64_t total = tile_off[nseg];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int64_t t = (int64_t)atomicAdd(tile_ctr, 1u);
+            s_t = t;
+            if (t < total) {
+                const int sg = seg_of_tile(tile_off, nseg, t);
+                s_seg = sg;
+                s_first = tile_off[sg];
+                s_end = index_end(segs[sg].f, segs[sg].n);
+            }
+        }
+        __syncthreads();
+        const int64_t t = s_t;
+        if (t >= total) break;
+        const CompactSeg<F>& sd = segs[s_seg];
+        const int64_t lt = t - s_first, end = s_end;
+        const int64_t tb = lt * kCompTile;
+        if (tb >= end) {                                   // past the segment's real end
+            if (lt == 0 && threadIdx.x == 0 && sd.count) *sd.count = 0;
+            __syncthreads();
+            continue;
+        }
+        const int64_t base = tb + (int64_t)threadIdx.x * kCompItems;
+        int64_t v[kCompItems];
+        typename F::value_type val[kCompItems];
+        int64_t tg[kCompItems];
+        F g = sd.f;
+        g.begin(base);
+#pragma unroll
+        for (int i = 0; i < kCompItems; i++) {
+            v[i] = (base + i < end && g.eval(base + i, val[i])) ? 1 : 0;
+            tg[i] = (base + i < end) ? g.tag(base + i) : -1;
+        }
+        int64_t hit[kCompItems];
+#pragma unroll
+        for (int i = 0; i < kCompItems; i++) hit[i] = v[i];
+        const int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kCompItems>(v, tmp);
+        if (threadIdx.x == 0) {
+            unsigned long long* sst = st + s_first;
+            int64_t excl = 0;
+            if (lt == 0) {
+                atomicExch(sst, kLbPre | (unsigned long long)tot);
+            } else {
+                atomicExch(sst + lt, kLbAgg | (unsigned long long)tot);
+                excl = lookback_prefix(sst, lt);
+                atomicExch(sst + lt, kLbPre | (unsigned long long)(excl + tot));
+            }
+            s_excl = excl;
+            if (tb + kCompTile >= end && sd.count) *sd.count = excl + tot;
+        }
+        __syncthreads();
+        const int64_t off = s_excl;
+        typename F::value_type* out = sd.out;
+#pragma unroll
+        for (int i = 0; i < kCompItems; i++) {
+            if (tg[i] >= 0) g.at(tg[i], off + v[i]);
+            if (hit[i]) out[off + v[i]] = val[i];
+        }
+        __syncthreads();
+    }
+}
+
+// All segments in one launch; each segment's kept count goes to its
+// `count` (device).
+template <class F>
+int compact_seg(const std::vector<CompactSeg<F>>& segs, cudaStream_t s) {
+    if (segs.empty()) return FAST_OK;
+    std::vector<int64_t> n(segs.size());
+    for (size_t i = 0; i < segs.size(); i++) n[i] = segs[i].n;
+    const std::vector<int64_t> toff = seg_tile_offsets(n, kCompTile);
+    SegBlock b;
+    int rc = seg_block_upload(segs, toff, &b, s);
+    if (rc == FAST_OK) {
+        const int64_t grid = std::min<int64_t>(b.tiles, (int64_t)num_sms() * 4);
+        k_compact_seg<F><<<(unsigned)grid, kCompBlock, 0, s>>>(
+            (const CompactSeg<F>*)b.base, (const int64_t*)(b.base + b.off_at), (int)segs.size(),
+            (unsigned long long*)(b.base + b.st_at), (unsigned int*)(b.base + b.st_at + b.tiles * sizeof(unsigned long long)));
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "segmented compaction launch");
+    }
+    dfree(b.base, s);
+    return rc;
+}
+
+// ------------------------------------------------------------------- scan
+
+// out[i] = in[0] + ... + in[i-1] over [0, n); *total (nullable) = the sum.
+// With `bits` set, in[i] = popcount(bits[i]) (the rank of a bitmap's words).
+// in and out may alias.
+template <class T>
+struct ScanSeg {
+    const T* in;
+    const uint32_t* bits;
+    T* out;
+    int64_t n;
+    T* total;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kScanBlock) k_scan_seg(const ScanSeg<T>* __restrict__ segs,
+                                                         const int64_t* __restrict__ tile_off, int nseg,
+                                                         unsigned long long* __restrict__ st,
+                                                         unsigned int* __restrict__ tile_ctr) {
+    __shared__ T tmp[kScanBlock / 32 + 1];
+    __shared__ int64_t s_t, s_excl, s_first;
+    __shared__ int s_seg;
+    const int64_t total = tile_off[nseg];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int64_t t = (int64_t)atomicAdd(tile_ctr, 1u);
+            s_t = t;
+            if (t < total) {
+                const int sg = seg_of_tile(tile_off, nseg, t);
+                s_seg = sg;
+                s_first = tile_off[sg];
+            }
+        }
+        __syncthreads();
+        const int64_t t = s_t;
+        if (t >= total) break;
+        const ScanSeg<T>& sd = segs[s_seg];
+        const int64_t lt = t - s_first, n = sd.n;
+        const int64_t tb = lt * kScanTile;
+        if (tb >= n) {                                     // empty segment
+            if (lt == 0 && threadIdx.x == 0 && sd.total) *sd.total = T(0);
+            __syncthreads();
+            continue;
+        }
+        const int64_t base = tb + (int64_t)threadIdx.x * kScanItems;
+        T v[kScanItems];
+#pragma unroll
+        for (int i = 0; i < kScanItems; i++) {
+            const int64_t x = base + i;
+            v[i] = x < n ? (sd.bits ? (T)__popc(sd.bits[x]) : sd.in[x]) : T(0);
+        }
+        const T tot = block_exclusive_scan<T, kScanBlock, kScanItems>(v, tmp);
+        if (threadIdx.x == 0) {
+            unsigned long long* sst = st + s_first;
+            int64_t excl = 0;
+            if (lt == 0) {
+                atomicExch(sst, kLbPre | (unsigned long long)tot);
+            } else {
+                atomicExch(sst + lt, kLbAgg | (unsigned long long)tot);
+                excl = lookback_prefix(sst, lt);
+                atomicExch(sst + lt, kLbPre | (unsigned long long)(excl + (int64_t)tot));
+            }
+            s_excl = excl;
+            if (tb + kScanTile >= n && sd.total) *sd.total = (T)(excl + (int64_t)tot);
+        }
+        __syncthreads();
+        const T off = (T)s_excl;
+        T* out = sd.out;
+#pragma unroll
+        for (int i = 0; i < kScanItems; i++)
+            if (base + i < n) out[base + i] = v[i] + off;
+        __syncthreads();
+    }
+}
+
+template <class T>
+int scan_seg(const std::vector<ScanSeg<T>>& segs, cudaStream_t s) {
+    if (segs.empty()) return FAST_OK;
+    std::vector<int64_t> n(segs.size());
+    for (size_t i = 0; i < segs.size(); i++) n[i] = segs[i].n;
+    const std::vector<int64_t> toff = seg_tile_offsets(n, kScanTile);
+    SegBlock b;
+    int rc = seg_block_upload(segs, toff, &b, s);
+    if (rc == FAST_OK) {
+        const int64_t grid = std::min<int64_t>(b.tiles, (int64_t)num_sms() * 2);
+        k_scan_seg<T><<<(unsigned)grid, kScanBlock, 0, s>>>(
+            (const ScanSeg<T>*)b.base, (const int64_t*)(b.base + b.off_at), (int)segs.size(),
+            (unsigned long long*)(b.base + b.st_at), (unsigned int*)(b.base + b.st_at + b.tiles * sizeof(unsigned long long)));
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "segmented scan launch");
+    }
+    dfree(b.base, s);
+    return rc;
+}
+
+}  // namespace fast

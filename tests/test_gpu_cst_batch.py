@@ -1,0 +1,169 @@
+"""The batched CST build (fast_build_cst_batch) against the oracle and
+against the per-query build.
+
+Every CST of a batch must equal the oracle's restatement of Alg. 1 and the
+workload estimate (root, t_q, order, candidate sets, tree and non-tree
+lists, c_u and W), in both matching orders and under both candidate
+filters, and must give the same embedding counts.  Batches mix query sizes
+1 to 16, invalid queries (reported per query), labels absent from G, and
+more queries than one group holds.
+
+Opt-in (FAST_CST_BATCH=1) until these tests have run on the hardware.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2102_10768_gb300 as F
+import synth
+from helpers import compare_cst
+
+pytestmark = [
+    pytest.mark.gpu,
+    pytest.mark.skipif(not os.environ.get("FAST_CST_BATCH"), reason="batched CST build: set FAST_CST_BATCH=1"),
+]
+
+RULES = [dict(), dict(order_rule=1), dict(filter_rule=1), dict(order_rule=1, filter_rule=1)]
+
+
+def _oracle_kw(rule):
+    kw = {}
+    if rule.get("order_rule") == 1:
+        kw["order"] = "greedy"
+    if rule.get("filter_rule") == 1:
+        kw["filter"] = "nlf"
+    return kw
+
+
+def rand_graph(seed, n_lo=40, n_hi=220, L_hi=4):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(n_lo, n_hi))
+    L = int(rng.integers(1, L_hi + 1))
+    p = float(rng.uniform(0.03, 0.2))
+    edges = np.array([(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p], np.int32).reshape(-1, 2)
+    labels = rng.integers(0, L, size=n).astype(np.int32)
+    return rng, n, edges, labels, L
+
+
+def rand_query(rng, L, k):
+    qe = set()
+    for v in range(1, k):
+        qe.add((int(rng.integers(0, v)), v))
+    dens = float(rng.uniform(0, 0.5))
+    for a in range(k):
+        for b in range(a + 1, k):
+            if rng.random() < dens:
+                qe.add((a, b))
+    ql = rng.integers(0, L, size=k).astype(np.int32)
+    return ql, np.array(sorted(qe), np.int32).reshape(-1, 2)
+
+
+def check_batch(g, o, qs, rule, bad=()):
+    cfg = F.default_config(**rule)
+    csts, status = F.build_csts(g, qs, cfg)
+    assert len(csts) == len(qs)
+    for i, ((ql, qe), c) in enumerate(zip(qs, csts)):
+        if i in bad:
+            assert status[i] == F.FAST_ERR_INVALID and c is None, i
+            continue
+        assert status[i] == 0 and c is not None, (i, status[i])
+        compare_cst(c, oracle.Cst(o, ql, qe, **_oracle_kw(rule)), len(ql))
+        assert F.match(c)["count"] == oracle.count(o, ql, qe)
+        c.close()
+
+
+@pytest.mark.parametrize("rule", range(len(RULES)))
+@pytest.mark.parametrize("seed", range(12))
+def test_batch_random_graphs(seed, rule):
+    rng, n, e, lab, L = rand_graph(7000 + seed)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    qs = [rand_query(rng, L, int(rng.integers(1, 8))) for _ in range(10)]
+    qs.append((np.array([L + 5, 0], np.int32), np.array([[0, 1]], np.int32)))    # a label G lacks
+    qs.append((np.array([0], np.int32), np.zeros((0, 2), np.int32)))             # k = 1
+    bad = {len(qs), len(qs) + 1}
+    qs.append((np.array([0, 1, 0], np.int32), np.array([[0, 1]], np.int32)))     # disconnected
+    qs.append((np.array([0, 1], np.int32), np.array([[0, 5]], np.int32)))        # edge out of range
+    check_batch(g, o, qs, RULES[rule], bad)
+
+
+@pytest.mark.parametrize("rule", range(len(RULES)))
+def test_batch_er_workload(rule):
+    w = synth.er_workload()
+    g, o = F.Graph(w.n, w.edges, w.labels), oracle.Graph(w.n, w.edges, w.labels)
+    wg = synth.WalkGraph(w.n, w.edges)
+    qs = [(q.labels, q.edges) for q in w.queries]
+    for i, k in enumerate((3, 5, 6, 7, 8)):
+        q = wg.query(w.labels, k, "sparse" if i % 2 else "induced", seed=31, stream=i)
+        qs.append((q.labels, q.edges))
+    check_batch(g, o, qs, RULES[rule])
+
+
+def _same_cst(a, b):
+    """Two CSTs of the same query from the library: equal arrays (W's
+    float64 twin within rounding, its sums being atomics)."""
+    assert a.root == b.root and a.order.tolist() == b.order.tolist() and a.parent.tolist() == b.parent.tolist()
+    assert a.ncand.tolist() == b.ncand.tolist() and a.W == b.W
+    assert abs(a.Wf - b.Wf) <= 1e-9 * max(1.0, abs(b.Wf))
+    for u in range(a.k):
+        assert np.array_equal(a.candidates(u), b.candidates(u))
+        assert np.array_equal(a.workload(u), b.workload(u))
+        if a.parent[u] >= 0:
+            for x, y in zip(a.tree_lists(u), b.tree_lists(u)):
+                assert np.array_equal(x, y)
+    na, nb = a.nontree(), b.nontree()
+    assert len(na) == len(nb)
+    for x, y in zip(na, nb):
+        assert x[:2] == y[:2] and np.array_equal(x[2], y[2]) and np.array_equal(x[3], y[3])
+
+
+def test_batch_powerlaw_equals_per_query():
+    n, e, lab = synth.powerlaw_graph(seed=2000, n=50_000, m=600_000)
+    g = F.Graph(n, e, lab)
+    wg = synth.WalkGraph(n, e)
+    qs = []
+    for k in (4, 8, 12, 16):
+        for j, kind in enumerate(("induced", "sparse") if k == 4 else ("dense", "sparse")):
+            for r in range(5):
+                q = wg.query(lab, k, kind, seed=77, stream=100 * k + 10 * j + r)
+                qs.append((q.labels, q.edges))
+    for rule in RULES:
+        cfg = F.default_config(**rule)
+        csts, status = F.build_csts(g, qs, cfg)
+        assert status.tolist() == [0] * len(qs)
+        for (ql, qe), c in zip(qs, csts):
+            one = F.Cst(g, ql, qe, cfg)
+            _same_cst(c, one)
+            lim = F.default_config(limit=1 << 16, **rule)
+            assert F.match(c, cfg=lim)["count"] == F.match(one, cfg=lim)["count"]
+            one.close()
+            c.close()
+
+
+def test_batch_more_than_one_group():
+    w = synth.er_workload()
+    g, o = F.Graph(w.n, w.edges, w.labels), oracle.Graph(w.n, w.edges, w.labels)
+    wg = synth.WalkGraph(w.n, w.edges)
+    qs = []
+    for i in range(1100):
+        q = wg.query(w.labels, 2 + i % 5, "sparse" if i % 2 else "induced", seed=41, stream=i)
+        qs.append((q.labels, q.edges))
+    csts, status = F.build_csts(g, qs)
+    assert status.tolist() == [0] * len(qs)
+    for i in list(range(0, 1100, 97)) + [1023, 1024, 1099]:
+        ql, qe = qs[i]
+        compare_cst(csts[i], oracle.Cst(o, ql, qe), len(ql))
+    for i, c in enumerate(csts):
+        ql, qe = qs[i]
+        assert c.W == oracle.Cst(o, ql, qe).workload()[1]
+        c.close()
+
+
+def test_batch_empty_and_all_invalid():
+    w = synth.er_workload()
+    g = F.Graph(w.n, w.edges, w.labels)
+    csts, status = F.build_csts(g, [])
+    assert csts == [] and status.size == 0
+    csts, status = F.build_csts(g, [(np.array([0, 1, 2], np.int32), np.array([[0, 1]], np.int32))])
+    assert csts == [None] and status.tolist() == [F.FAST_ERR_INVALID]
