@@ -62,6 +62,9 @@ def parse():
     p.add_argument("--order", choices=["path", "greedy"], default="greedy",
                    help="matching order: the greedy rule (default) or the paper's path-based order "
                         "(also reported beside the headline as path_order)")
+    p.add_argument("--build", choices=["threads", "batched"], default="threads",
+                   help="how the batched step builds its CSTs: per query on the host threads (default) or all "
+                        "queries together (fast_build_cst_batch)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     return p.parse_args()
 
@@ -293,6 +296,7 @@ def run_ours(args):
     # graph-replayed persistent matcher launch for every chunk of every query
     bcfg = F.Config.from_buffer_copy(cfg)
     bcfg.time_budget_s = args.batch_budget
+    bcfg.build_rule = 1 if args.build == "batched" else 0
     bt = F.Batch(g, len(bq), bcfg, threads=args.threads)
     tuned = None
     if args.autotune:
@@ -459,7 +463,7 @@ def run_ours(args):
         "config": {"workload": desc, "queries_per_step": len(qs),
                    "mode": f"batched: fast_batch_run, {args.threads} build threads, one graph-replayed matcher "
                            f"launch per step (budget {args.batch_budget} s)",
-                   "order": args.order, "filter": args.filter, "autotuned": tuned,
+                   "order": args.order, "filter": args.filter, "cst_build": args.build, "autotuned": tuned,
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}, queries per rank"},
         "queries_per_sec": len(qs) * steps * world / t_s,
         "embeddings_per_step": tot_emb / steps,

@@ -115,6 +115,11 @@ typedef struct {
      * also neighbour label frequencies: for every label, v has at least as
      * many neighbours with it as u has (smaller CSTs; the same embeddings). */
     int32_t filter_rule;
+    /* How fast_batch_run and fast_match_batch build the CSTs of a batch.
+     * 0: each query's fast_build_cst on a pool of host threads.  1: all of
+     * them together with fast_build_cst_batch.  The CSTs, and so every
+     * result, are the same either way. */
+    int32_t build_rule;
 } fast_config;
 
 /* Default tunables: delta_w = 2^20, no sampling, max_chunks = 2^16,

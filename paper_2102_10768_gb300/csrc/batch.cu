@@ -211,9 +211,26 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
     if (nq > 0 && (!qs || !counts || !status)) return set_error(FAST_ERR_INVALID, "fast_batch_run: NULL array");
     std::vector<fast_cst*> csts(nq, nullptr);
     std::vector<fast_chunks*> chs(nq, nullptr);
-    std::vector<int> st(nq, FAST_OK);
+    std::vector<int32_t> st(nq, FAST_OK);
     auto t0 = std::chrono::steady_clock::now();
-    // ---- 1. CSTs and partitions, concurrently
+    // ---- 1. CSTs and partitions, concurrently (build_rule 1: the CSTs of
+    //         all queries together first, then the partitions)
+    const bool together = b->base.build_rule == 1;
+    if (together && nq > 0) {
+        std::vector<const fast_config*> cf(nq);
+        for (int i = 0; i < nq; i++) cf[i] = &b->cls[size_class(qs[i].n)];
+        int rc = FAST_OK;
+        {
+            PoolScope scratch(b->ws[0], b->pools[0]);
+            rc = build_cst_batch(b->g, nq, qs, cf.data(), b->ws[0], csts.data(), st.data());
+        }
+        if (rc == FAST_OK && cudaStreamSynchronize(b->ws[0]) != cudaSuccess)
+            rc = set_error(FAST_ERR_CUDA, "fast_batch_run: batched CST build");
+        if (rc != FAST_OK) {
+            for (int i = 0; i < nq; i++) cst_release_nosync(csts[i]);
+            return rc;
+        }
+    }
     {
         std::atomic<int> next{0};
         int T = std::min<int>(b->nthreads, std::max(nq, 1));
@@ -226,7 +243,7 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
                     int i = next.fetch_add(1);
                     if (i >= nq) break;
                     const fast_config& cc = b->cls[size_class(qs[i].n)];
-                    int rc = fast_build_cst(b->g, &qs[i], &cc, b->ws[w], &csts[i]);
+                    int rc = together ? st[i] : fast_build_cst(b->g, &qs[i], &cc, b->ws[w], &csts[i]);
                     if (rc == FAST_OK) rc = fast_partition(csts[i], &cc, b->ws[w], &chs[i]);
                     st[i] = rc;
                 }

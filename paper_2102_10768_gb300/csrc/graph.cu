@@ -62,6 +62,7 @@ extern "C" void fast_config_default(fast_config* cfg) {
     cfg->queue_cells = 0;
     cfg->order_rule = 0;
     cfg->filter_rule = 0;
+    cfg->build_rule = 0;
 }
 
 namespace {

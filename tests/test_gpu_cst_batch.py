@@ -167,3 +167,26 @@ def test_batch_empty_and_all_invalid():
     assert csts == [] and status.size == 0
     csts, status = F.build_csts(g, [(np.array([0, 1, 2], np.int32), np.array([[0, 1]], np.int32))])
     assert csts == [None] and status.tolist() == [F.FAST_ERR_INVALID]
+
+
+def test_batch_run_with_the_batched_build():
+    """fast_batch_run with build_rule 1 gives the counts and statuses of the
+    per-query build, invalid queries included."""
+    n, e, lab = synth.powerlaw_graph(seed=2000, n=50_000, m=600_000)
+    g = F.Graph(n, e, lab)
+    wg = synth.WalkGraph(n, e)
+    qs = []
+    for k in (4, 8, 16):
+        for j, kind in enumerate(("induced", "sparse") if k == 4 else ("dense", "sparse")):
+            for r in range(8):
+                q = wg.query(lab, k, kind, seed=91, stream=100 * k + 10 * j + r)
+                qs.append((q.labels, q.edges))
+    qs.insert(5, (np.array([0, 1, 0], np.int32), np.array([[0, 1]], np.int32)))      # disconnected
+    for rule in RULES:
+        base = F.default_config(limit=1 << 16, time_budget_s=60.0, **rule)
+        c0, s0 = F.Batch(g, len(qs), base).run(qs)
+        one = F.Config.from_buffer_copy(base)
+        one.build_rule = 1
+        c1, s1 = F.Batch(g, len(qs), one).run(qs)
+        assert s1.tolist() == s0.tolist() and c1.tolist() == c0.tolist(), rule
+        assert s0[5] == F.FAST_ERR_INVALID
