@@ -38,6 +38,7 @@ class FastError(RuntimeError):
 
 
 class Config(ctypes.Structure):
+    __slots__ = ()              # a misspelled field raises instead of being ignored
     _fields_ = [("delta_w", ctypes.c_uint64), ("sample_root", ctypes.c_double),
                 ("sample_deep", ctypes.c_double), ("sample_seed", ctypes.c_uint64),
                 ("max_chunks", ctypes.c_int64), ("warps_per_block", ctypes.c_int32),
@@ -157,9 +158,13 @@ def default_stream():
 
 
 def default_config(**kw) -> Config:
+    """fast_config_default, then the given fields (unknown names raise)."""
     c = Config()
     lib().fast_config_default(ctypes.byref(c))
+    fields = {f[0] for f in Config._fields_}
     for k, v in kw.items():
+        if k not in fields:
+            raise TypeError(f"fast_config has no field {k!r}")
         setattr(c, k, v)
     return c
 

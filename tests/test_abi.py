@@ -43,3 +43,13 @@ def test_config_default_without_gpu():
     c_size = next(i for i in range(256) if buf[i] == 0xAB)
     assert c_size == ctypes.sizeof(F.Config) == 88
     assert F.lib().fast_last_error() == b""
+
+
+def test_config_rejects_unknown_fields():
+    import pytest
+    with pytest.raises(TypeError):
+        F.default_config(fiter_rule=1)
+    c = F.default_config(filter_rule=1, build_rule=1)
+    assert c.build_rule == 1
+    with pytest.raises(AttributeError):
+        c.bulid_rule = 1
