@@ -256,7 +256,9 @@ void fast_free_cst(fast_cst* c);
  */
 int fast_partition(const fast_cst* c, const fast_config* cfg, void* stream, fast_chunks** out);
 
-/* Number of chunks, and their summed workload estimate (saturating). */
+/* Number of chunks, and their summed workload estimate (saturating; summed
+ * on request: asking for it reads the descriptors back on the partition's
+ * stream and synchronises it). */
 int fast_chunks_info(const fast_chunks* ch, int64_t* count, uint64_t* w_sum);
 
 /*

@@ -119,7 +119,6 @@ struct fast_chunks {
     const fast_cst* c = nullptr;
     int64_t n = 0;
     Chunk* d = nullptr;        // device [n]
-    uint64_t w_sum = 0;
     cudaStream_t stream = nullptr;
 };
 

@@ -384,16 +384,6 @@ int partition(const fast_cst* c, const fast_config* cfg_in, cudaStream_t s, fast
         }
     }
     for (auto& lv : levels) dfree(lv.first, s);
-    if (rc == FAST_OK) {
-        // summed estimate (host side; chunk counts are modest)
-        std::vector<Chunk> h(total);
-        cudaError_t e = total ? cudaMemcpyAsync(h.data(), ch->d, total * sizeof(Chunk), cudaMemcpyDeviceToHost, s) : cudaSuccess;
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) rc = cuda_status(e, "partition readback", __FILE__, __LINE__);
-        uint64_t ws = 0;
-        for (auto& x : h) ws = sat_add(ws, x.w);
-        if (ch) ch->w_sum = ws;
-    }
     if (rc != FAST_OK) {
         if (ch) { dfree_direct(ch->d, s); delete ch; }
         return rc;
@@ -412,7 +402,17 @@ extern "C" int fast_partition(const fast_cst* c, const fast_config* cfg, void* s
 extern "C" int fast_chunks_info(const fast_chunks* ch, int64_t* count, uint64_t* w_sum) {
     if (!ch) return set_error(FAST_ERR_INVALID, "fast_chunks_info: NULL chunks");
     if (count) *count = ch->n;
-    if (w_sum) *w_sum = ch->w_sum;
+    if (w_sum) {
+        // summed on request from the descriptors (the partition itself
+        // does not read them back)
+        cudaStream_t s = ch->stream;
+        std::vector<Chunk> h(ch->n);
+        if (ch->n) FAST_CUDA(cudaMemcpyAsync(h.data(), ch->d, ch->n * sizeof(Chunk), cudaMemcpyDeviceToHost, s));
+        FAST_CUDA(cudaStreamSynchronize(s));
+        uint64_t ws = 0;
+        for (auto& x : h) ws = sat_add(ws, x.w);
+        *w_sum = ws;
+    }
     return FAST_OK;
 }
 
