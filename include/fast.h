@@ -89,7 +89,7 @@ typedef struct {
     double sample_root;
     double sample_deep;
     uint64_t sample_seed;
-    int64_t max_chunks;      /* fast_partition fails with FAST_ERR_LIMIT beyond this */
+    int64_t max_chunks;      /* chunks of one partition at most: a level that would pass it caps its splits (fast_partition) */
     /* Matcher launch shape: warps per CTA and CTAs per SM (persistent). */
     int32_t warps_per_block;
     int32_t blocks_per_sm;
