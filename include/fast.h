@@ -256,6 +256,22 @@ void fast_free_cst(fast_cst* c);
  */
 int fast_partition(const fast_cst* c, const fast_config* cfg, void* stream, fast_chunks** out);
 
+/*
+ * The partitions of nq CSTs built together (Sec. IV-B, Algorithm 2, as
+ * fast_partition): the pending parts of all CSTs are processed level by
+ * level in one set of launches, with one host round trip per level for the
+ * whole batch (two when some CST's level hits its max_chunks).  outs[i]
+ * receives CST i's chunk list, the same list in the same order as
+ * fast_partition gives with cfg (NULL: each CST's own configuration); free
+ * each with fast_free_chunks.  status[i] is FAST_OK, or FAST_ERR_INVALID for
+ * a NULL CST (outs[i] is then NULL).  csts, outs and status are host arrays
+ * of nq entries.  Returns FAST_ERR_INVALID for bad arguments, FAST_ERR_OOM or
+ * FAST_ERR_CUDA when the batch fails (every outs[i] is then NULL), else
+ * FAST_OK.
+ */
+int fast_partition_batch(const fast_cst* const* csts, int32_t nq, const fast_config* cfg, void* stream,
+                         fast_chunks** outs, int32_t* status);
+
 /* Number of chunks, and their summed workload estimate (saturating; summed
  * on request: asking for it reads the descriptors back on the partition's
  * stream and synchronises it). */

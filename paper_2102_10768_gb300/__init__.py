@@ -65,6 +65,7 @@ _SIGS = {
     "fast_free_graph": (None, [_vp]),
     "fast_build_cst": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "fast_build_cst_batch": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "fast_partition_batch": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "fast_cst_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fast_cst_candidates": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
     "fast_cst_tree_size": (ctypes.c_int, [_vp, _i32, _vp]),
@@ -320,8 +321,21 @@ class Chunks:
         self.stream = stream if stream is not None else cst.stream
         _check(lib().fast_partition(cst.handle, ctypes.byref(cfg) if cfg else None, self.stream, ctypes.byref(h)))
         self._h = h
+        self._load_info()
+
+    @classmethod
+    def _adopt(cls, cst: Cst, h, stream):
+        """Wraps a chunk list that the library built (fast_partition_batch)."""
+        self = cls.__new__(cls)
+        self.cst = cst
+        self.stream = stream
+        self._h = h
+        self._load_info()
+        return self
+
+    def _load_info(self):
         n, ws = _i64(), _u64()
-        _check(lib().fast_chunks_info(h, ctypes.byref(n), ctypes.byref(ws)))
+        _check(lib().fast_chunks_info(self._h, ctypes.byref(n), ctypes.byref(ws)))
         self.n, self.w_sum = n.value, ws.value
 
     @property
@@ -397,6 +411,20 @@ def build_csts(graph: Graph, queries, cfg: Config | None = None, stream=None):
             continue
         csts.append(Cst._adopt(graph, keep[2 * i], keep[2 * i + 1], _vp(outs[i]), st))
     return csts, status[:nq]
+
+
+def partition_many(csts, cfg: Config | None = None, stream=None):
+    """Partitions of many CSTs built together (fast_partition_batch): a list
+    with a Chunks per CST, and the status array."""
+    nq = len(csts)
+    hs = (_vp * max(nq, 1))(*[c.handle if c is not None else None for c in csts])
+    outs = (_vp * max(nq, 1))()
+    status = np.zeros(max(nq, 1), np.int32)
+    first = next((c for c in csts if c is not None), None)
+    st = stream if stream is not None else (first.stream if first is not None else default_stream())
+    _check(lib().fast_partition_batch(hs, nq, ctypes.byref(cfg) if cfg else None, st, outs, _p(status)))
+    chunks = [Chunks._adopt(c, _vp(outs[i]), st) if status[i] == 0 and outs[i] else None for i, c in enumerate(csts)]
+    return chunks, status[:nq]
 
 
 class Batch:

@@ -132,4 +132,10 @@ void chunks_release_nosync(fast_chunks* ch);
 // cfgs[i] (NULL: defaults); outs[i] and status[i] as fast_build_cst_batch.
 int build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, const fast_config* const* cfgs,
                     cudaStream_t s, fast_cst** outs, int32_t* status);
+
+// The partitions of nq CSTs built together (partition_batch.cu), CST i with
+// cfgs[i] (NULL: its own configuration); outs[i] and status[i] as
+// fast_partition_batch.
+int partition_batch(const fast_cst* const* csts, int32_t nq, const fast_config* const* cfgs, cudaStream_t s,
+                    fast_chunks** outs, int32_t* status);
 }  // namespace fast
