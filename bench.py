@@ -62,9 +62,10 @@ def parse():
     p.add_argument("--order", choices=["path", "greedy"], default="greedy",
                    help="matching order: the greedy rule (default) or the paper's path-based order "
                         "(also reported beside the headline as path_order)")
-    p.add_argument("--build", choices=["threads", "batched"], default="threads",
-                   help="how the batched step builds its CSTs: per query on the host threads (default) or all "
-                        "queries together (fast_build_cst_batch)")
+    p.add_argument("--build", choices=["threads", "batched", "batched-all"], default="threads",
+                   help="how the batched step builds its CSTs and partitions: per query on the host threads "
+                        "(default), the CSTs of all queries together (fast_build_cst_batch), or both together "
+                        "(also fast_partition_batch)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
     return p.parse_args()
 
@@ -296,7 +297,7 @@ def run_ours(args):
     # graph-replayed persistent matcher launch for every chunk of every query
     bcfg = F.Config.from_buffer_copy(cfg)
     bcfg.time_budget_s = args.batch_budget
-    bcfg.build_rule = 1 if args.build == "batched" else 0
+    bcfg.build_rule = {"threads": 0, "batched": 1, "batched-all": 2}[args.build]
     bt = F.Batch(g, len(bq), bcfg, threads=args.threads)
     tuned = None
     if args.autotune:

@@ -115,10 +115,13 @@ typedef struct {
      * also neighbour label frequencies: for every label, v has at least as
      * many neighbours with it as u has (smaller CSTs; the same embeddings). */
     int32_t filter_rule;
-    /* How fast_batch_run and fast_match_batch build the CSTs of a batch.
-     * 0: each query's fast_build_cst on a pool of host threads.  1: all of
-     * them together with fast_build_cst_batch.  The CSTs, and so every
-     * result, are the same either way. */
+    /* How fast_batch_run and fast_match_batch build the CSTs and partitions
+     * of a batch.  0: each query's fast_build_cst and fast_partition on a
+     * pool of host threads.  1: the CSTs together (fast_build_cst_batch),
+     * the partitions on the threads.  2: both together (also
+     * fast_partition_batch).  The CSTs and chunk lists, and so every
+     * result, are the same either way; fast_batch_create rejects other
+     * values. */
     int32_t build_rule;
 } fast_config;
 

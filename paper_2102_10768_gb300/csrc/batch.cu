@@ -126,6 +126,8 @@ int batch_create(const fast_graph* g, const fast_config* cfg, int32_t max_q, int
     if (!out) return set_error(FAST_ERR_INVALID, "fast_batch_create: out is NULL");
     *out = nullptr;
     if (!g || max_q < 1) return set_error(FAST_ERR_INVALID, "fast_batch_create: bad graph or max_queries");
+    if (cfg && (cfg->build_rule < 0 || cfg->build_rule > 2))
+        return set_error(FAST_ERR_INVALID, "fast_batch_create: build_rule %d (0, 1 or 2)", cfg->build_rule);
     fast_batch* b = new fast_batch();
     cudaGetDevice(&b->device);
     b->g = g;
@@ -214,8 +216,10 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
     std::vector<int32_t> st(nq, FAST_OK);
     auto t0 = std::chrono::steady_clock::now();
     // ---- 1. CSTs and partitions, concurrently (build_rule 1: the CSTs of
-    //         all queries together first, then the partitions)
-    const bool together = b->base.build_rule == 1;
+    //         all queries together first, then the partitions; 2: the
+    //         partitions together too)
+    const bool together = b->base.build_rule >= 1;
+    const bool parts_together = b->base.build_rule == 2;
     if (together && nq > 0) {
         std::vector<const fast_config*> cf(nq);
         for (int i = 0; i < nq; i++) cf[i] = &b->cls[size_class(qs[i].n)];
@@ -231,7 +235,26 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
             return rc;
         }
     }
-    {
+    if (parts_together && nq > 0) {
+        std::vector<const fast_cst*> cc(nq);
+        std::vector<const fast_config*> cf(nq);
+        std::vector<int32_t> pst(nq, FAST_OK);
+        for (int i = 0; i < nq; i++) {
+            cc[i] = st[i] == FAST_OK ? csts[i] : nullptr;
+            cf[i] = &b->cls[size_class(qs[i].n)];
+        }
+        int rc = FAST_OK;
+        {
+            PoolScope scratch(b->ws[0], b->pools[0]);
+            rc = partition_batch(cc.data(), nq, cf.data(), b->ws[0], chs.data(), pst.data());
+        }
+        if (rc == FAST_OK && cudaStreamSynchronize(b->ws[0]) != cudaSuccess)
+            rc = set_error(FAST_ERR_CUDA, "fast_batch_run: batched partition");
+        if (rc != FAST_OK) {
+            for (int i = 0; i < nq; i++) cst_release_nosync(csts[i]);
+            return rc;
+        }
+    } else {
         std::atomic<int> next{0};
         int T = std::min<int>(b->nthreads, std::max(nq, 1));
         std::vector<std::thread> pool;

@@ -94,3 +94,32 @@ def test_power_law_graph():
             assert ch.copy() == want.copy()
             want.close()
             ch.close()
+
+
+def test_batch_run_with_batched_partitions():
+    """fast_batch_run with build_rule 2 (CSTs and partitions together) gives
+    the counts and statuses of the per-query path."""
+    n, e, lab = synth.powerlaw_graph(seed=2000, n=50_000, m=600_000)
+    g = F.Graph(n, e, lab)
+    wg = synth.WalkGraph(n, e)
+    qs = []
+    for k in (4, 8, 16):
+        for j, kind in enumerate(("induced", "sparse") if k == 4 else ("dense", "sparse")):
+            for r in range(6):
+                q = wg.query(lab, k, kind, seed=93, stream=100 * k + 10 * j + r)
+                qs.append((q.labels, q.edges))
+    qs.insert(3, (np.array([0, 1, 0], np.int32), np.array([[0, 1]], np.int32)))      # disconnected
+    for rule in (dict(), dict(order_rule=1, filter_rule=1)):
+        base = F.default_config(limit=1 << 16, time_budget_s=60.0, max_chunks=1024, **rule)
+        c0, s0 = F.Batch(g, len(qs), base).run(qs)
+        both = F.Config.from_buffer_copy(base)
+        both.build_rule = 2
+        c2, s2 = F.Batch(g, len(qs), both).run(qs)
+        assert s2.tolist() == s0.tolist() and c2.tolist() == c0.tolist(), rule
+
+
+def test_batch_create_rejects_unknown_build_rule():
+    w = synth.er_workload()
+    g = F.Graph(w.n, w.edges, w.labels)
+    with pytest.raises(F.FastError):
+        F.Batch(g, 4, F.default_config(build_rule=3))
