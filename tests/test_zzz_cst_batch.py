@@ -185,3 +185,10 @@ def test_batch_run_with_the_batched_build():
         c1, s1 = F.Batch(g, len(qs), one).run(qs)
         assert s1.tolist() == s0.tolist() and c1.tolist() == c0.tolist(), rule
         assert s0[5] == F.FAST_ERR_INVALID
+
+
+def test_batch_create_rejects_unknown_build_rule():
+    w = synth.er_workload()
+    g = F.Graph(w.n, w.edges, w.labels)
+    with pytest.raises(F.FastError):
+        F.Batch(g, 4, F.default_config(build_rule=3))

@@ -116,10 +116,3 @@ def test_batch_run_with_batched_partitions():
         both.build_rule = 2
         c2, s2 = F.Batch(g, len(qs), both).run(qs)
         assert s2.tolist() == s0.tolist() and c2.tolist() == c0.tolist(), rule
-
-
-def test_batch_create_rejects_unknown_build_rule():
-    w = synth.er_workload()
-    g = F.Graph(w.n, w.edges, w.labels)
-    with pytest.raises(F.FastError):
-        F.Batch(g, 4, F.default_config(build_rule=3))
