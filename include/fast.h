@@ -472,6 +472,14 @@ uint64_t fast_match_noalloc_scratch_bytes(void);
 
 /* ---------------------------------------------------------- measurement */
 
+/* Testing hook (failure injection on the host): the next `after` device
+ * allocations of the library succeed and the one after them fails with
+ * FAST_ERR_OOM, once; after < 0 turns it off (the default).  It drives every
+ * allocation error path without touching the GPU.  Returns the countdown it
+ * replaces: >= 0 while the failure is still to come, -1 once it has happened
+ * (or when it was off). */
+int64_t fast_inject_alloc_failure(int64_t after);
+
 /* Duration in milliseconds of the last matcher kernel launched by this host
  * thread, measured with CUDA events recorded on the launching stream around
  * the kernel (0 if none ran). */

@@ -66,6 +66,7 @@ _SIGS = {
     "fast_build_cst": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "fast_build_cst_batch": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
     "fast_partition_batch": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    "fast_inject_alloc_failure": (ctypes.c_int64, [_i64]),
     "fast_cst_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fast_cst_candidates": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
     "fast_cst_tree_size": (ctypes.c_int, [_vp, _i32, _vp]),
@@ -156,6 +157,13 @@ def default_stream():
     except Exception:
         pass
     return None
+
+
+def inject_alloc_failure(after: int) -> int:
+    """fast_inject_alloc_failure: the next `after` device allocations succeed,
+    the one after them fails with FAST_ERR_OOM (once); after < 0: off.
+    Returns the replaced countdown (-1: the failure has happened, or was off)."""
+    return lib().fast_inject_alloc_failure(after)
 
 
 def default_config(**kw) -> Config:

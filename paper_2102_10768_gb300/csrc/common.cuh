@@ -24,6 +24,11 @@ void note_launch(int n = 1);
 // Turns a CUDA error into FAST_ERR_OOM / FAST_ERR_CUDA with a message.
 int cuda_status(cudaError_t e, const char* what, const char* file, int line);
 
+// Allocation-failure injection (fast_inject_alloc_failure): true for the
+// one device allocation the armed countdown reaches, which then fails with
+// FAST_ERR_OOM.  Disarmed, it costs one relaxed atomic load.
+bool alloc_fault_due();
+
 #define FAST_CUDA(call)                                                          \
     do {                                                                         \
         cudaError_t _e = (call);                                                 \
@@ -83,6 +88,10 @@ template <class T>
 inline int dalloc_direct(T** p, size_t n, cudaStream_t s) {
     size_t bytes = n * sizeof(T);
     if (bytes == 0) bytes = 256;
+    if (alloc_fault_due()) {
+        *p = nullptr;
+        return set_error(FAST_ERR_OOM, "device allocation of %zu bytes failed: injected", bytes);
+    }
     cudaError_t e = cudaMallocAsync((void**)p, bytes, s);
     if (e != cudaSuccess) {
         *p = nullptr;

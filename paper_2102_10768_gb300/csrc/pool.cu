@@ -11,6 +11,7 @@
 // queued on that call's stream; it is handed out again only to the same call
 // (same stream, so the kernels are ordered), and PoolScope synchronises the
 // stream before the pool can serve any other call.
+#include <atomic>
 #include <map>
 #include <memory>
 #include <unordered_map>
@@ -71,7 +72,21 @@ void pool_delete(ScratchPool* p) {
 
 ScratchPool* pool_active() { return tl_active; }
 
+// Allocations left before the injected failure; negative: disarmed.
+std::atomic<int64_t> g_alloc_countdown{-1};
+
+bool alloc_fault_due() {
+    if (g_alloc_countdown.load(std::memory_order_relaxed) < 0) return false;
+    if (g_alloc_countdown.fetch_sub(1, std::memory_order_relaxed) != 0) return false;
+    g_alloc_countdown.store(-1, std::memory_order_relaxed);    // one failure, then disarmed
+    return true;
+}
+
 int pool_alloc(ScratchPool* p, void** out, size_t bytes) {
+    if (alloc_fault_due()) {
+        *out = nullptr;
+        return set_error(FAST_ERR_OOM, "scratch region of %zu bytes: injected failure", bytes);
+    }
     bytes = (bytes + kPoolAlign - 1) / kPoolAlign * kPoolAlign;
     for (int pass = 0; pass < 2; pass++) {
         for (int b = 0; b < (int)p->blocks.size(); b++) {
@@ -140,6 +155,7 @@ PoolScope::~PoolScope() {
 }
 
 int Arena::grow(size_t bytes, cudaStream_t s) {
+    if (alloc_fault_due()) return set_error(FAST_ERR_OOM, "CST block of %zu bytes: injected failure", bytes);
     size_t sz = bytes;
     if (sz < next_) sz = next_;
     void* b = nullptr;
@@ -163,3 +179,7 @@ void Arena::release(cudaStream_t s) {
 }
 
 }  // namespace fast
+
+extern "C" int64_t fast_inject_alloc_failure(int64_t after) {
+    return fast::g_alloc_countdown.exchange(after < 0 ? -1 : after, std::memory_order_relaxed);
+}

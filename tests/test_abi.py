@@ -53,3 +53,25 @@ def test_config_rejects_unknown_fields():
     assert c.build_rule == 1
     with pytest.raises(AttributeError):
         c.bulid_rule = 1
+
+
+def test_injected_allocation_failure_fires_once():
+    """fast_inject_alloc_failure(0): the next device allocation fails with
+    FAST_ERR_OOM and says it was injected; the injector is then off, so the
+    next call reaches a real allocation (which, on a machine without a GPU,
+    fails for that reason instead)."""
+    import numpy as np
+    import pytest
+    e = np.array([[0, 1], [1, 2]], np.int32)
+    lab = np.zeros(4, np.int32)
+    assert F.inject_alloc_failure(0) == -1
+    try:
+        with pytest.raises(F.FastError, match="injected"):
+            F.Graph(4, e, lab)
+    finally:
+        assert F.inject_alloc_failure(-1) == -1           # it fired
+    assert F.inject_alloc_failure(7) == -1 and F.inject_alloc_failure(-1) == 7
+    try:
+        F.Graph(4, e, lab)
+    except F.FastError as err:
+        assert "injected" not in str(err)
