@@ -24,6 +24,7 @@ p50/p99), and a Poisson stream into the request loop (served).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -66,7 +67,9 @@ def parse():
                    help="how the batched step builds its CSTs and partitions: per query on the host threads "
                         "(default), the CSTs of all queries together (fast_build_cst_batch), or both together "
                         "(also fast_partition_batch)")
-    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample")
+    p.add_argument("--no-build-legs", dest="build_legs", action="store_false",
+                   help="do not also time the batched CST build (in a child process) beside the headline")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample (0: none)")
     return p.parse_args()
 
 
@@ -183,6 +186,30 @@ def oracle_sample(args, og, qs, budget_s, start=0):
         emb += r["count"]
         done += 1
     return emb, t, done, i
+
+
+def build_leg(args, rule, digest):
+    """The same batched step with another build rule, in a child process (a
+    failure there cannot touch the numbers above): its throughput and phase
+    times, and whether its per-query counts equal the headline step's."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--steps", "2", "--warmup", "1", "--no-serve",
+           "--cpu-seconds", "0", "--no-build-legs", "--build", rule, "--queries", str(args.queries),
+           "--seed", str(args.seed), "--limit", str(args.limit), "--budget", str(args.budget),
+           "--delta-w", str(args.delta_w), "--max-chunks", str(args.max_chunks), "--order", args.order,
+           "--filter", args.filter, "--threads", str(args.threads), "--batch-budget", str(args.batch_budget)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
+        js = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode != 0 or not js:
+            tail = (r.stderr.strip().splitlines() or [""])[-1]
+            return {"build": rule, "error": f"exit {r.returncode}: {tail[:300]}"}
+        d = json.loads(js[-1])
+        return {"build": rule, "value": d["value"], "unit": d["unit"], "steps": d["steps"],
+                "ms_per_step": d["ms_per_step"], "build_ms_per_step": d["build_ms_per_step"],
+                "match_ms_per_step": d["match_ms_per_step"], "gpu_launches_per_step": d["gpu_launches"] / d["steps"],
+                "clocks": d.get("clocks"), "counts_equal": digest is not None and d.get("counts_sha1") == digest}
+    except Exception as ex:                                   # a timeout or an unreadable line
+        return {"build": rule, "error": repr(ex)[:300]}
 
 
 def cpu_baseline(args, n, e, lab, qs, budget_s):
@@ -327,7 +354,7 @@ def run_ours(args):
         if bad:
             raise F.FastError(bad[0], "batched step: a query failed")
         tm = bt.timing()
-        return int(c.sum()), ev0.elapsed_time(ev1), tm, int((st == F.FAST_ERR_TIMEOUT).sum())
+        return int(c.sum()), ev0.elapsed_time(ev1), tm, int((st == F.FAST_ERR_TIMEOUT).sum()), c
 
     for _ in range(args.warmup):
         bstep()
@@ -338,8 +365,9 @@ def run_ours(args):
     clocks.start()
     launches0 = F.kernel_launches()
     tot_emb, tot_ms, tot_kms, tot_bytes, tot_build, tot_cut = 0, 0.0, 0.0, 0, 0.0, 0
+    last_counts = None
     for _ in range(args.steps):
-        em, ms, tm, cut = bstep()
+        em, ms, tm, cut, last_counts = bstep()
         tot_emb += em
         tot_ms += ms
         tot_kms += tm["match_ms"]
@@ -455,7 +483,8 @@ def run_ours(args):
     peak, peak_kind = peaks()
     achieved = tot_bytes / (tot_kms / 1000.0) / 1e9 if tot_kms > 0 else 0.0
     q_achieved = q_bytes / (q_kms / 1000.0) / 1e9 if q_kms > 0 else 0.0
-    cpu = cpu_baseline(args, n, e, lab, qs, args.cpu_seconds) if world == 1 else None
+    cpu = cpu_baseline(args, n, e, lab, qs, args.cpu_seconds) if world == 1 and args.cpu_seconds > 0 else None
+    digest = hashlib.sha1(np.asarray(last_counts, np.int64).tobytes()).hexdigest() if last_counts is not None else None
     line = {
         "metric": METRIC, "value": tot_all / t_s, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_s / steps,
@@ -492,6 +521,9 @@ def run_ours(args):
         line["served"] = served
     if cpu:
         line["cpu_baseline"] = cpu
+    line["counts_sha1"] = digest
+    if world == 1 and args.build_legs and args.build == "threads":
+        line["batched_build"] = build_leg(args, "batched", digest)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
