@@ -58,7 +58,8 @@ def _L():
                                      i64, vp, vp, vp, vp, i64, ctypes.c_int, u64]
         lib.oracle_check_embeddings.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, i64, vp]
         lib.oracle_check_embeddings.restype = i64
-        lib.oracle_cst_build.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]
+        lib.oracle_cst_build.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int]
         lib.oracle_cst_build.restype = vp
         lib.oracle_cst_free.argtypes = [vp]
         lib.oracle_cst_root.argtypes = [vp]
@@ -192,15 +193,18 @@ class Cst:
 
     ORDERS = {"path": 0, "greedy": 1}
     FILTERS = {"ldf": 0, "nlf": 1}
+    REFINES = {"once": 0, "fixpoint": 1}
 
-    def __init__(self, g: Graph, qlabels, qedges, order: str = "path", filter: str = "ldf"):
+    def __init__(self, g: Graph, qlabels, qedges, order: str = "path", filter: str = "ldf", refine: str = "once"):
         """order: "path" (the paper's path-based order) or "greedy" (edges
         to already placed vertices first); filter: "ldf" (label and degree)
-        or "nlf" (also neighbour label frequencies); see oracle/cst_ref.c."""
+        or "nlf" (also neighbour label frequencies); refine: "once" (the
+        paper's single bottom-up pass) or "fixpoint" (repeated, with the
+        non-tree neighbour test); see oracle/cst_ref.c."""
         ql, qe = _qarrays(qlabels, qedges)
         self.k = ql.shape[0]
         self._h = _L().oracle_cst_build(g._h, self.k, _p(ql), qe.shape[0], _p(qe), self.ORDERS[order],
-                                        self.FILTERS[filter])
+                                        self.FILTERS[filter], self.REFINES[refine])
         if not self._h:
             raise ValueError("oracle_cst_build: invalid or disconnected query")
         k = self.k

@@ -22,7 +22,14 @@
  *   bottom-up for u in reverse BFS order: each child list N^u_{u_c}(v) is cut
  *            to the (already refined) C(u_c); v stays in C(u) iff every such
  *            list is non-empty and (u is the root or v lies in some list of
- *            the parent).  One pass, as written.
+ *            the parent).  refine rule 0: one pass, as written.
+ *            refine rule 1 (the fixpoint refinement the paper leaves out,
+ *            as CS-style filters do): v must also have, for every query
+ *            neighbour w of u joined by a non-tree edge, a neighbour in C(w);
+ *            the pass repeats until it removes nothing.  Sound: an
+ *            embedding's image of u passes every test, so no embedding is
+ *            lost; for a tree query with pairwise distinct labels the result
+ *            is exactly the projections of the embedding set.
  *   order    rule 0 (the paper's path-based order, Sec. IV-B): depth-first
  *            preorder of t_q from the root, children visited in increasing
  *            (|C(u_c)|, u_c): whole root-to-leaf paths in turn.
@@ -108,8 +115,10 @@ void oracle_cst_free(ocst* c) {
  * Returns a handle, or NULL on invalid or disconnected input.
  */
 ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int32_t* qe, int order_rule,
-                       int filter_rule) {
-    if (k < 1 || k > CMAXK || order_rule < 0 || order_rule > 1 || filter_rule < 0 || filter_rule > 1) return NULL;
+                       int filter_rule, int refine_rule) {
+    if (k < 1 || k > CMAXK || order_rule < 0 || order_rule > 1 || filter_rule < 0 || filter_rule > 1 ||
+        refine_rule < 0 || refine_rule > 1)
+        return NULL;
     int A[CMAXK][CMAXK];
     memset(A, 0, sizeof(A));
     int dq[CMAXK] = {0};
@@ -195,7 +204,11 @@ ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int
     }
     free(mark);
 
-    /* bottom-up refinement */
+    /* bottom-up refinement (rule 1: repeated, with the non-tree test, until
+     * a pass removes nothing) */
+    int64_t removed;
+    do {
+    removed = 0;
     for (int t = k - 1; t >= 0; t--) {
         int u = c->bfs[t];
         int64_t nu = c->cand[u].n;
@@ -221,8 +234,16 @@ ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int
                 if (o == 0) ok = 0;
             }
             if (ok && u != r && !haspar[i]) ok = 0;
-            (void)v;
+            if (ok && refine_rule == 1)
+                for (int w = 0; w < k && ok; w++) {
+                    if (!A[u][w] || c->parent[w] == u || c->parent[u] == w) continue;   /* tree edge */
+                    int any = 0;
+                    for (int64_t j = g->off[v]; j < g->off[v + 1] && !any; j++)
+                        if (find_sorted(c->cand[w].v, c->cand[w].n, g->adj[j]) >= 0) any = 1;
+                    if (!any) ok = 0;
+                }
             keep[i] = (uint8_t)ok;
+            if (!ok) removed++;
         }
         /* drop invalid candidates together with their lists */
         int64_t o = 0;
@@ -243,6 +264,7 @@ ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int
         for (int w = 0; w < k; w++) if (c->parent[w] == u) c->tree_n[w] = o;
         free(keep); free(haspar);
     }
+    } while (refine_rule == 1 && removed > 0);
 
     /* matching order, rule 1: greedy by edges to the placed vertices */
     if (order_rule == 1) {

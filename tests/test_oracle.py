@@ -571,3 +571,70 @@ def test_partition_complete_for_every_order_and_filter(seed, order, filt):
         chunks = c.partition(max(1, wi // 30), max_chunks=cap)
         s = sum(oracle.count(g, ql, qe, allow=c.chunk_allow(j, pre, a, b)) for (j, pre, a, b, w, i) in chunks)
         assert s == total
+
+
+# ------------------------------------------------- fixpoint refinement
+
+def test_fixpoint_refinement_hand_case():
+    """One bottom-up pass, as the paper writes it, keeps the B candidates of a
+    parent candidate that is removed after them; the fixpoint removes them.
+    Query A-B, A-C rooted at A; in G, a2 has two B neighbours and no C
+    neighbour."""
+    e = np.array([(0, 1), (0, 2), (3, 4), (3, 5)], np.int32)
+    lab = np.array([0, 1, 2, 0, 1, 1], np.int32)
+    g = oracle.Graph(6, e, lab)
+    ql, qe = np.array([0, 1, 2], np.int32), np.array([(0, 1), (0, 2)], np.int32)
+    once, fix = oracle.Cst(g, ql, qe), oracle.Cst(g, ql, qe, refine="fixpoint")
+    assert once.root == fix.root == 0
+    assert [once.cand(u).tolist() for u in range(3)] == [[0], [1, 4, 5], [2]]
+    assert [fix.cand(u).tolist() for u in range(3)] == [[0], [1], [2]]
+    assert once.workload()[1] == fix.workload()[1] == oracle.count(g, ql, qe) == 1
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_fixpoint_refinement_is_sound_tighter_and_arc_consistent(seed):
+    """The fixpoint keeps every embedding's images, lies inside the single
+    pass's sets (same root and t_q), and is arc consistent: along every query
+    edge, tree or not, each candidate has a neighbour among the other end's
+    candidates.  W can only drop and still bounds the count."""
+    n, edges, labels, ql, qe = _cst_case(seed)
+    g = oracle.Graph(n, edges, labels)
+    once = oracle.Cst(g, ql, qe)
+    fix = oracle.Cst(g, ql, qe, refine="fixpoint")
+    k = len(ql)
+    off_g, adj_g = g.csr()
+    N = lambda v: set(adj_g[off_g[v]:off_g[v + 1]].tolist())
+    C = [set(fix.cand(u).tolist()) for u in range(k)]
+    assert fix.root == once.root and fix.parent.tolist() == once.parent.tolist()
+    for u in range(k):
+        assert C[u] <= set(once.cand(u).tolist())
+    r = oracle.match(g, ql, qe, max_emb=1 << 18)
+    for row in r["emb"].tolist():
+        for u in range(k):
+            assert row[u] in C[u]
+    for a, b in qe.tolist():
+        for x, y in ((a, b), (b, a)):
+            for v in C[x]:
+                assert N(v) & C[y], (x, y, v)
+    assert r["count"] <= fix.workload()[1] <= once.workload()[1]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_fixpoint_is_exact_for_trees_with_distinct_labels(seed):
+    """For a tree query whose labels are pairwise distinct, the fixpoint's
+    C(u) is exactly the set of images of u over all embeddings: on a tree,
+    arc consistency leaves only values that extend to a homomorphism, and
+    distinct labels make every homomorphism injective."""
+    rng = np.random.default_rng(700 + seed)
+    n, L = 150, 6
+    edges, labels = random_graph(rng, n, 0.06, L)
+    k = int(rng.integers(2, 6))
+    ql = rng.permutation(L)[:k].astype(np.int32)
+    qe = np.array([[int(rng.integers(0, v)), v] for v in range(1, k)], np.int32)
+    g = oracle.Graph(n, edges, labels)
+    fix = oracle.Cst(g, ql, qe, refine="fixpoint")
+    r = oracle.match(g, ql, qe, max_emb=1 << 20)
+    assert r["complete"] and r["count"] < 1 << 20
+    for u in range(k):
+        proj = set(r["emb"][:, u].tolist()) if r["count"] else set()
+        assert set(fix.cand(u).tolist()) == proj, u
