@@ -193,14 +193,15 @@ class Cst:
 
     ORDERS = {"path": 0, "greedy": 1}
     FILTERS = {"ldf": 0, "nlf": 1}
-    REFINES = {"once": 0, "fixpoint": 1}
+    REFINES = {"once": 0, "fixpoint": 1, "once_nt": 2}
 
     def __init__(self, g: Graph, qlabels, qedges, order: str = "path", filter: str = "ldf", refine: str = "once"):
         """order: "path" (the paper's path-based order) or "greedy" (edges
         to already placed vertices first); filter: "ldf" (label and degree)
         or "nlf" (also neighbour label frequencies); refine: "once" (the
-        paper's single bottom-up pass) or "fixpoint" (repeated, with the
-        non-tree neighbour test); see oracle/cst_ref.c."""
+        paper's single bottom-up pass), "fixpoint" (repeated, with the
+        non-tree neighbour test) or "once_nt" (one pass with that test); see
+        oracle/cst_ref.c."""
         ql, qe = _qarrays(qlabels, qedges)
         self.k = ql.shape[0]
         self._h = _L().oracle_cst_build(g._h, self.k, _p(ql), qe.shape[0], _p(qe), self.ORDERS[order],

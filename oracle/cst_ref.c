@@ -30,6 +30,10 @@
  *            embedding's image of u passes every test, so no embedding is
  *            lost; for a tree query with pairwise distinct labels the result
  *            is exactly the projections of the embedding set.
+ *            refine rule 2: the same non-tree test in the single pass,
+ *            against each set as it stands when u is reached (refined for
+ *            vertices later in the BFS order, top-down for earlier ones);
+ *            no repeat.  Between rule 1 and rule 0 as sets.
  *   order    rule 0 (the paper's path-based order, Sec. IV-B): depth-first
  *            preorder of t_q from the root, children visited in increasing
  *            (|C(u_c)|, u_c): whole root-to-leaf paths in turn.
@@ -117,7 +121,7 @@ void oracle_cst_free(ocst* c) {
 ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int32_t* qe, int order_rule,
                        int filter_rule, int refine_rule) {
     if (k < 1 || k > CMAXK || order_rule < 0 || order_rule > 1 || filter_rule < 0 || filter_rule > 1 ||
-        refine_rule < 0 || refine_rule > 1)
+        refine_rule < 0 || refine_rule > 2)
         return NULL;
     int A[CMAXK][CMAXK];
     memset(A, 0, sizeof(A));
@@ -234,7 +238,7 @@ ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int
                 if (o == 0) ok = 0;
             }
             if (ok && u != r && !haspar[i]) ok = 0;
-            if (ok && refine_rule == 1)
+            if (ok && refine_rule >= 1)
                 for (int w = 0; w < k && ok; w++) {
                     if (!A[u][w] || c->parent[w] == u || c->parent[u] == w) continue;   /* tree edge */
                     int any = 0;

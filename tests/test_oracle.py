@@ -638,3 +638,44 @@ def test_fixpoint_is_exact_for_trees_with_distinct_labels(seed):
     for u in range(k):
         proj = set(r["emb"][:, u].tolist()) if r["count"] else set()
         assert set(fix.cand(u).tolist()) == proj, u
+
+
+def test_once_with_non_tree_test_hand_case():
+    """Triangle query A-B-C rooted at A (non-tree edge B-C).  G holds the
+    triangle a1 b1 c1 and a path b2 - a2 - c2 whose b2 and c2 are not
+    adjacent (each has one more neighbour, so the degree filter keeps them).
+    One pass keeps a2, b2 and c2; the pass with the non-tree test removes c2
+    and b2 (no neighbour among the other's candidates), and then a2, whose
+    list into B is empty."""
+    e = np.array([(0, 1), (0, 2), (1, 2), (3, 4), (3, 5), (4, 6), (5, 7)], np.int32)
+    lab = np.array([0, 1, 2, 0, 1, 2, 3, 3], np.int32)
+    g = oracle.Graph(8, e, lab)
+    ql, qe = np.array([0, 1, 2], np.int32), np.array([(0, 1), (0, 2), (1, 2)], np.int32)
+    once = oracle.Cst(g, ql, qe)
+    nt = oracle.Cst(g, ql, qe, refine="once_nt")
+    assert once.root == nt.root == 0
+    assert [once.cand(u).tolist() for u in range(3)] == [[0, 3], [1, 4], [2, 5]]
+    assert [nt.cand(u).tolist() for u in range(3)] == [[0], [1], [2]]
+    assert oracle.count(g, ql, qe) == 1
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_once_with_non_tree_test_lies_between(seed):
+    """The single pass with the non-tree test keeps every embedding's images
+    and lies between the fixpoint and the paper's single pass, vertex by
+    vertex (same root and t_q)."""
+    n, edges, labels, ql, qe = _cst_case(seed)
+    g = oracle.Graph(n, edges, labels)
+    once = oracle.Cst(g, ql, qe)
+    nt = oracle.Cst(g, ql, qe, refine="once_nt")
+    fix = oracle.Cst(g, ql, qe, refine="fixpoint")
+    k = len(ql)
+    assert nt.root == once.root and nt.parent.tolist() == once.parent.tolist()
+    for u in range(k):
+        a, b, c = set(fix.cand(u).tolist()), set(nt.cand(u).tolist()), set(once.cand(u).tolist())
+        assert a <= b <= c, u
+    r = oracle.match(g, ql, qe, max_emb=1 << 18)
+    for row in r["emb"].tolist():
+        for u in range(k):
+            assert row[u] in set(nt.cand(u).tolist())
+    assert r["count"] <= nt.workload()[1] <= once.workload()[1]
