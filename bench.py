@@ -67,6 +67,9 @@ def parse():
                    help="how the batched step builds its CSTs and partitions: per query on the host threads "
                         "(default), the CSTs of all queries together (fast_build_cst_batch), or both together "
                         "(also fast_partition_batch)")
+    p.add_argument("--refine", choices=["once", "once_nt"], default="once",
+                   help="bottom-up refinement: the paper's single pass (default) or the pass with the non-tree "
+                        "neighbour test (needs --build batched or batched-all)")
     p.add_argument("--no-build-legs", dest="build_legs", action="store_false",
                    help="do not also time the batched CST build (in a child process) beside the headline")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample (0: none)")
@@ -325,6 +328,7 @@ def run_ours(args):
     bcfg = F.Config.from_buffer_copy(cfg)
     bcfg.time_budget_s = args.batch_budget
     bcfg.build_rule = {"threads": 0, "batched": 1, "batched-all": 2}[args.build]
+    bcfg.refine_rule = 2 if args.refine == "once_nt" else 0
     bt = F.Batch(g, len(bq), bcfg, threads=args.threads)
     tuned = None
     if args.autotune:
@@ -493,7 +497,8 @@ def run_ours(args):
         "config": {"workload": desc, "queries_per_step": len(qs),
                    "mode": f"batched: fast_batch_run, {args.threads} build threads, one graph-replayed matcher "
                            f"launch per step (budget {args.batch_budget} s)",
-                   "order": args.order, "filter": args.filter, "cst_build": args.build, "autotuned": tuned,
+                   "order": args.order, "filter": args.filter, "cst_build": args.build, "refine": args.refine,
+                   "autotuned": tuned,
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}, queries per rank"},
         "queries_per_sec": len(qs) * steps * world / t_s,
         "embeddings_per_step": tot_emb / steps,

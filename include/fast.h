@@ -123,6 +123,14 @@ typedef struct {
      * result, are the same either way; fast_batch_create rejects other
      * values. */
     int32_t build_rule;
+    /* Bottom-up refinement of the CST (Sec. IV-A).  0: the paper's single
+     * pass.  2: the same pass where a candidate v of u must also have, for
+     * every query neighbour w of u joined by a non-tree edge, a neighbour in
+     * C(w) as it stands when u is reached (refined for vertices later in the
+     * BFS order, top-down for earlier ones): smaller CSTs, the same
+     * embeddings.  Rule 2 is built by fast_build_cst_batch only (the batch
+     * with build_rule >= 1); fast_build_cst and build_rule 0 reject it. */
+    int32_t refine_rule;
 } fast_config;
 
 /* Default tunables: delta_w = 2^20, no sampling, max_chunks = 2^16,

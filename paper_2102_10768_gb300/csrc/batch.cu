@@ -128,6 +128,9 @@ int batch_create(const fast_graph* g, const fast_config* cfg, int32_t max_q, int
     if (!g || max_q < 1) return set_error(FAST_ERR_INVALID, "fast_batch_create: bad graph or max_queries");
     if (cfg && (cfg->build_rule < 0 || cfg->build_rule > 2))
         return set_error(FAST_ERR_INVALID, "fast_batch_create: build_rule %d (0, 1 or 2)", cfg->build_rule);
+    if (cfg && cfg->refine_rule != 0 && (cfg->refine_rule != 2 || cfg->build_rule < 1))
+        return set_error(FAST_ERR_INVALID, "fast_batch_create: refine_rule %d needs 2 and build_rule >= 1",
+                         cfg->refine_rule);
     fast_batch* b = new fast_batch();
     cudaGetDevice(&b->device);
     b->g = g;

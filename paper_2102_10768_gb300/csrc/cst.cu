@@ -366,6 +366,9 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
     if (cfg_in && (cfg_in->filter_rule < 0 || cfg_in->filter_rule > 1))
         return set_error(FAST_ERR_INVALID, "fast_build_cst: filter_rule %d (0 label and degree, 1 label frequencies)",
                          cfg_in->filter_rule);
+    if (cfg_in && cfg_in->refine_rule != 0)
+        return set_error(FAST_ERR_INVALID, "fast_build_cst: refine_rule %d (only fast_build_cst_batch refines further)",
+                         cfg_in->refine_rule);
     const int k = q->n;
     fast_cst* c = new fast_cst();
     memset(c->cand, 0, sizeof(c->cand)); memset(c->t_off, 0, sizeof(c->t_off)); memset(c->t_idx, 0, sizeof(c->t_idx));

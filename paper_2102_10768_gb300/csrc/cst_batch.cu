@@ -174,6 +174,42 @@ __global__ void k_valid_rows_b(const ValidDesc* __restrict__ D, const int64_t* _
     });
 }
 
+// Refine rule 2, the non-tree test: flag[r] = 1 if candidate cand[r] of u
+// has a neighbour in the bitmap of C(w), for one non-tree query neighbour w
+// (its label segment in G; every member of the bitmap carries w's label, so
+// an ungrouped row needs no label test).  One warp per row, rows of all
+// (query, neighbour) pairs end to end.
+struct NtDesc {
+    const int32_t* cand;
+    int32_t l;
+    const uint32_t* bits;
+    uint8_t* flag;
+};
+
+__global__ void k_nt_support_b(const NtDesc* __restrict__ D, const int64_t* __restrict__ item_off, int nseg,
+                               GraphRuns G, const int32_t* __restrict__ col) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = item_off[nseg];
+    for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < total;
+         it += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int s = seg_of_tile(item_off, nseg, it);
+        const NtDesc& d = D[s];
+        const int64_t r = it - item_off[s];
+        int64_t b, len;
+        label_segment(G, d.cand[r], d.l, &b, &len);
+        bool any = false;
+        for (int64_t base = 0; base < len; base += 32) {      // the same steps on every lane
+            bool hit = false;
+            if (base + lane < len) {
+                const int32_t x = col[b + base + lane];
+                hit = (d.bits[x >> 5] >> (x & 31)) & 1u;
+            }
+            if (__any_sync(0xffffffffu, hit)) { any = true; break; }
+        }
+        if (lane == 0) d.flag[r] = any ? 1 : 0;
+    }
+}
+
 // off[*n] = *val (as k_set_tail), one thread per descriptor.
 struct SetTailDesc {
     int64_t* off;
@@ -439,6 +475,8 @@ struct Q {
     fast_cst* c = nullptr;
     int k = 0;
     bool nlf = false;
+    bool nt_refine = false;       // refine rule 2: the non-tree test in the bottom-up pass
+    uint32_t* root_bits = nullptr; // rule 2: bitmap of C_td(root) for the test
     int A[kMaxK][kMaxK] = {};
     int dq[kMaxK] = {};
     int bpos[kMaxK] = {};         // vertex -> BFS position
@@ -783,6 +821,25 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
         }
     }
 
+    // refine rule 2 tests against C_td(root) until the root's own step: its
+    // bitmap (the other vertices' top-down bitmaps already exist)
+    {
+        Carver cv;
+        std::vector<SetBitsDesc> sb;
+        std::vector<int64_t> ni;
+        for (auto& q : Qs)
+            if (q.nt_refine) cv.add(&q.root_bits, nw);
+        FAST_TRY(cv.alloc(keep, true));
+        for (int qi = 0; qi < nq; qi++) {
+            Q& q = Qs[qi];
+            if (!q.nt_refine) continue;
+            const int r = q.c->root;
+            sb.push_back({q.td_cand[r], zp(F_TD + 0, qi), q.root_bits});
+            ni.push_back(q.ctd[r]);
+        }
+        FAST_TRY(run_items(k_set_bits_b, sb, ni, s));
+    }
+
     // ---------------------------------------------------- bottom-up
     for (int t = K - 1; t >= 0; t--) {
         act.clear();
@@ -827,6 +884,52 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
             }
             FAST_TRY(run_tiles(k_any_alive_b, aa, ent, s));
         }
+        // refine rule 2: per (query, non-tree neighbour w of u), which rows
+        // have a neighbour in C(w) as it stands now
+        std::vector<int> na, nwv, nbeg(act.size() + 1, 0);
+        for (size_t a = 0; a < act.size(); a++) {
+            const Q& q = Qs[act[a]];
+            const int u = q.c->bfs[t];
+            if (q.nt_refine)
+                for (int w = 0; w < q.k; w++)
+                    if (q.A[u][w] && q.c->parent[w] != u && q.c->parent[u] != w) { na.push_back((int)a); nwv.push_back(w); }
+            nbeg[a + 1] = (int)na.size();
+        }
+        std::vector<uint8_t*> ntf(na.size(), nullptr);
+        if (!na.empty()) {
+            Carver cf;
+            for (size_t j = 0; j < na.size(); j++) {
+                const Q& q = Qs[act[na[j]]];
+                cf.add(&ntf[j], q.ctd[q.c->bfs[t]]);
+            }
+            FAST_TRY(cf.alloc(lvl, true));
+            std::vector<NtDesc> nd;
+            std::vector<int64_t> ni;
+            for (size_t j = 0; j < na.size(); j++) {
+                const Q& q = Qs[act[na[j]]];
+                const int u = q.c->bfs[t], w = nwv[j];
+                // later in the BFS order: already refined; earlier: its
+                // top-down set (the root's own bitmap; the others' reached
+                // bitmaps are not rewritten before their step)
+                const uint32_t* bits = (w == q.c->root && q.bpos[w] < t) ? q.root_bits : q.alive[w];
+                nd.push_back({q.td_cand[u], q.c->qlabel[w], bits, ntf[j]});
+                ni.push_back(q.ctd[u]);
+            }
+            if (!nd.empty()) {
+                const std::vector<int64_t> off = prefix(ni);
+                if (off.back() > 0) {
+                    Scratch sc(s);
+                    const NtDesc* dd = nullptr;
+                    const int64_t* doff = nullptr;
+                    FAST_TRY(upload(nd, off, sc, &dd, &doff));
+                    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(off.back(), 8),
+                                                                                  (int64_t)num_sms() * 16));
+                    k_nt_support_b<<<(unsigned)blocks, 256, 0, s>>>(dd, doff, (int)nd.size(), G, g->col);
+                    note_launch();
+                    if (cudaGetLastError() != cudaSuccess) return set_error(FAST_ERR_CUDA, "batched non-tree test launch");
+                }
+            }
+        }
         {
             std::vector<ValidDesc> vd;
             std::vector<int64_t> ni;
@@ -837,6 +940,7 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
                 ValidDesc d;
                 memset(&d, 0, sizeof(d));
                 for (int j = pbeg[a]; j < pbeg[a + 1]; j++) d.cf.has[d.cf.nch++] = has[j];
+                for (int j = nbeg[a]; j < nbeg[a + 1]; j++) d.cf.has[d.cf.nch++] = ntf[j];
                 d.valid = valid[a];
                 d.vflag = newrow[a];
                 vd.push_back(d);
@@ -1131,6 +1235,8 @@ int build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, 
                 rc = set_error(FAST_ERR_INVALID,
                                "fast_build_cst_batch: filter_rule %d (0 label and degree, 1 label frequencies)",
                                cf->filter_rule);
+            if (rc == FAST_OK && cf && cf->refine_rule != 0 && cf->refine_rule != 2)
+                rc = set_error(FAST_ERR_INVALID, "fast_build_cst_batch: refine_rule %d (0 or 2)", cf->refine_rule);
             status[i] = rc;
             if (rc != FAST_OK) continue;
             fast_cst* c = new fast_cst();
@@ -1148,6 +1254,7 @@ int build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, 
             q.c = c;
             q.k = c->k;
             q.nlf = c->cfg.filter_rule == 1;
+            q.nt_refine = c->cfg.refine_rule == 2;
             Qs.push_back(q);
         }
         int rc = Qs.empty() ? FAST_OK : build_all(g, Qs, s);

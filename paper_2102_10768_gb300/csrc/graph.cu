@@ -63,6 +63,7 @@ extern "C" void fast_config_default(fast_config* cfg) {
     cfg->order_rule = 0;
     cfg->filter_rule = 0;
     cfg->build_rule = 0;
+    cfg->refine_rule = 0;
 }
 
 namespace {

@@ -192,3 +192,17 @@ def test_batch_create_rejects_unknown_build_rule():
     g = F.Graph(w.n, w.edges, w.labels)
     with pytest.raises(F.FastError):
         F.Batch(g, 4, F.default_config(build_rule=3))
+
+
+def test_refine_rule_needs_the_batched_build():
+    """The per-query build and the threaded batch reject refine rule 2 before
+    any device work; rule 1 (the fixpoint) is the oracle's only."""
+    w = synth.er_workload()
+    g = F.Graph(w.n, w.edges, w.labels)
+    q = w.queries[0]
+    with pytest.raises(F.FastError):
+        F.Cst(g, q.labels, q.edges, F.default_config(refine_rule=2))
+    with pytest.raises(F.FastError):
+        F.Batch(g, 4, F.default_config(refine_rule=2))
+    with pytest.raises(F.FastError):
+        F.Batch(g, 4, F.default_config(refine_rule=1, build_rule=1))
