@@ -73,7 +73,10 @@ def parse():
     p.add_argument("--no-build-legs", dest="build_legs", action="store_false",
                    help="do not also time the batched CST build (in a child process) beside the headline")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle sample (0: none)")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.refine != "once" and args.build == "threads":
+        p.error("--refine once_nt needs --build batched or batched-all")
+    return args
 
 
 def query_stream0(rank: int, k: int, kind: str) -> int:
