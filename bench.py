@@ -198,7 +198,7 @@ def build_leg(args, rule, digest):
     """The same batched step with another build rule, in a child process (a
     failure there cannot touch the numbers above): its throughput and phase
     times, and whether its per-query counts equal the headline step's."""
-    cmd = [sys.executable, os.path.abspath(__file__), "--steps", "2", "--warmup", "1", "--no-serve",
+    cmd = [sys.executable, os.path.abspath(__file__), "--steps", "2", "--warmup", "3", "--no-serve",
            "--cpu-seconds", "0", "--no-build-legs", "--build", rule, "--queries", str(args.queries),
            "--seed", str(args.seed), "--limit", str(args.limit), "--budget", str(args.budget),
            "--delta-w", str(args.delta_w), "--max-chunks", str(args.max_chunks), "--order", args.order,
