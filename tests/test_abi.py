@@ -76,3 +76,20 @@ def test_injected_allocation_failure_fires_once():
         F.Graph(4, e, lab)
     except F.FastError as err:
         assert "injected" not in str(err)
+
+
+def test_every_kernel_launch_is_counted():
+    """fast_kernel_launches (the bench's gpu_launches) counts every launch the
+    library makes: each `<<<` in its sources is followed by note_launch()
+    within a few lines."""
+    import glob
+    missing = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "paper_2102_10768_gb300", "csrc", "*.cu*"))):
+        lines = open(path).read().split("\n")
+        for i, ln in enumerate(lines):
+            if "<<<" not in ln or ln.lstrip().startswith("//"):
+                continue
+            window = "\n".join(lines[i:i + 6])
+            if "note_launch(" not in window:
+                missing.append(f"{os.path.basename(path)}:{i + 1}")
+    assert not missing, missing
