@@ -93,3 +93,26 @@ def test_every_kernel_launch_is_counted():
             if "note_launch(" not in window:
                 missing.append(f"{os.path.basename(path)}:{i + 1}")
     assert not missing, missing
+
+
+def test_product_never_imports_the_oracle():
+    """The library's package never imports oracle/; bench.py imports it only
+    inside its CPU baseline and reference arm."""
+    import ast
+    import glob
+
+    def oracle_imports(tree):
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import) and any(a.name.split(".")[0] == "oracle" for a in node.names):
+                yield node
+            if isinstance(node, ast.ImportFrom) and (node.module or "").split(".")[0] == "oracle":
+                yield node
+
+    for path in glob.glob(os.path.join(ROOT, "paper_2102_10768_gb300", "**", "*.py"), recursive=True):
+        assert not list(oracle_imports(ast.parse(open(path).read()))), path
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    allowed = set()
+    for fn in ast.walk(tree):
+        if isinstance(fn, ast.FunctionDef) and fn.name in ("cpu_baseline", "run_reference", "oracle_sample"):
+            allowed |= {id(n) for n in oracle_imports(fn)}
+    assert all(id(n) in allowed for n in oracle_imports(tree))
