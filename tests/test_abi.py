@@ -116,3 +116,17 @@ def test_product_never_imports_the_oracle():
         if isinstance(fn, ast.FunctionDef) and fn.name in ("cpu_baseline", "run_reference", "oracle_sample"):
             allowed |= {id(n) for n in oracle_imports(fn)}
     assert all(id(n) in allowed for n in oracle_imports(tree))
+
+
+def test_oracle_and_library_share_no_code():
+    """No library source includes an oracle file and no oracle source includes
+    a library file (they meet only through synth/'s inputs and the tests)."""
+    import glob
+    import re
+    inc = re.compile(r'#\s*include\s*"([^"]+)"')
+    for path in glob.glob(os.path.join(ROOT, "paper_2102_10768_gb300", "csrc", "*")):
+        for name in inc.findall(open(path).read()):
+            assert "oracle" not in name, (path, name)
+    for path in glob.glob(os.path.join(ROOT, "oracle", "*.[ch]")):
+        for name in inc.findall(open(path).read()):
+            assert "csrc" not in name and "fast.h" not in name and "internal" not in name, (path, name)
