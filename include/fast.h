@@ -347,8 +347,10 @@ typedef struct fast_batch fast_batch;
  * max_queries queries, `threads` host worker threads' CUDA streams (<= 0:
  * 8), and, once run, a CUDA graph of the matcher launch that later runs
  * replay.  cfg (NULL: defaults) seeds every query-size class's configuration
- * (classes: |V(q)| <= 4, 8, 16, 24, 32); cfg->limit and time_budget_s apply
- * to every query of a run.  Uses the current CUDA device.  One call at a
+ * (classes: |V(q)| <= 4, 8, 16, 24, 32); cfg->limit, time_budget_s and
+ * build_rule apply to every query of a run.  FAST_ERR_INVALID for a
+ * build_rule outside 0..2, or a refine_rule other than 0 (or 2 with
+ * build_rule >= 1).  Uses the current CUDA device.  One call at a
  * time per fast_batch (its buffers, graph and per-worker scratch pools are
  * shared by its runs); separate fast_batch objects may run concurrently.
  */
@@ -357,9 +359,10 @@ int fast_batch_create(const fast_graph* g, const fast_config* cfg, int32_t max_q
 
 /*
  * Match nq queries (nq <= max_queries): the worker threads build each
- * query's CST and partition concurrently on their own streams; then one
- * graph-replayed matcher launch enumerates all chunks of all queries, warps
- * sharing work across queries.  counts_out[i] (host) = number of embeddings
+ * query's CST and partition concurrently on their own streams (cfg's
+ * build_rule 1: the CSTs of all queries are built together first, 2: the
+ * partitions too); then one graph-replayed matcher launch enumerates all
+ * chunks of all queries, warps sharing work across queries.  counts_out[i] (host) = number of embeddings
  * of query i (min(total, limit) when cfg->limit > 0); status_out[i] (host) =
  * FAST_OK, the error of that query's CST build or partition (the others
  * still run), or FAST_ERR_TIMEOUT when the time budget ended the launch
