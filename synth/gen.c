@@ -13,6 +13,7 @@
  * count or on the host architecture.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -43,24 +44,52 @@ static inline uint64_t below(uint64_t r, uint64_t n) {
 /* ------------------------------------------------- stable radix sort */
 
 /* Sorts idx[0..n) by key[idx[i]] ascending, stable (ties keep input order).
- * 16-bit digits, passes only over the bits that vary. */
+ * 16-bit digits, passes only over the bits that vary.  Each pass splits the
+ * array into one contiguous range per thread; every thread counts its
+ * digits, the offsets are laid out digit by digit and, within a digit,
+ * thread by thread, and every thread scatters its range in order -- so equal
+ * digits keep their input order and the result does not depend on the
+ * number of threads. */
 static int sort_idx_by_key(const uint64_t* key, uint32_t* idx, int64_t n) {
     if (n <= 1) return 0;
     uint64_t kmax = 0;
+#pragma omp parallel for reduction(| : kmax) schedule(static)
     for (int64_t i = 0; i < n; i++) kmax |= key[i];
     int bits = 0;
     while (bits < 64 && (kmax >> bits)) bits++;
+    int T = omp_get_max_threads();
+    if (T < 1) T = 1;
+    if (T > 64) T = 64;
+    if (n < (int64_t)T * 65536) T = 1;            /* small inputs: one range */
     uint32_t* tmp = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
-    int64_t* cnt = (int64_t*)malloc(65536 * sizeof(int64_t));
+    int64_t* cnt = (int64_t*)malloc((size_t)T * 65536 * sizeof(int64_t));
     if (!tmp || !cnt) { free(tmp); free(cnt); return -1; }
     uint32_t* a = idx; uint32_t* b = tmp;
     for (int sh = 0; sh < bits; sh += 16) {
-        memset(cnt, 0, 65536 * sizeof(int64_t));
-        for (int64_t i = 0; i < n; i++) cnt[(key[a[i]] >> sh) & 0xFFFF]++;
-        int64_t s = 0;
-        for (int d = 0; d < 65536; d++) { int64_t c = cnt[d]; cnt[d] = s; s += c; }
-        for (int64_t i = 0; i < n; i++) b[cnt[(key[a[i]] >> sh) & 0xFFFF]++] = a[i];
-        uint32_t* t = a; a = b; b = t;
+        int used = T;
+#pragma omp parallel num_threads(T)
+        {
+            const int t = omp_get_thread_num(), nt = omp_get_num_threads();
+#pragma omp single
+            used = nt;
+            const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
+            int64_t* c = cnt + (int64_t)t * 65536;
+            memset(c, 0, 65536 * sizeof(int64_t));
+            for (int64_t i = lo; i < hi; i++) c[(key[a[i]] >> sh) & 0xFFFF]++;
+#pragma omp barrier
+#pragma omp single
+            {
+                int64_t s = 0;
+                for (int d = 0; d < 65536; d++)
+                    for (int u = 0; u < used; u++) {
+                        int64_t x = cnt[(int64_t)u * 65536 + d];
+                        cnt[(int64_t)u * 65536 + d] = s;
+                        s += x;
+                    }
+            }
+            for (int64_t i = lo; i < hi; i++) b[c[(key[a[i]] >> sh) & 0xFFFF]++] = a[i];
+        }
+        uint32_t* t2 = a; a = b; b = t2;
     }
     if (a != idx) memcpy(idx, a, (size_t)n * sizeof(uint32_t));
     free(tmp); free(cnt);
@@ -95,10 +124,10 @@ static int unique_edges(edge_fn fn, const void* ctx, int64_t m, int32_t* out /*[
             idx[i] = (uint32_t)i;
         }
         if (sort_idx_by_key(key, idx, cap) != 0) { free(es); free(key); free(idx); free(keep); return -1; }
-        for (int64_t i = 0; i < cap; i++) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < cap; i++) {               /* loops (UINT64_MAX) sort last */
             uint64_t k = key[idx[i]];
-            if (k == UINT64_MAX) break;
-            if (i == 0 || key[idx[i - 1]] != k) keep[idx[i]] = 1;
+            if (k != UINT64_MAX && (i == 0 || key[idx[i - 1]] != k)) keep[idx[i]] = 1;
         }
         int64_t got = 0;
         for (int64_t i = 0; i < cap && got < m; i++)

@@ -363,3 +363,27 @@ def test_labels_bit_exact():
     k6 = _rkey(seed, 6)
     want = [_cdf_pick(cdf, _u01(_rnd(k6, i))) for i in range(n)]
     assert synth.labels_zipf(n, L, seed, s).tolist() == want
+
+
+def test_generators_do_not_depend_on_the_thread_count():
+    """The edge lists (and the walks, whose graph is sorted the same way) come
+    out the same with 1 and with 3 OpenMP threads, on inputs large enough for
+    the sort to split its ranges across threads."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import hashlib, numpy as np, synth\n"
+        "h = lambda a: hashlib.sha1(np.ascontiguousarray(a).tobytes()).hexdigest()\n"
+        "e = synth.chung_lu_edges(200_000, 1_200_000, 2.1, 3)\n"
+        "r = synth.rmat_edges(17, 900_000, 3)\n"
+        "w = synth.WalkGraph(200_000, e).query(synth.labels_zipf(200_000, 8, 3), 8, 'sparse', 3, 1)\n"
+        "print(h(e), h(r), h(w.verts), h(w.edges))\n"
+    )
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for t in ("1", "3"):
+        env = dict(os.environ, OMP_NUM_THREADS=t, PYTHONPATH=root)
+        outs.append(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                                   check=True, timeout=300).stdout)
+    assert outs[0] == outs[1] and outs[0].strip()
