@@ -43,14 +43,14 @@ static inline uint64_t below(uint64_t r, uint64_t n) {
 
 /* ------------------------------------------------- stable radix sort */
 
-/* Sorts idx[0..n) by key[idx[i]] ascending, stable (ties keep input order).
- * 16-bit digits, passes only over the bits that vary.  Each pass splits the
- * array into one contiguous range per thread; every thread counts its
- * digits, the offsets are laid out digit by digit and, within a digit,
- * thread by thread, and every thread scatters its range in order -- so equal
- * digits keep their input order and the result does not depend on the
- * number of threads. */
-static int sort_idx_by_key(const uint64_t* key, uint32_t* idx, int64_t n) {
+/* Sorts key[0..n) ascending and carries val[] along, stable (equal keys
+ * keep their input order).  LSD radix, 16-bit digits, passes only over the
+ * bits that vary.  Each pass splits the arrays into one contiguous range per
+ * thread; every thread counts its digits, the offsets are laid out digit by
+ * digit and, within a digit, thread by thread, and every thread scatters its
+ * range in order -- so the result does not depend on the number of
+ * threads. */
+static int sort_kv(uint64_t* key, uint32_t* val, int64_t n) {
     if (n <= 1) return 0;
     uint64_t kmax = 0;
 #pragma omp parallel for reduction(| : kmax) schedule(static)
@@ -61,10 +61,11 @@ static int sort_idx_by_key(const uint64_t* key, uint32_t* idx, int64_t n) {
     if (T < 1) T = 1;
     if (T > 64) T = 64;
     if (n < (int64_t)T * 65536) T = 1;            /* small inputs: one range */
-    uint32_t* tmp = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
+    uint64_t* tk = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+    uint32_t* tv = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
     int64_t* cnt = (int64_t*)malloc((size_t)T * 65536 * sizeof(int64_t));
-    if (!tmp || !cnt) { free(tmp); free(cnt); return -1; }
-    uint32_t* a = idx; uint32_t* b = tmp;
+    if (!tk || !tv || !cnt) { free(tk); free(tv); free(cnt); return -1; }
+    uint64_t* xk = key; uint32_t* xv = val; uint64_t* yk = tk; uint32_t* yv = tv;
     for (int sh = 0; sh < bits; sh += 16) {
         int used = T;
 #pragma omp parallel num_threads(T)
@@ -75,7 +76,7 @@ static int sort_idx_by_key(const uint64_t* key, uint32_t* idx, int64_t n) {
             const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
             int64_t* c = cnt + (int64_t)t * 65536;
             memset(c, 0, 65536 * sizeof(int64_t));
-            for (int64_t i = lo; i < hi; i++) c[(key[a[i]] >> sh) & 0xFFFF]++;
+            for (int64_t i = lo; i < hi; i++) c[(xk[i] >> sh) & 0xFFFF]++;
 #pragma omp barrier
 #pragma omp single
             {
@@ -87,12 +88,20 @@ static int sort_idx_by_key(const uint64_t* key, uint32_t* idx, int64_t n) {
                         s += x;
                     }
             }
-            for (int64_t i = lo; i < hi; i++) b[c[(key[a[i]] >> sh) & 0xFFFF]++] = a[i];
+            for (int64_t i = lo; i < hi; i++) {
+                int64_t o = c[(xk[i] >> sh) & 0xFFFF]++;
+                yk[o] = xk[i];
+                yv[o] = xv[i];
+            }
         }
-        uint32_t* t2 = a; a = b; b = t2;
+        uint64_t* t1 = xk; xk = yk; yk = t1;
+        uint32_t* t2 = xv; xv = yv; yv = t2;
     }
-    if (a != idx) memcpy(idx, a, (size_t)n * sizeof(uint32_t));
-    free(tmp); free(cnt);
+    if (xk != key) {
+        memcpy(key, xk, (size_t)n * sizeof(uint64_t));
+        memcpy(val, xv, (size_t)n * sizeof(uint32_t));
+    }
+    free(tk); free(tv); free(cnt);
     return 0;
 }
 
@@ -123,11 +132,11 @@ static int unique_edges(edge_fn fn, const void* ctx, int64_t m, int32_t* out /*[
             key[i] = (s == d) ? UINT64_MAX : ((lo << 32) | hi);
             idx[i] = (uint32_t)i;
         }
-        if (sort_idx_by_key(key, idx, cap) != 0) { free(es); free(key); free(idx); free(keep); return -1; }
+        if (sort_kv(key, idx, cap) != 0) { free(es); free(key); free(idx); free(keep); return -1; }
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < cap; i++) {               /* loops (UINT64_MAX) sort last */
-            uint64_t k = key[idx[i]];
-            if (k != UINT64_MAX && (i == 0 || key[idx[i - 1]] != k)) keep[idx[i]] = 1;
+            uint64_t k = key[i];
+            if (k != UINT64_MAX && (i == 0 || key[i - 1] != k)) keep[idx[i]] = 1;   /* first occurrence */
         }
         int64_t got = 0;
         for (int64_t i = 0; i < cap && got < m; i++)
@@ -279,43 +288,107 @@ static int pair_present(const walk_graph* g, int32_t a, int32_t b) {
     return l < g->nkeys && g->keys[l] == k;
 }
 
+/* Sorts the values a[0..n) ascending in place (LSD radix, 16-bit digits,
+ * only the bits that vary; per-thread ranges as in sort_kv). */
+static int sort_u64(uint64_t* a, int64_t n) {
+    if (n <= 1) return 0;
+    uint64_t kmax = 0;
+#pragma omp parallel for reduction(| : kmax) schedule(static)
+    for (int64_t i = 0; i < n; i++) kmax |= a[i];
+    int bits = 0;
+    while (bits < 64 && (kmax >> bits)) bits++;
+    int T = omp_get_max_threads();
+    if (T < 1) T = 1;
+    if (T > 64) T = 64;
+    if (n < (int64_t)T * 65536) T = 1;
+    uint64_t* tmp = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+    int64_t* cnt = (int64_t*)malloc((size_t)T * 65536 * sizeof(int64_t));
+    if (!tmp || !cnt) { free(tmp); free(cnt); return -1; }
+    uint64_t* x = a; uint64_t* y = tmp;
+    for (int sh = 0; sh < bits; sh += 16) {
+        int used = T;
+#pragma omp parallel num_threads(T)
+        {
+            const int t = omp_get_thread_num(), nt = omp_get_num_threads();
+#pragma omp single
+            used = nt;
+            const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
+            int64_t* c = cnt + (int64_t)t * 65536;
+            memset(c, 0, 65536 * sizeof(int64_t));
+            for (int64_t i = lo; i < hi; i++) c[(x[i] >> sh) & 0xFFFF]++;
+#pragma omp barrier
+#pragma omp single
+            {
+                int64_t s = 0;
+                for (int d = 0; d < 65536; d++)
+                    for (int u = 0; u < used; u++) {
+                        int64_t v = cnt[(int64_t)u * 65536 + d];
+                        cnt[(int64_t)u * 65536 + d] = s;
+                        s += v;
+                    }
+            }
+            for (int64_t i = lo; i < hi; i++) y[c[(x[i] >> sh) & 0xFFFF]++] = x[i];
+        }
+        uint64_t* t2 = x; x = y; y = t2;
+    }
+    if (x != a) memcpy(a, x, (size_t)n * sizeof(uint64_t));
+    free(tmp); free(cnt);
+    return 0;
+}
+
 void* synth_walk_graph_new(int64_t n, int64_t m, const int32_t* edges) {
     walk_graph* g = (walk_graph*)calloc(1, sizeof(walk_graph));
     if (!g) return NULL;
     g->n = n;
     g->off = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));
     uint64_t* key = (uint64_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(uint64_t));
-    uint32_t* idx = (uint32_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(uint32_t));
-    if (!g->off || !key || !idx) { free(key); free(idx); free(g->off); free(g); return NULL; }
+    if (!g->off || !key) { free(key); free(g->off); free(g); return NULL; }
+    /* distinct unordered pairs (lo << 32 | hi), ascending; loops dropped */
     int64_t nk = 0;
     for (int64_t e = 0; e < m; e++) {
         int32_t s = edges[2 * e], d = edges[2 * e + 1];
         if (s == d) continue;
         uint64_t lo = (uint64_t)(s < d ? s : d), hi = (uint64_t)(s < d ? d : s);
-        key[nk] = (lo << 32) | hi; idx[nk] = (uint32_t)nk; nk++;
+        key[nk++] = (lo << 32) | hi;
     }
-    sort_idx_by_key(key, idx, nk);
-    g->keys = (uint64_t*)malloc((size_t)(nk > 0 ? nk : 1) * sizeof(uint64_t));
+    if (sort_u64(key, nk) != 0) { free(key); free(g->off); free(g); return NULL; }
     int64_t u = 0;
-    for (int64_t i = 0; i < nk; i++) {
-        uint64_t k = key[idx[i]];
-        if (u == 0 || g->keys[u - 1] != k) g->keys[u++] = k;
-    }
+    for (int64_t i = 0; i < nk; i++)
+        if (u == 0 || key[u - 1] != key[i]) key[u++] = key[i];
+    g->keys = key;
     g->nkeys = u;
-    free(key); free(idx);
-    for (int64_t i = 0; i < u; i++) {
-        g->off[(g->keys[i] >> 32) + 1]++;
-        g->off[(g->keys[i] & 0xFFFFFFFFu) + 1]++;
+    /* Row v holds its smaller neighbours (pairs (lo, v), ascending lo) and
+     * then its larger ones (its own run of pairs (v, hi), ascending hi): the
+     * same rows a fill in key order gives.  The smaller ones come from the
+     * pairs sorted by (hi, lo). */
+    uint64_t* sw = (uint64_t*)malloc((size_t)(u > 0 ? u : 1) * sizeof(uint64_t));
+    int64_t* nlo = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));   /* pairs with lo = v */
+    int64_t* nhi = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));   /* pairs with hi = v */
+    if (!sw || !nlo || !nhi) { free(sw); free(nlo); free(nhi); free(key); free(g->off); free(g); return NULL; }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < u; i++) sw[i] = (key[i] << 32) | (key[i] >> 32);
+    if (sort_u64(sw, u) != 0) { free(sw); free(nlo); free(nhi); free(key); free(g->off); free(g); return NULL; }
+    for (int64_t i = 0; i < u; i++) { nlo[key[i] >> 32]++; nhi[sw[i] >> 32]++; }
+    /* offsets, and where each row's run starts in key[] and in sw[] */
+    int64_t* slo = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t* shi = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
+    if (!slo || !shi) { free(slo); free(shi); free(sw); free(nlo); free(nhi); free(key); free(g->off); free(g); return NULL; }
+    int64_t ol = 0, oh = 0;
+    for (int64_t v = 0; v < n; v++) {
+        slo[v] = ol; shi[v] = oh;
+        ol += nlo[v]; oh += nhi[v];
+        g->off[v + 1] = g->off[v] + nlo[v] + nhi[v];
     }
-    for (int64_t v = 0; v < n; v++) g->off[v + 1] += g->off[v];
     g->nbr = (int32_t*)malloc((size_t)(g->off[n] > 0 ? g->off[n] : 1) * sizeof(int32_t));
-    int64_t* cur = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
-    memcpy(cur, g->off, (size_t)(n + 1) * sizeof(int64_t));
+    if (!g->nbr) { free(slo); free(shi); free(sw); free(nlo); free(nhi); free(key); free(g->off); free(g); return NULL; }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < u; i++) {
-        int32_t a = (int32_t)(g->keys[i] >> 32), b = (int32_t)(g->keys[i] & 0xFFFFFFFFu);
-        g->nbr[cur[a]++] = b; g->nbr[cur[b]++] = a;
+        int64_t v = (int64_t)(sw[i] >> 32);                        /* pair (lo, v): v's smaller neighbour */
+        g->nbr[g->off[v] + (i - shi[v])] = (int32_t)(sw[i] & 0xFFFFFFFFu);
+        int64_t w = (int64_t)(key[i] >> 32);                       /* pair (w, hi): w's larger neighbour */
+        g->nbr[g->off[w] + nhi[w] + (i - slo[w])] = (int32_t)(key[i] & 0xFFFFFFFFu);
     }
-    free(cur);
+    free(slo); free(shi); free(sw); free(nlo); free(nhi);
     return g;
 }
 
