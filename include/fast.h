@@ -310,9 +310,13 @@ void fast_free_chunks(fast_chunks* ch);
  * (Synchronizer).  The Generator may scan whichever of those lists is
  * shortest (their intersection is the same set).
  *   k:           embeddings to write (0: count only).
- *   emb_out:     device buffer of k rows x |V(q)| uint32 data-vertex ids,
- *                column u = M(u) (query vertex id order); any k embeddings
- *                of the enumerated set, each once.  NULL iff k == 0.
+ *   emb_out:     k rows x |V(q)| uint32 data-vertex ids, column u = M(u)
+ *                (query vertex id order); any k embeddings of the
+ *                enumerated set, each once.  NULL iff k == 0.  Device (or
+ *                managed) memory is written by the kernel directly; any
+ *                other pointer is taken as host memory: the rows go to a
+ *                library-owned device buffer of min(k, limit) rows first
+ *                and are copied to emb_out before the call returns.
  *   count_out:   host; total number of embeddings in the chunks.
  *   written_out: host; rows written = min(k, count).
  *   chunk_counts: optional device buffer of one uint64 per chunk.

@@ -459,19 +459,9 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         for (int u = 0; u < k; u++) c0[u] = (int64_t)hc[u];
 
         // ------------------------------------------------- root and t_q
-        int r = 0;
-        for (int u = 1; u < k; u++)
-            if ((unsigned __int128)c0[u] * (unsigned)dq[r] < (unsigned __int128)c0[r] * (unsigned)dq[u]) r = u;
+        const int r = choose_root(k, c0, dq);
         c->root = r;
-        {
-            int seen[kMaxK] = {0}, qh = 0, qt = 0;
-            c->bfs[qt++] = r; seen[r] = 1; c->parent[r] = -1;
-            while (qh < qt) {
-                int u = c->bfs[qh++];
-                for (int w = 0; w < k; w++)
-                    if (A[u][w] && !seen[w]) { seen[w] = 1; c->parent[w] = u; c->bfs[qt++] = w; }
-            }
-        }
+        bfs_tree(k, A, r, c->bfs, c->parent);
         cap_c[r] = c0[r];
 
         // ------------------------------------------------ C(root) = C0(root)
@@ -589,79 +579,37 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         }
 
         // ------------------------------------------------ matching order
-        if (c->cfg.order_rule == 1) {
-            // greedy: the unplaced vertex whose t_q parent is placed, with the
-            // most query edges to placed vertices (then fewer candidates, then id)
-            bool placed[kMaxK] = {false};
-            c->order[0] = r;
-            placed[r] = true;
-            for (int no = 1; no < k; no++) {
-                int best = -1, bb = -1;
-                for (int u = 0; u < k; u++) {
-                    if (placed[u] || !placed[c->parent[u]]) continue;
-                    int b = 0;
-                    for (int w = 0; w < k; w++) b += (placed[w] && A[u][w]) ? 1 : 0;
-                    if (best < 0 || b > bb ||
-                        (b == bb && (c->ncand[u] < c->ncand[best] || (c->ncand[u] == c->ncand[best] && u < best)))) {
-                        best = u;
-                        bb = b;
-                    }
-                }
-                c->order[no] = best;
-                placed[best] = true;
-            }
-            for (int i = 0; i < k; i++) c->pos[c->order[i]] = i;
-        } else {
-            int stack[kMaxK], sp = 0, no = 0;
-            stack[sp++] = r;
-            while (sp) {
-                int u = stack[--sp];
-                c->order[no++] = u;
-                int chl[kMaxK], nc = 0;
-                for (int w = 0; w < k; w++) if (c->parent[w] == u) chl[nc++] = w;
-                std::sort(chl, chl + nc, [&](int a, int b) {
-                    return c->ncand[a] != c->ncand[b] ? c->ncand[a] < c->ncand[b] : a < b;
-                });
-                for (int i = nc - 1; i >= 0; i--) stack[sp++] = chl[i];
-            }
-            for (int i = 0; i < k; i++) c->pos[c->order[i]] = i;
-        }
+        matching_order(k, A, r, c->parent, c->ncand, c->cfg.order_rule, c->order, c->pos);
 
         // ------------------------------------------------------ non-tree
-        c->nnt = 0;
-        for (int i = 0; i < k && rc == FAST_OK; i++) {
-            int ui = c->order[i];
-            for (int j = 0; j < i && rc == FAST_OK; j++) {
-                int uj = c->order[j];
-                if (!A[ui][uj] || c->parent[ui] == uj || c->parent[uj] == ui) continue;
-                int e = c->nnt++;
-                c->nt_from[e] = uj; c->nt_to[e] = ui;
-                int64_t rows = c->ncand[uj];
-                rc = dalloc(&e_off, rows + 1, s); if (rc) break;
-                rc = dalloc(&seg, rows, s); if (rc) break;
-                if (rows > 0) {
-                    k_cand_segment<<<grid_for(rows, 256), 256, 0, s>>>(c->cand[uj], rows, G, q->labels[ui], seg, e_off);
-                    note_launch();
-                }
-                rc = scan_exclusive<int64_t>(e_off, e_off, rows, e_off + rows, s); if (rc) break;
-                int64_t E = degsum(q->labels[uj]);
-                if (E > kBoundedListCap) {
-                    if (cudaMemcpyAsync(&E, e_off + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                        cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "edge space size"); break; }
-                }
-                rc = dalloc(&c->n_off[e], rows + 1, s); if (rc) break;
-                rc = dalloc(&c->n_idx[e], E, s); if (rc) break;
-                NonTreeF f{};
-                f.e_off = e_off; f.rows = rows; f.seg = seg; f.col = g->col;
-                f.alive = bits[ui].alive; f.rank = bits[ui].rank; f.n_off = c->n_off[e];
-                f.E = e_off + rows;
-                int64_t* kept = sz + 3 * kMaxK + e;
-                rc = compact(f, E, c->n_idx[e], kept, s); if (rc) break;
-                k_fill_tail<<<grid_for(rows + 1, 256), 256, 0, s>>>(e_off, nullptr, rows, rows, kept, c->n_off[e]);
+        c->nnt = nontree_edges(k, A, c->order, c->parent, c->nt_from, c->nt_to);
+        for (int e = 0; e < c->nnt && rc == FAST_OK; e++) {
+            const int ui = c->nt_to[e], uj = c->nt_from[e];
+            int64_t rows = c->ncand[uj];
+            rc = dalloc(&e_off, rows + 1, s); if (rc) break;
+            rc = dalloc(&seg, rows, s); if (rc) break;
+            if (rows > 0) {
+                k_cand_segment<<<grid_for(rows, 256), 256, 0, s>>>(c->cand[uj], rows, G, q->labels[ui], seg, e_off);
                 note_launch();
-                dfree(e_off, s);
-                dfree(seg, s);
             }
+            rc = scan_exclusive<int64_t>(e_off, e_off, rows, e_off + rows, s); if (rc) break;
+            int64_t E = degsum(q->labels[uj]);
+            if (E > kBoundedListCap) {
+                if (cudaMemcpyAsync(&E, e_off + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(FAST_ERR_CUDA, "edge space size"); break; }
+            }
+            rc = dalloc(&c->n_off[e], rows + 1, s); if (rc) break;
+            rc = dalloc(&c->n_idx[e], E, s); if (rc) break;
+            NonTreeF f{};
+            f.e_off = e_off; f.rows = rows; f.seg = seg; f.col = g->col;
+            f.alive = bits[ui].alive; f.rank = bits[ui].rank; f.n_off = c->n_off[e];
+            f.E = e_off + rows;
+            int64_t* kept = sz + 3 * kMaxK + e;
+            rc = compact(f, E, c->n_idx[e], kept, s); if (rc) break;
+            k_fill_tail<<<grid_for(rows + 1, 256), 256, 0, s>>>(e_off, nullptr, rows, rows, kept, c->n_off[e]);
+            note_launch();
+            dfree(e_off, s);
+            dfree(seg, s);
         }
         if (rc) break;
 

@@ -495,57 +495,11 @@ struct Q {
     int64_t* seg = nullptr;
 };
 
-// Matching order of one query from its refined candidate counts (the same
-// rules as the per-query build: path-based by default, greedy with
-// order_rule 1).
-void matching_order(const Q& q, fast_cst* c) {
-    const int k = q.k, r = c->root;
-    if (c->cfg.order_rule == 1) {
-        bool placed[kMaxK] = {false};
-        c->order[0] = r;
-        placed[r] = true;
-        for (int no = 1; no < k; no++) {
-            int best = -1, bb = -1;
-            for (int u = 0; u < k; u++) {
-                if (placed[u] || !placed[c->parent[u]]) continue;
-                int b = 0;
-                for (int w = 0; w < k; w++) b += (placed[w] && q.A[u][w]) ? 1 : 0;
-                if (best < 0 || b > bb ||
-                    (b == bb && (c->ncand[u] < c->ncand[best] || (c->ncand[u] == c->ncand[best] && u < best)))) {
-                    best = u;
-                    bb = b;
-                }
-            }
-            c->order[no] = best;
-            placed[best] = true;
-        }
-    } else {
-        int stack[kMaxK], sp = 0, no = 0;
-        stack[sp++] = r;
-        while (sp) {
-            int u = stack[--sp];
-            c->order[no++] = u;
-            int chl[kMaxK], nc = 0;
-            for (int w = 0; w < k; w++) if (c->parent[w] == u) chl[nc++] = w;
-            std::sort(chl, chl + nc, [&](int a, int b) {
-                return c->ncand[a] != c->ncand[b] ? c->ncand[a] < c->ncand[b] : a < b;
-            });
-            for (int i = nc - 1; i >= 0; i--) stack[sp++] = chl[i];
-        }
-    }
-    for (int i = 0; i < k; i++) c->pos[c->order[i]] = i;
-    // non-tree edges, earlier -> later in the order
-    c->nnt = 0;
-    for (int i = 0; i < k; i++) {
-        const int ui = c->order[i];
-        for (int j = 0; j < i; j++) {
-            const int uj = c->order[j];
-            if (!q.A[ui][uj] || c->parent[ui] == uj || c->parent[uj] == ui) continue;
-            const int e = c->nnt++;
-            c->nt_from[e] = uj;
-            c->nt_to[e] = ui;
-        }
-    }
+// Matching order and non-tree edges of one query from its refined candidate
+// counts, by the rules the per-query build uses.
+void order_and_nontree(const Q& q, fast_cst* c) {
+    fast::matching_order(q.k, q.A, c->root, c->parent, c->ncand, c->cfg.order_rule, c->order, c->pos);
+    c->nnt = nontree_edges(q.k, q.A, c->order, c->parent, c->nt_from, c->nt_to);
 }
 
 int fetch(const int64_t* d, std::vector<int64_t>& h, size_t words, cudaStream_t s) {
@@ -686,19 +640,9 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
         fast_cst* c = q.c;
         const int k = q.k;
         for (int u = 0; u < k; u++) q.c0[u] = h[(size_t)u * nq + qi];
-        int r = 0;
-        for (int u = 1; u < k; u++)
-            if ((unsigned __int128)q.c0[u] * (unsigned)q.dq[r] < (unsigned __int128)q.c0[r] * (unsigned)q.dq[u]) r = u;
+        const int r = choose_root(k, q.c0, q.dq);
         c->root = r;
-        int seen[kMaxK] = {0}, qh = 0, qt = 0;
-        c->bfs[qt++] = r;
-        seen[r] = 1;
-        c->parent[r] = -1;
-        while (qh < qt) {
-            int u = c->bfs[qh++];
-            for (int w = 0; w < k; w++)
-                if (q.A[u][w] && !seen[w]) { seen[w] = 1; c->parent[w] = u; c->bfs[qt++] = w; }
-        }
+        bfs_tree(k, q.A, r, c->bfs, c->parent);
         for (int t = 0; t < k; t++) q.bpos[c->bfs[t]] = t;
     }
 
@@ -1037,7 +981,7 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
             c->ncand[u] = h[(size_t)t * nq + qi];
             c->t_entries[u] = c->parent[u] < 0 ? 0 : h[(size_t)(kMaxK + t) * nq + qi];
         }
-        matching_order(q, c);
+        order_and_nontree(q, c);
     }
 
     // ------------------------------------------------------ non-tree

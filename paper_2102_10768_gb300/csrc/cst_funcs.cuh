@@ -272,6 +272,98 @@ inline int validate_query(const fast_query_desc* q, int A[kMaxK][kMaxK], int* dq
     return FAST_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Host rules of query preparation, shared by the per-query and the batched
+// builds (Sec. IV-A and IV-B; the tie-breaks the paper leaves open are fixed
+// here once).
+
+// Root of t_q: argmin |C0(u)| / d_q(u), compared exactly by cross
+// multiplication; ties go to the smaller id.
+inline int choose_root(int k, const int64_t* c0, const int* dq) {
+    int r = 0;
+    for (int u = 1; u < k; u++)
+        if ((unsigned __int128)c0[u] * (unsigned)dq[r] < (unsigned __int128)c0[r] * (unsigned)dq[u]) r = u;
+    return r;
+}
+
+// BFS tree t_q from r, neighbours visited in increasing id: bfs[] is the
+// visiting order, parent[r] = -1.
+inline void bfs_tree(int k, const int A[kMaxK][kMaxK], int r, int* bfs, int* parent) {
+    int seen[kMaxK] = {0}, qh = 0, qt = 0;
+    bfs[qt++] = r;
+    seen[r] = 1;
+    parent[r] = -1;
+    while (qh < qt) {
+        const int u = bfs[qh++];
+        for (int w = 0; w < k; w++)
+            if (A[u][w] && !seen[w]) { seen[w] = 1; parent[w] = u; bfs[qt++] = w; }
+    }
+}
+
+// Matching order from the refined candidate counts.  rule 0 (path-based):
+// depth-first preorder of t_q, children by increasing (|C|, id), so whole
+// root-to-leaf paths come in turn.  rule 1 (greedy): after the root, the
+// unplaced vertex whose t_q parent is placed with the most query edges to
+// placed vertices; ties to the smaller |C|, then the smaller id.  Writes
+// order[position] and pos[vertex].
+inline void matching_order(int k, const int A[kMaxK][kMaxK], int r, const int* parent, const int64_t* ncand, int rule,
+                           int* order, int* pos) {
+    if (rule == 1) {
+        bool placed[kMaxK] = {false};
+        order[0] = r;
+        placed[r] = true;
+        for (int no = 1; no < k; no++) {
+            int best = -1, bb = -1;
+            for (int u = 0; u < k; u++) {
+                if (placed[u] || !placed[parent[u]]) continue;
+                int b = 0;
+                for (int w = 0; w < k; w++) b += (placed[w] && A[u][w]) ? 1 : 0;
+                if (best < 0 || b > bb || (b == bb && (ncand[u] < ncand[best] || (ncand[u] == ncand[best] && u < best)))) {
+                    best = u;
+                    bb = b;
+                }
+            }
+            order[no] = best;
+            placed[best] = true;
+        }
+    } else {
+        int stack[kMaxK], sp = 0, no = 0;
+        stack[sp++] = r;
+        while (sp) {
+            const int u = stack[--sp];
+            order[no++] = u;
+            int chl[kMaxK], nc = 0;
+            for (int w = 0; w < k; w++) if (parent[w] == u) chl[nc++] = w;
+            for (int i = 1; i < nc; i++)                  // insertion sort by (|C|, id)
+                for (int j = i; j > 0; j--) {
+                    const int a = chl[j - 1], b = chl[j];
+                    if (ncand[b] < ncand[a] || (ncand[b] == ncand[a] && b < a)) { chl[j - 1] = b; chl[j] = a; }
+                    else break;
+                }
+            for (int i = nc - 1; i >= 0; i--) stack[sp++] = chl[i];
+        }
+    }
+    for (int i = 0; i < k; i++) pos[order[i]] = i;
+}
+
+// Non-tree edges of q, each once, from the earlier to the later endpoint in
+// the order, listed by the later endpoint's position, then the earlier's.
+// Returns their number.
+inline int nontree_edges(int k, const int A[kMaxK][kMaxK], const int* order, const int* parent, int* from, int* to) {
+    int n = 0;
+    for (int i = 0; i < k; i++) {
+        const int ui = order[i];
+        for (int j = 0; j < i; j++) {
+            const int uj = order[j];
+            if (!A[ui][uj] || parent[ui] == uj || parent[uj] == ui) continue;
+            from[n] = uj;
+            to[n] = ui;
+            n++;
+        }
+    }
+    return n;
+}
+
 // One flat copy list: descriptor d moves bytes [0, n_d) from src_d to dst_d;
 // piece_off[d] is the first 64 KB piece of d in a flat piece space.
 struct CopyDesc {

@@ -7,10 +7,7 @@ from the allocation call; no test faults, traps or hangs the GPU.
 
 Each sweep fails allocation n of one pipeline for n = 0, 1, 2, ... until the
 pipeline gets through without reaching the injected failure.
-
-Opt-in (FAST_FAULT_INJECTION=1) until these tests have run on the hardware.
 """
-import os
 
 import numpy as np
 import pytest
@@ -21,7 +18,6 @@ import synth
 
 pytestmark = [
     pytest.mark.gpu,
-    pytest.mark.skipif(not os.environ.get("FAST_FAULT_INJECTION"), reason="failure injection: set FAST_FAULT_INJECTION=1"),
 ]
 
 LIMIT = 5000

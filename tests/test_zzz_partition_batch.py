@@ -6,10 +6,7 @@ and in order, what fast_partition gives for it with the same configuration
 max_chunks cap hit or not, with sampling, with CSTs of no embedding, and
 with a NULL CST reported per entry.  Matching over the batched chunks gives
 the same counts.
-
-Opt-in (FAST_PARTITION_BATCH=1) until these tests have run on the hardware.
 """
-import os
 
 import numpy as np
 import pytest
@@ -19,8 +16,6 @@ import synth
 
 pytestmark = [
     pytest.mark.gpu,
-    pytest.mark.skipif(not os.environ.get("FAST_PARTITION_BATCH"),
-                       reason="batched partition: set FAST_PARTITION_BATCH=1"),
 ]
 
 
@@ -56,7 +51,8 @@ def check(csts, cfg):
         assert ch.n == want.n
         assert ch.copy() == want.copy()
         assert ch.w_sum == want.w_sum
-        assert F.match(c, ch)["count"] == F.match(c, want)["count"]
+        mc = F.default_config(limit=1 << 20)
+        assert F.match(c, ch, cfg=mc)["count"] == F.match(c, want, cfg=mc)["count"]
         want.close()
         ch.close()
 

@@ -2,10 +2,7 @@
 the batched CST build, against the oracle's restatement of the same rule:
 every CST array, in both orders and under both filters, and the same
 embedding counts as the paper's single pass.
-
-Opt-in (FAST_REFINE=1) until these tests have run on the hardware.
 """
-import os
 
 import numpy as np
 import pytest
@@ -17,7 +14,6 @@ from helpers import compare_cst
 
 pytestmark = [
     pytest.mark.gpu,
-    pytest.mark.skipif(not os.environ.get("FAST_REFINE"), reason="refine rule 2: set FAST_REFINE=1"),
 ]
 
 RULES = [dict(), dict(order_rule=1), dict(filter_rule=1), dict(order_rule=1, filter_rule=1)]
