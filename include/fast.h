@@ -411,21 +411,25 @@ typedef struct {
                                 request's projected bytes exceed the whole budget */
     int32_t pad;
     uint64_t t_arrive_ns;    /* submitted */
-    uint64_t t_start_ns;     /* admitted by a worker */
+    uint64_t t_start_ns;     /* admitted into a group */
     uint64_t t_done_ns;      /* count known */
 } fast_result;
 
 /*
  * A request loop over the resident data graph g (the host/accelerator task
- * flow of Sec. IV, kept on one GPU): requests wait in a FIFO queue; each of
- * `workers` host threads (<= 0: 4), with its own CUDA stream, takes the head
- * request when its projected device bytes -- label buckets and neighbour
- * lists its CST can hold, plus the matcher's scratch -- fit in what
- * budget_bytes leaves (a request is always admitted when nothing runs), then
- * builds its CST, partitions it and matches it with cfg (NULL: defaults;
- * blocks_per_sm sizes each matcher launch, so 1 lets about four launches
- * share the GPU).  Requests arriving while others run are admitted as
- * workers and memory free up; their kernels overlap on the device.
+ * flow of Sec. IV, kept on one GPU) with continuous batching: requests wait
+ * in a FIFO queue; each of `workers` group workers (<= 0: 2), with its own
+ * CUDA stream and its own batch (as fast_batch_create with cfg, up to 1024
+ * requests), takes every request at the head of the queue whose projected
+ * device bytes -- label buckets and neighbour lists its CST can hold, plus
+ * the matcher's scratch -- fit in what budget_bytes leaves (the head
+ * request is always admitted when nothing runs) and runs them as one batch:
+ * their CSTs and partitions are built together (cfg->build_rule) and one
+ * matcher launch (cfg->warps_per_block x cfg->blocks_per_sm per SM)
+ * enumerates all of them.  Requests arriving while a group is on the GPU
+ * form the next group; with two or more workers one group's build overlaps
+ * another's matcher on the device.  cfg NULL: defaults.  Errors as
+ * fast_batch_create.
  */
 int fast_server_create(const fast_graph* g, const fast_config* cfg, uint64_t budget_bytes, int32_t workers,
                        fast_server** out);
@@ -445,6 +449,9 @@ int fast_server_poll(fast_server* s, int32_t max_results, fast_result* out, int3
 
 /* Requests queued, requests running, projected bytes admitted. */
 int fast_server_stats(fast_server* s, int64_t* pending, int64_t* running, uint64_t* in_use_bytes);
+
+/* Groups formed so far and the requests they held (their mean size). */
+int fast_server_groups(fast_server* s, uint64_t* groups, uint64_t* requests);
 
 /* Stop: requests still queued are dropped, running ones finish. */
 void fast_server_destroy(fast_server* s);

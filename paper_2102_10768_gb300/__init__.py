@@ -93,6 +93,7 @@ _SIGS = {
     "fast_server_create": (ctypes.c_int, [_vp, _vp, _u64, _i32, _vp]),
     "fast_server_submit": (ctypes.c_int, [_vp, _vp, _vp]),
     "fast_server_poll": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32]),
+    "fast_server_groups": (ctypes.c_int, [_vp, _vp, _vp]),
     "fast_server_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "fast_server_destroy": (None, [_vp]),
     "fast_now_ns": (ctypes.c_uint64, []),
@@ -519,6 +520,12 @@ class Server:
         p, r, b = _i64(), _i64(), _u64()
         _check(lib().fast_server_stats(self._h, ctypes.byref(p), ctypes.byref(r), ctypes.byref(b)))
         return {"pending": p.value, "running": r.value, "in_use_bytes": b.value}
+
+    def groups(self):
+        """(groups formed, requests they held)."""
+        gr, rq = _u64(), _u64()
+        _check(lib().fast_server_groups(self._h, ctypes.byref(gr), ctypes.byref(rq)))
+        return gr.value, rq.value
 
     def close(self):
         if getattr(self, "_h", None):

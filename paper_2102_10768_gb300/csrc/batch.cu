@@ -82,6 +82,7 @@ struct fast_batch {
     uint64_t g_limit = ~0ull;
     uint64_t g_cells = 0;
     unsigned char* g_chunks = nullptr;
+    int g_kernels = 0;                    // kernels in the captured graph (launched per replay)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<ScratchPool*> pools;      // per build thread: scratch of its CSTs and partitions
     double last_build_ms = 0.0, last_match_ms = 0.0;
@@ -200,12 +201,22 @@ int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream
         e = cudaGraphInstantiate(&b->exec, graph, 0);
         if (e != cudaSuccess) rc = cuda_status(e, "graph instantiate", __FILE__, __LINE__);
     }
+    // the enqueue counted each kernel it recorded (one graph node each);
+    // they run, and are counted, at each replay instead
+    size_t nodes = 0;
+    if (rc == FAST_OK && cudaGraphGetNodes(graph, nullptr, &nodes) != cudaSuccess) {
+        cudaGetLastError();
+        nodes = 0;
+    }
+    const int recorded = (int)nodes;
+    note_launch(-recorded);
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cap);
     (void)s;
     if (rc == FAST_OK) {
         b->g_warp_words = warp_words; b->g_warps = lc.warps_per_block; b->g_bps = lc.blocks_per_sm;
         b->g_budget = lc.time_budget_s; b->g_limit = lc.limit; b->g_chunks = b->d_chunks; b->g_cells = cells;
+        b->g_kernels = recorded;
     }
     return rc;
 }
@@ -325,6 +336,7 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
         rc = batch_graph(b, warp_words, lc, s); if (rc) break;
         FAST_CUDA_BREAK(rc, cudaEventRecord(b->ev0, s));
         FAST_CUDA_BREAK(rc, cudaGraphLaunch(b->exec, s));
+        note_launch(b->g_kernels);            // the kernels the graph holds, matcher included
         FAST_CUDA_BREAK(rc, cudaEventRecord(b->ev1, s));
         if (nq > 0) FAST_CUDA_BREAK(rc, cudaMemcpyAsync(b->h_qtotal, b->d_qtotal, (size_t)nq * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         FAST_CUDA_BREAK(rc, cudaMemcpyAsync(b->h_ctr, b->d_ctr, match_counter_words() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));

@@ -1,15 +1,20 @@
 // Serving: a request loop over a resident data graph with continuous
 // batching.
 //
-// Requests enter a FIFO queue.  Worker threads, each with its own CUDA
-// stream, take the head request as soon as they are free and the request's
-// projected device bytes fit in what the budget has left (admission); they
-// build its CST (Alg. 1), partition it (Alg. 2) and launch the matcher on
-// their own stream.  Requests that arrive while others run are admitted as
-// workers and memory free up, and their kernels overlap on the device with
-// the ones already running (each matcher launch takes a share of the SMs, so
-// several run at once).  Every result carries its arrival, start and finish
-// times on one steady clock, from which the caller reads latency.
+// Requests enter a FIFO queue.  Each of a few group workers, with its own
+// CUDA stream and its own batch (fixed device buffers and a captured matcher
+// launch, batch.cu), repeatedly takes every request at the head of the queue
+// whose projected device bytes still fit in what the budget has left
+// (admission), up to a group cap, and runs them as one batch: their CSTs
+// (Alg. 1) and partitions (Alg. 2) are built together and one matcher launch
+// enumerates all of their chunks, warps stealing work across the requests.
+// Requests that arrive while a group is on the GPU form the next group and
+// are admitted as soon as a worker and memory free up; with two or more
+// workers one group's build overlaps another's matcher on the device.  At
+// low load a group is a single request, which then has the whole GPU; under
+// load the groups grow and the loop reaches the batched throughput.  Every
+// result carries its arrival, admission and finish times on one steady
+// clock, from which the caller reads latency.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -54,6 +59,9 @@ struct fast_server {
     bool stop = false;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
+    std::vector<fast_batch*> batches;    // one per worker: a group's buffers and captured launch
+    int group_cap = 1024;                // requests per group
+    uint64_t groups = 0, grouped = 0;    // groups formed, requests in them
     std::vector<double> label_deg;       // mean degree of the vertices of each label
 };
 
@@ -85,11 +93,19 @@ uint64_t projected_bytes(const fast_server* S, const Req& r) {
     return (uint64_t)b;
 }
 
+// One group worker: take the admissible head of the queue, run it as one
+// batch, report every request of it.
 void worker_main(fast_server* S, int w) {
     cudaSetDevice(S->device);
     cudaStream_t st = S->streams[w];
+    fast_batch* b = S->batches[w];
+    std::vector<Req> grp;
+    std::vector<fast_query_desc> qd;
+    std::vector<uint64_t> counts;
+    std::vector<int32_t> status;
     for (;;) {
-        Req r;
+        grp.clear();
+        uint64_t t_start = 0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv.wait(lk, [&] {
@@ -100,47 +116,59 @@ void worker_main(fast_server* S, int w) {
                        h.projected > S->budget;
             });
             if (S->stop) return;                 // requests not yet started are dropped
-            if (S->pending.empty()) continue;
-            r = std::move(S->pending.front());
-            S->pending.pop_front();
-            if (r.projected > S->budget) {
-                fast_result res;
-                memset(&res, 0, sizeof(res));
-                res.id = r.id; res.status = FAST_ERR_OOM;
-                res.t_arrive_ns = r.t_arrive; res.t_start_ns = res.t_done_ns = now_ns();
-                S->done.push_back(res);
-                S->cv.notify_all();
-                continue;
+            t_start = now_ns();
+            // the admissible head of the queue, in order: a request beyond the
+            // whole budget is answered at once; the group stops at the first
+            // request that does not fit in what is left (FIFO), or at the cap
+            while (!S->pending.empty() && (int)grp.size() < S->group_cap) {
+                Req& h = S->pending.front();
+                if (h.projected > S->budget) {
+                    fast_result res;
+                    memset(&res, 0, sizeof(res));
+                    res.id = h.id; res.status = FAST_ERR_OOM;
+                    res.t_arrive_ns = h.t_arrive; res.t_start_ns = res.t_done_ns = now_ns();
+                    S->done.push_back(res);
+                    S->pending.pop_front();
+                    continue;
+                }
+                const bool idle = S->running == 0 && grp.empty();
+                if (!idle && h.projected > S->budget - std::min(S->budget, S->in_use)) break;
+                S->in_use += h.projected;
+                S->running++;
+                grp.push_back(std::move(h));
+                S->pending.pop_front();
             }
-            S->in_use += r.projected;
-            S->running++;
+            if (!grp.empty()) { S->groups++; S->grouped += grp.size(); }
         }
-        fast_result res;
-        memset(&res, 0, sizeof(res));
-        res.id = r.id;
-        res.t_arrive_ns = r.t_arrive;
-        res.t_start_ns = now_ns();
-        fast_query_desc q;
-        q.n = (int32_t)r.labels.size();
-        q.m = (int32_t)(r.edges.size() / 2);
-        q.labels = r.labels.data();
-        q.edges = r.edges.data();
-        fast_cst* c = nullptr;
-        fast_chunks* ch = nullptr;
-        uint64_t count = 0;
-        int rc = fast_build_cst(S->g, &q, &S->cfg, st, &c);
-        if (rc == FAST_OK) rc = fast_partition(c, &S->cfg, st, &ch);
-        if (rc == FAST_OK) rc = fast_match_ex(c, ch, &S->cfg, 0, nullptr, &count, nullptr, nullptr, st);
-        if (ch) fast_free_chunks(ch);
-        if (c) fast_free_cst(c);
-        res.count = count;
-        res.status = rc;
-        res.t_done_ns = now_ns();
+        S->cv.notify_all();
+        if (grp.empty()) continue;
+        const int n = (int)grp.size();
+        qd.resize(n);
+        counts.assign(n, 0);
+        status.assign(n, FAST_OK);
+        for (int i = 0; i < n; i++) {
+            qd[i].n = (int32_t)grp[i].labels.size();
+            qd[i].m = (int32_t)(grp[i].edges.size() / 2);
+            qd[i].labels = grp[i].labels.data();
+            qd[i].edges = grp[i].edges.data();
+        }
+        int rc = fast_batch_run(b, n, qd.data(), counts.data(), status.data(), st);
+        const uint64_t t_done = now_ns();
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            S->in_use -= r.projected;
-            S->running--;
-            S->done.push_back(res);
+            for (int i = 0; i < n; i++) {
+                fast_result res;
+                memset(&res, 0, sizeof(res));
+                res.id = grp[i].id;
+                res.t_arrive_ns = grp[i].t_arrive;
+                res.t_start_ns = t_start;
+                res.t_done_ns = t_done;
+                res.count = rc == FAST_OK ? counts[i] : 0;
+                res.status = rc == FAST_OK ? status[i] : rc;
+                S->in_use -= grp[i].projected;
+                S->running--;
+                S->done.push_back(res);
+            }
         }
         S->cv.notify_all();
     }
@@ -166,7 +194,7 @@ extern "C" int fast_server_create(const fast_graph* g, const fast_config* cfg, u
     if (cfg) S->cfg = *cfg; else fast_config_default(&S->cfg);
     S->budget = budget_bytes;
     cudaGetDevice(&S->device);
-    int W = workers > 0 ? workers : 4;
+    int W = workers > 0 ? workers : 2;
     // mean degree per label, for the admission estimate
     unsigned long long* sum = nullptr;
     cudaStream_t s0 = nullptr;
@@ -188,13 +216,22 @@ extern "C" int fast_server_create(const fast_graph* g, const fast_config* cfg, u
     dfree(sum, s0);
     cudaStreamSynchronize(s0);
     if (rc != FAST_OK) { delete S; return rc; }
-    S->streams.resize(W);
-    for (auto& st : S->streams)
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-            for (auto x : S->streams) if (x) cudaStreamDestroy(x);
-            delete S;
-            return set_error(FAST_ERR_CUDA, "fast_server_create: stream");
+    S->streams.assign(W, nullptr);
+    S->batches.assign(W, nullptr);
+    for (int w = 0; w < W && rc == FAST_OK; w++) {
+        if (cudaStreamCreateWithFlags(&S->streams[w], cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(FAST_ERR_CUDA, "fast_server_create: stream");
+            break;
         }
+        rc = fast_batch_create(g, &S->cfg, S->group_cap, 0, &S->batches[w]);
+    }
+    if (rc != FAST_OK) {
+        for (auto x : S->batches) if (x) fast_free_batch(x);
+        for (auto x : S->streams) if (x) cudaStreamDestroy(x);
+        delete S;
+        return rc;
+    }
     for (int w = 0; w < W; w++) S->workers.emplace_back(worker_main, S, w);
     *out = S;
     return FAST_OK;
@@ -241,6 +278,14 @@ extern "C" int fast_server_stats(fast_server* S, int64_t* pending, int64_t* runn
     return FAST_OK;
 }
 
+extern "C" int fast_server_groups(fast_server* S, uint64_t* groups, uint64_t* requests) {
+    if (!S) return set_error(FAST_ERR_INVALID, "fast_server_groups: NULL server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (groups) *groups = S->groups;
+    if (requests) *requests = S->grouped;
+    return FAST_OK;
+}
+
 extern "C" void fast_server_destroy(fast_server* S) {
     if (!S) return;
     {
@@ -249,6 +294,7 @@ extern "C" void fast_server_destroy(fast_server* S) {
     }
     S->cv.notify_all();
     for (auto& t : S->workers) t.join();
+    for (auto b : S->batches) fast_free_batch(b);
     for (auto st : S->streams) cudaStreamDestroy(st);
     delete S;
 }

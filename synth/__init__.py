@@ -158,6 +158,26 @@ def walk_queries(n: int, edges: np.ndarray, labels: np.ndarray, k: int, count: i
         wg.close()
 
 
+def kinds_for(k: int) -> tuple:
+    """The two query kinds drawn at size k: dense and sparse, except that a
+    4-vertex query cannot have average degree > 3, so 4-vertex queries are
+    induced and sparse."""
+    return ("induced", "sparse") if k == 4 else ("dense", "sparse")
+
+
+def mixed_queries(wg: "WalkGraph", labels: np.ndarray, sizes, per_size: int, seed: int) -> list:
+    """per_size random-walk queries of each size in `sizes`, the two kinds of
+    kinds_for(k) alternating, walk j of size k drawn from stream
+    100,000 * k + j: a list of (labels, edges)."""
+    qs = []
+    for k in sizes:
+        kinds = kinds_for(k)
+        for j in range(per_size):
+            q = wg.query(labels, k, kinds[j % 2], seed, 100_000 * k + j)
+            qs.append((q.labels, q.edges))
+    return qs
+
+
 # ----------------------------------------------------------------- workloads
 
 @dataclass

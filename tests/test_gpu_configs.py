@@ -32,18 +32,8 @@ L_RMAT = 1 << 12         # RMAT graphs: heavier hubs, so a smaller limit keeps t
 BUDGET = 20_000_000
 
 
-def kinds_for(k):
-    return ("induced", "sparse") if k == 4 else ("dense", "sparse")
-
-
 def draw(wg, lab, sizes, per_size, seed):
-    qs = []
-    for k in sizes:
-        kinds = kinds_for(k)
-        for j in range(per_size):
-            q = wg.query(lab, k, kinds[j % 2], seed, 100_000 * k + j)
-            qs.append((q.labels, q.edges))
-    return qs
+    return synth.mixed_queries(wg, lab, sizes, per_size, seed)
 
 
 def check_against_oracle(o, qs, counts, status, lim):

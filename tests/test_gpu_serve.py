@@ -1,7 +1,8 @@
-"""Serving with continuous batching: every request's result equals the one
-it gets alone; admission by projected bytes serialises requests when the
-budget holds only one, and rejects a request that exceeds the whole
-budget."""
+"""Serving with continuous batching: requests queued while a group runs are
+run together as the next group (one batched build and one matcher launch);
+every request's result equals the one it gets alone; admission by projected
+bytes serialises requests when the budget holds only one, and rejects a
+request that exceeds the whole budget."""
 import time
 
 import numpy as np
@@ -55,6 +56,29 @@ def test_results_equal_alone_under_random_arrivals(env, seed):
         assert r["status"] == 0
         assert r["count"] == alone[ids[r["id"]]]
         assert r["t_arrive_ns"] <= r["t_start_ns"] <= r["t_done_ns"]
+
+
+def test_requests_queued_meanwhile_run_as_one_group(env):
+    w, g, qs, alone = env
+    s = F.Server(g, budget_bytes=8 << 30, cfg=F.default_config(build_rule=2), workers=1)
+    reps = 5
+    ids = {}
+    for r in range(reps):                     # all at once: the first group starts while the rest queue
+        for i, q in enumerate(qs):
+            ids[s.submit(*q)] = i
+    res = drain(s, len(ids))
+    groups, grouped = s.groups()
+    s.close()
+    assert len(res) == len(ids) == grouped
+    assert groups < grouped / 4, (groups, grouped)
+    for r in res:
+        assert r["status"] == 0
+        assert r["count"] == alone[ids[r["id"]]]
+    # the requests of a group are admitted together and finish together
+    spans = {}
+    for r in res:
+        spans.setdefault(r["t_start_ns"], set()).add(r["t_done_ns"])
+    assert len(spans) == groups and all(len(v) == 1 for v in spans.values())
 
 
 def test_budget_for_one_request_serialises(env):
