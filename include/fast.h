@@ -289,6 +289,16 @@ int fast_partition_batch(const fast_cst* const* csts, int32_t nq, const fast_con
 int fast_chunks_info(const fast_chunks* ch, int64_t* count, uint64_t* w_sum);
 
 /*
+ * A new chunk list holding chunks idx[0..n) of ch (host indices, in that
+ * order; each in 0..count-1, else FAST_ERR_INVALID), for the same CST: a
+ * rank's share when the chunks of one query are split over several GPUs
+ * (partitions are disjoint, complete search spaces, Sec. IV-B, so the
+ * counts of the shares add up to the query's).  Free with fast_free_chunks.
+ * Synchronises `stream`.
+ */
+int fast_chunks_select(const fast_chunks* ch, const int64_t* idx, int64_t n, void* stream, fast_chunks** out);
+
+/*
  * Copy the chunk descriptors to host arrays of `count` entries: j[i],
  * prefix[i][k] (candidate-local indices of positions 0..j-1; -1 beyond),
  * a[i], b[i], w[i] (W', saturating uint64), id[i] (sampling id).
@@ -319,7 +329,9 @@ void fast_free_chunks(fast_chunks* ch);
  *                and are copied to emb_out before the call returns.
  *   count_out:   host; total number of embeddings in the chunks.
  *   written_out: host; rows written = min(k, count).
- *   chunk_counts: optional device buffer of one uint64 per chunk.
+ *   chunk_counts: optional device buffer of one uint64 per chunk (with
+ *                chunks NULL, one: the count of the whole CST).  Given, it
+ *                keeps every run on the warp that took it (no donation).
  * The call synchronises `stream`.  FAST_ERR_TIMEOUT (time budget spent)
  * and FAST_ERR_OVERFLOW leave a partial or saturated count in *count_out.
  */
@@ -378,6 +390,10 @@ int fast_batch_run(fast_batch* b, int32_t nq, const fast_query_desc* queries, ui
 /* Last run: wall time of the CST/partition phase, event time of the matcher
  * launch, bytes the matcher requested, and chunks matched. */
 int fast_batch_timing(const fast_batch* b, double* build_ms, double* match_ms, uint64_t* match_bytes, int64_t* chunks);
+
+/* Last run's matcher launch: bytes requested (as fast_last_match_bytes) and
+ * their floor (as fast_last_match_floor_bytes), over all its queries. */
+int fast_batch_bytes(const fast_batch* b, uint64_t* requested, uint64_t* floor);
 
 /* Read (get != NULL) and/or replace (set != NULL) the configuration of the
  * size class that a query of size_class_k vertices falls into. */
@@ -515,6 +531,19 @@ double fast_last_match_ms(void);
  * gathered, and 4|V(q)| B per embedding written.  Counted by every lane of
  * the search itself, whichever level of the memory hierarchy serves it. */
 uint64_t fast_last_match_bytes(void);
+
+/* The floor of fast_last_match_bytes for the same launch: what any search
+ * over the CST that scans the shortest list into each position must read.
+ * Per extension of a partial result to position d: the new image (4 B),
+ * 16 B of offsets for the tree list and for each earlier non-tree
+ * neighbour's list into d, and 4 B per entry of the shortest of those lists;
+ * per candidate in all of them while an earlier position has its label, its
+ * data vertex (4 B); per embedding written, 4|V(q)| B.  A chunk of a
+ * partition that starts at position j > 0 counts its run as one such
+ * extension.  Without a partition the count is independent of how the
+ * work is spread over warps, and equals the oracle's floor for the same CST
+ * and order. */
+uint64_t fast_last_match_floor_bytes(void);
 
 /* Kernels launched by the library since the process started (all threads). */
 uint64_t fast_kernel_launches(void);

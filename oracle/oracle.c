@@ -163,41 +163,62 @@ static int64_t cst_list(const sctx* c, int32_t x, int u, int32_t* buf) {
     return n;
 }
 
-/* Bytes a search over the candidate search tree requests to extend the
- * valid partial M[0..d) by one position.  lo[0] is what any such search must
- * read: 4 B for the image of the last position, 16 B of list offsets for the
- * tree list and for each earlier non-tree neighbour's list, 4 B per
- * tree-list entry, and 4 B for an entry's data vertex when an earlier
- * position has the same label and the entry passed the non-tree checks.
- * lo[1] adds a ceiling on the non-tree list reads of a warp-cooperative
- * merge: per non-tree list, its entries plus one 32-entry tile, and per
- * 32-entry segment of the tree list ten more 32-entry probe rounds. */
+/* Bytes a search over the candidate search tree reads to extend the valid
+ * partial M[0..d) to position d.  The candidates of position d are the
+ * intersection of the CST list from the image of its tree parent and the
+ * lists from the images of its earlier non-tree neighbours (Alg. 5 and 7;
+ * the CST lists, with the allowed sets taken as the candidate sets).
+ *
+ * lo[0], the floor: what a search that scans the shortest of those lists
+ * (the generator) and checks its entries against the others must read --
+ * 4 B for the image of the last mapped position, 16 B of offsets (begin and
+ * end) per list, 4 B per generator entry, and 4 B for the data vertex of
+ * each entry in every list while an earlier position has the same label
+ * (the visited check, Alg. 6).
+ *
+ * lo[1], a ceiling for a warp that takes the generator 32 entries at a time
+ * (S = ceil(|G| / 32) segments) and tests them against each other list L by
+ * a merge with a forward-only cursor: tiles of 32 entries whose positions
+ * never decrease except for one re-read at each segment start (at most
+ * |L| + 32 S entries), and per tile that holds no pending candidate one
+ * galloping search (one round of 32 probes, then at most five 33-way
+ * refinement rounds of 32 probes, since a gallop spans at most 32 * 2^25
+ * entries), at most min(|G|, ceil(|L| / 32) + S) of them.  lo[1] = lo[0] +
+ * sum over L of 4 (|L| + 32 S) + 4 * 32 * 6 * min(|G|, ceil(|L|/32) + S). */
 static void extension_bytes(const sctx* c, const int32_t* M, int d, double* lo) {
     const og* g = c->g;
-    int u = c->order[d];
-    int32_t x = M[c->par[d]];
-    double b = 4.0 + 16.0 + 16.0 * c->nb[d], extra = 0.0;
-    int64_t maxd = g->off[x + 1] - g->off[x];
-    for (int j = 0; j < c->nb[d]; j++) {
-        int32_t y = M[c->bn[d][j]];
-        if (g->off[y + 1] - g->off[y] > maxd) maxd = g->off[y + 1] - g->off[y];
+    const int u = c->order[d];
+    const int nl = 1 + c->nb[d];                    /* the tree list, then the non-tree lists */
+    int32_t* L[OMAXK];
+    int64_t len[OMAXK];
+    for (int j = 0; j < nl; j++) {
+        const int32_t x = j == 0 ? M[c->par[d]] : M[c->bn[d][j - 1]];
+        const int64_t deg = g->off[x + 1] - g->off[x];
+        L[j] = (int32_t*)malloc((size_t)(deg > 0 ? deg : 1) * sizeof(int32_t));
+        len[j] = cst_list(c, x, u, L[j]);
     }
-    int32_t* T = (int32_t*)malloc((size_t)(maxd > 0 ? maxd : 1) * sizeof(int32_t));
-    int32_t* N = (int32_t*)malloc((size_t)(maxd > 0 ? maxd : 1) * sizeof(int32_t));
-    int64_t nt = cst_list(c, x, u, T);
+    int gi = 0;                                     /* the generator: shortest, ties to the earlier list */
+    for (int j = 1; j < nl; j++) if (len[j] < len[gi]) gi = j;
+    const int64_t ng = len[gi];
     int same = 0;
     for (int j = 0; j < d; j++) if (c->ql[c->order[j]] == c->ql[u]) same = 1;
-    uint8_t* ok = (uint8_t*)malloc((size_t)(nt > 0 ? nt : 1));
-    for (int64_t i = 0; i < nt; i++) { ok[i] = 1; b += 4.0; }
-    int64_t segs = (nt + 31) / 32;
-    for (int j = 0; j < c->nb[d]; j++) {
-        int64_t nn = cst_list(c, M[c->bn[d][j]], u, N);
-        extra += 4.0 * (double)(nn + 32) + 4.0 * 32.0 * 10.0 * (double)segs;
-        for (int64_t i = 0; i < nt; i++)
-            if (ok[i] && !in_sorted(N, nn, T[i])) ok[i] = 0;
+    int64_t inter = 0;                              /* generator entries present in every list */
+    for (int64_t i = 0; i < ng; i++) {
+        int in_all = 1;
+        for (int j = 0; j < nl && in_all; j++)
+            if (j != gi && !in_sorted(L[j], len[j], L[gi][i])) in_all = 0;
+        inter += in_all;
     }
-    if (same) for (int64_t i = 0; i < nt; i++) if (ok[i]) b += 4.0;
-    free(T); free(N); free(ok);
+    double b = 4.0 + 16.0 * nl + 4.0 * (double)ng + (same ? 4.0 * (double)inter : 0.0);
+    double extra = 0.0;
+    const int64_t segs = (ng + 31) / 32;
+    for (int j = 0; j < nl; j++) {
+        if (j == gi || ng == 0) continue;
+        int64_t gallops = (len[j] + 31) / 32 + segs;
+        if (gallops > ng) gallops = ng;
+        extra += 4.0 * (double)(len[j] + 32 * segs) + 4.0 * 32.0 * 6.0 * (double)gallops;
+    }
+    for (int j = 0; j < nl; j++) free(L[j]);
     lo[0] += b;
     lo[1] += b + extra;
 }

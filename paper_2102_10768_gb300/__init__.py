@@ -94,6 +94,9 @@ _SIGS = {
     "fast_server_submit": (ctypes.c_int, [_vp, _vp, _vp]),
     "fast_server_poll": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32]),
     "fast_server_groups": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fast_batch_bytes": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fast_chunks_select": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "fast_last_match_floor_bytes": (ctypes.c_uint64, []),
     "fast_server_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "fast_server_destroy": (None, [_vp]),
     "fast_now_ns": (ctypes.c_uint64, []),
@@ -361,6 +364,21 @@ class Chunks:
         return [(int(j[i]), tuple(int(x) for x in pre[i, :j[i]]), int(a[i]), int(b[i]), int(w[i]), int(ids[i]))
                 for i in range(n)]
 
+    def weights(self) -> np.ndarray:
+        """W' of every chunk (uint64)."""
+        n = self.n
+        w = np.empty(max(n, 1), np.uint64)
+        _check(lib().fast_chunks_copy(self._h, None, None, None, None, _p(w), None, self.stream))
+        return w[:n]
+
+    def select(self, idx) -> "Chunks":
+        """fast_chunks_select: the chunks idx (host indices, in order) as a new
+        list over the same CST -- one rank's share of a sharded query."""
+        ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).reshape(-1))
+        h = _vp()
+        _check(lib().fast_chunks_select(self._h, _p(ix) if ix.size else None, ix.size, self.stream, ctypes.byref(h)))
+        return Chunks._adopt(self.cst, h, self.stream)
+
     def close(self):
         if getattr(self, "_h", None):
             lib().fast_free_chunks(self._h)
@@ -458,9 +476,11 @@ class Batch:
         return counts[:n].astype(np.int64), status[:n]
 
     def timing(self):
-        b, m, by, ch = ctypes.c_double(), ctypes.c_double(), _u64(), _i64()
+        b, m, by, ch, fl = ctypes.c_double(), ctypes.c_double(), _u64(), _i64(), _u64()
         _check(lib().fast_batch_timing(self._h, ctypes.byref(b), ctypes.byref(m), ctypes.byref(by), ctypes.byref(ch)))
-        return {"build_ms": b.value, "match_ms": m.value, "match_bytes": by.value, "chunks": ch.value}
+        _check(lib().fast_batch_bytes(self._h, None, ctypes.byref(fl)))
+        return {"build_ms": b.value, "match_ms": m.value, "match_bytes": by.value, "floor_bytes": fl.value,
+                "chunks": ch.value}
 
     def config(self, k: int, new: Config | None = None) -> Config:
         c = Config()
@@ -582,8 +602,13 @@ def last_match_ms() -> float:
 
 
 def last_match_bytes() -> int:
-    """Algorithmic bytes of the last fast_match on this thread."""
+    """Bytes the last fast_match on this thread requested."""
     return int(lib().fast_last_match_bytes())
+
+
+def last_match_floor_bytes() -> int:
+    """The floor of those bytes (fast_last_match_floor_bytes)."""
+    return int(lib().fast_last_match_floor_bytes())
 
 
 def kernel_launches() -> int:

@@ -38,7 +38,7 @@ int match_batched_enqueue(const void* d_plans, int warp_words, const void* d_chu
                           void* d_dq, uint32_t* d_dq_state, uint64_t dq_cap, uint64_t limit, double budget_s,
                           int warps, int bps, cudaStream_t s);
 int match_smem_optin(size_t bytes);
-int match_status_of(const unsigned long long* h_ctr, uint64_t* bytes);
+int match_status_of(const unsigned long long* h_ctr, uint64_t* bytes, uint64_t* floor);
 }  // namespace fast
 
 using namespace fast;
@@ -86,7 +86,7 @@ struct fast_batch {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<ScratchPool*> pools;      // per build thread: scratch of its CSTs and partitions
     double last_build_ms = 0.0, last_match_ms = 0.0;
-    uint64_t last_bytes = 0;
+    uint64_t last_bytes = 0, last_floor = 0;
     int64_t last_chunks = 0;
 };
 
@@ -201,14 +201,22 @@ int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream
         e = cudaGraphInstantiate(&b->exec, graph, 0);
         if (e != cudaSuccess) rc = cuda_status(e, "graph instantiate", __FILE__, __LINE__);
     }
-    // the enqueue counted each kernel it recorded (one graph node each);
+    // the enqueue counted each kernel it recorded (one kernel node each);
     // they run, and are counted, at each replay instead
-    size_t nodes = 0;
-    if (rc == FAST_OK && cudaGraphGetNodes(graph, nullptr, &nodes) != cudaSuccess) {
+    int recorded = 0;
+    if (rc == FAST_OK) {
+        size_t nodes = 0;
+        std::vector<cudaGraphNode_t> nv;
+        if (cudaGraphGetNodes(graph, nullptr, &nodes) == cudaSuccess) {
+            nv.resize(nodes);
+            if (nodes && cudaGraphGetNodes(graph, nv.data(), &nodes) != cudaSuccess) nv.clear();
+        }
+        for (auto nd : nv) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) recorded++;
+        }
         cudaGetLastError();
-        nodes = 0;
     }
-    const int recorded = (int)nodes;
     note_launch(-recorded);
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cap);
@@ -346,7 +354,7 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
         cudaEventElapsedTime(&ms, b->ev0, b->ev1);
         b->last_match_ms = ms;
     } while (0);
-    int gst = match_status_of(b->h_ctr, &b->last_bytes);
+    int gst = match_status_of(b->h_ctr, &b->last_bytes, &b->last_floor);
     cudaStreamSynchronize(s);               // no gather copy may still read a chunk list
     for (int i = 0; i < nq; i++) {
         // the matcher is done (or never ran); the builders' streams stay ordered
@@ -384,6 +392,13 @@ extern "C" int fast_batch_timing(const fast_batch* b, double* build_ms, double* 
     if (match_ms) *match_ms = b->last_match_ms;
     if (match_bytes) *match_bytes = b->last_bytes;
     if (chunks) *chunks = b->last_chunks;
+    return FAST_OK;
+}
+
+extern "C" int fast_batch_bytes(const fast_batch* b, uint64_t* requested, uint64_t* floor) {
+    if (!b) return set_error(FAST_ERR_INVALID, "fast_batch_bytes: NULL batch");
+    if (requested) *requested = b->last_bytes;
+    if (floor) *floor = b->last_floor;
     return FAST_OK;
 }
 

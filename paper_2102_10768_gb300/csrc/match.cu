@@ -7,8 +7,7 @@
 //   Generator        the candidates of depth d are the intersection of the
 //                    tree list from the parent's image and the CST list from
 //                    every earlier non-tree neighbour's image, all sorted
-//                    over C(u_d); the warp scans the shortest of them (the
-//                    tree list in the counting pass, whose bytes are pinned);
+//                    over C(u_d); the warp scans the shortest of them;
 //   EdgeValidator    membership in each other list by a warp-cooperative
 //                    merge (a cursor per list, coalesced 32-entry tiles, a
 //                    shuffle search, galloping), shortest lists first,
@@ -43,6 +42,7 @@ namespace {
 
 thread_local double g_last_match_ms = 0.0;
 thread_local uint64_t g_last_match_bytes = 0;
+thread_local uint64_t g_last_match_floor = 0;
 
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -97,6 +97,7 @@ struct MatchOut {
     uint64_t emb_cap;                 // rows that may be written
     unsigned long long* stats;        // nullable: [k] partial results per depth
     unsigned long long* bytes;        // bytes the search requested
+    unsigned long long* floor;        // the floor of those bytes (see k_match)
     const unsigned long long* deadline;  // device word: %globaltimer limit, 0 = none
     uint64_t limit;                   // 0 = enumerate everything
     // Donated runs: a bounded ring of dq_cap cells.  Ticket t (a count of
@@ -284,6 +285,16 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
     unsigned long long iter = 0;
     const unsigned long long deadline = *O.deadline;
     unsigned long long lb = 0;             // this lane's bytes requested (entries of 4 B, offsets of 8 B)
+    // lane 0: the floor of the bytes, what any search over the CST that scans
+    // the shortest list into each position must read: per extension of a
+    // partial result to position d, the new image (4 B), the offsets of the
+    // tree list and of each earlier non-tree neighbour's list into d (16 B
+    // each) and every entry of the generator list (4 B); per candidate that
+    // passes the list checks while an earlier position has its label, its
+    // data vertex (4 B); per embedding written, its row (4|V(q)| B).  A static
+    // chunk that starts at position j > 0 counts its run's extension the same
+    // way; a donated run counts only what it scans.
+    unsigned long long fb = 0;
     unsigned long long local = 0;          // lane 0: count not yet flushed
 
     for (;;) {
@@ -353,6 +364,7 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
         }
         unsigned long long ccount = 0;         // lane 0: this item's count
         if (__all_sync(0xffffffffu, ok_prefix)) {
+            if (kind == 1 && j > 0 && lane == 0) fb += 4 + 16 + 16ull * (P.nt_begin[j + 1] - P.nt_begin[j]);
             // ---- depth j: the item's run of L_j
             int d = j;
             int64_t seg_next = 0, seg_end = 0, seg_base = 0;   // lane d: depth d's list scan
@@ -461,10 +473,10 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                     int64_t lo = P.t_off[d][mp], hi = P.t_off[d][mp + 1];
                     // Generator list: the candidates of depth d are the intersection of
                     // the tree list and every non-tree list into d, all sorted over
-                    // C(u_d).  Scan the shortest and check the others (the same set; the
-                    // counting pass keeps the tree list, whose bytes the oracle pins).
+                    // C(u_d).  Scan the shortest (ties to the tree list, then to the
+                    // earlier non-tree edge) and check the others: the same set.
                     int src = 0;
-                    if (!STATS) {
+                    {
                         const int e0 = P.nt_begin[d], ne = P.nt_begin[d + 1] - e0;
                         if (ne > 0) {
                             uint32_t mf = __shfl_sync(0xffffffffu, m_reg, lane < ne ? P.nt_from[e0 + lane] : 0);
@@ -490,6 +502,7 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                         gsrc[d] = src;
                         tcur[d] = 0;
                         lb += 16 + 16ull * (P.nt_begin[d + 1] - P.nt_begin[d]);
+                        fb += 4 + 16 + 16ull * (P.nt_begin[d + 1] - P.nt_begin[d]);
                     }
                     for (int e = P.nt_begin[d] + lane; e < P.nt_begin[d + 1]; e += 32) ncur[e] = 0;
                     __syncwarp();
@@ -508,6 +521,7 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                         cnd = (d == 0) ? (uint32_t)idx : __ldg((src == 0 ? P.t_idx[d] : P.n_idx[gen_e]) + idx);
                         if (d > 0) lb += 4;
                     }
+                    if (d > 0 && lane == 0) fb += 4ull * (unsigned long long)(se - sn < 32 ? se - sn : 32);
                     // a non-tree list generates: the tree list is checked like the others
                     if (src != 0 && __any_sync(0xffffffffu, ok)) {
                         uint32_t mp = __shfl_sync(0xffffffffu, m_reg, P.par[d]);
@@ -534,6 +548,10 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                     int32_t gc = -1;
                     uint32_t sl = P.same_lab[d];
                     if (sl || (EMIT && d == k - 1)) {
+                        if (sl) {
+                            const uint32_t pm = __ballot_sync(0xffffffffu, ok);
+                            if (lane == 0) fb += 4ull * __popc(pm);
+                        }
                         if (ok) { gc = __ldg(P.cand[d] + cnd); lb += 4; }
                         while (sl) {
                             int p = __ffs(sl) - 1;
@@ -553,6 +571,10 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                             if (lane == 0) base = atomicAdd(O.emb_slot, (unsigned long long)__popc(mask));
                             base = __shfl_sync(0xffffffffu, base, 0);
                             unsigned long long slot = base + __popc(mask & lanemask_lt());
+                            if (lane == 0 && base < O.emb_cap) {
+                                const unsigned long long nw = __popc(mask);
+                                fb += 4ull * k * (nw < O.emb_cap - base ? nw : O.emb_cap - base);
+                            }
                             bool wr = ok && slot < O.emb_cap;
                             if (wr) lb += 4ull * k;
                             for (int p = 0; p < k - 1; p++) {
@@ -582,6 +604,7 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
     }
     for (int o = 16; o > 0; o >>= 1) lb += __shfl_xor_sync(0xffffffffu, lb, o);
     if (lane == 0 && lb) atomicAdd(O.bytes, lb);
+    if (lane == 0 && fb) atomicAdd(O.floor, fb);
 }
 
 MatchPlan make_plan(const fast_cst* c) {
@@ -654,7 +677,7 @@ int matcher_smem_optin(size_t bytes) {
 }
 
 // counter block layout (unsigned long long words)
-enum { kNext = 0, kTotal, kSlot, kStatus, kBytes, kHead, kTail, kOut, kIdle, kDeadline, kQStop, kStats,
+enum { kNext = 0, kTotal, kSlot, kStatus, kBytes, kFloor, kHead, kTail, kOut, kIdle, kDeadline, kQStop, kStats,
        kCtrWords = kStats + kMaxK + 1 };
 constexpr uint64_t kQueueCap = 1 << 16;
 
@@ -729,9 +752,11 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
         MatchOut O;
         O.next_chunk = ctr + kNext; O.total = ctr + kTotal; O.emb_slot = ctr + kSlot; O.status = (int*)(ctr + kStatus);
         O.qstop = (int*)(ctr + kQStop); O.nq = 1;
-        O.chunk_counts = chunk_counts; O.emb = emb_dev; O.emb_cap = emb_cap;
+        // without a partition the root runs are internal: the whole CST is the one chunk
+        O.chunk_counts = chunks ? chunk_counts : nullptr; O.emb = emb_dev; O.emb_cap = emb_cap;
         O.stats = stats_out ? ctr + kStats : nullptr;
         O.bytes = ctr + kBytes;
+        O.floor = ctr + kFloor;
         O.deadline = ctr + kDeadline;
         O.limit = cfg.limit;
         O.dq = dq; O.dq_state = dq_state; O.dq_cap = donate ? cells : 0;
@@ -759,12 +784,17 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
     }
     unsigned long long h[kCtrWords];
     memset(h, 0, sizeof(h));
+    if (rc == FAST_OK && !chunks && chunk_counts) {
+        cudaError_t e = cudaMemcpyAsync(chunk_counts, ctr + kTotal, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) rc = cuda_status(e, "fast_match chunk count", __FILE__, __LINE__);
+    }
     if (rc == FAST_OK) {
         cudaError_t e = cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_status(e, "fast_match", __FILE__, __LINE__);
         g_last_match_ms = 0.0;
         g_last_match_bytes = h[kBytes];
+        g_last_match_floor = h[kFloor];
         if (rc == FAST_OK && timed) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, match_events().a, match_events().b) == cudaSuccess) g_last_match_ms = ms;
@@ -816,6 +846,8 @@ extern "C" int fast_match_stats(const fast_cst* c, const fast_chunks* chunks, co
 extern "C" double fast_last_match_ms(void) { return g_last_match_ms; }
 
 extern "C" uint64_t fast_last_match_bytes(void) { return g_last_match_bytes; }
+
+extern "C" uint64_t fast_last_match_floor_bytes(void) { return g_last_match_floor; }
 
 // ------------------------------------------------------ allocation-free matcher
 //
@@ -920,6 +952,7 @@ int run_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_c
     O.chunk_counts = nullptr; O.emb = emb_out; O.emb_cap = emb_cap;
     O.stats = nullptr;
     O.bytes = ctr + kBytes;
+    O.floor = ctr + kFloor;
     O.deadline = ctr + kDeadline;
     O.limit = cfg.limit;
     O.dq = dq; O.dq_state = dq_state; O.dq_cap = cells;
@@ -996,7 +1029,7 @@ int match_batched_enqueue(const void* d_plans, int warp_words, const void* d_chu
     O.next_chunk = d_ctr + kNext; O.total = d_qtotal; O.qstop = d_qstop; O.nq = max_q;
     O.emb_slot = d_ctr + kSlot; O.status = (int*)(d_ctr + kStatus);
     O.chunk_counts = nullptr; O.emb = nullptr; O.emb_cap = 0; O.stats = nullptr;
-    O.bytes = d_ctr + kBytes; O.deadline = d_ctr + kDeadline; O.limit = limit;
+    O.bytes = d_ctr + kBytes; O.floor = d_ctr + kFloor; O.deadline = d_ctr + kDeadline; O.limit = limit;
     O.dq = (Chunk*)d_dq; O.dq_state = d_dq_state; O.dq_cap = dq_cap;
     O.dq_head = d_ctr + kHead; O.dq_tail = d_ctr + kTail; O.outstanding = d_ctr + kOut;
     O.idle = (unsigned int*)(d_ctr + kIdle);
@@ -1015,8 +1048,9 @@ int match_batched_enqueue(const void* d_plans, int warp_words, const void* d_chu
 
 int match_smem_optin(size_t bytes) { return matcher_smem_optin(bytes); }
 
-int match_status_of(const unsigned long long* h_ctr, uint64_t* bytes) {
+int match_status_of(const unsigned long long* h_ctr, uint64_t* bytes, uint64_t* floor) {
     if (bytes) *bytes = h_ctr[kBytes];
+    if (floor) *floor = h_ctr[kFloor];
     return (int)h_ctr[kStatus];
 }
 

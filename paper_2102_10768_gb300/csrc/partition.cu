@@ -288,6 +288,49 @@ extern "C" int fast_chunks_copy(const fast_chunks* ch, int32_t* j, int32_t* pref
     return FAST_OK;
 }
 
+__global__ void k_gather_chunks(const Chunk* __restrict__ src, const int64_t* __restrict__ idx, int64_t n,
+                                Chunk* __restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+
+extern "C" int fast_chunks_select(const fast_chunks* ch, const int64_t* idx, int64_t n, void* stream,
+                                  fast_chunks** out) {
+    if (!out) return set_error(FAST_ERR_INVALID, "fast_chunks_select: out is NULL");
+    *out = nullptr;
+    if (!ch || n < 0 || (n > 0 && !idx)) return set_error(FAST_ERR_INVALID, "fast_chunks_select: bad arguments");
+    for (int64_t i = 0; i < n; i++)
+        if (idx[i] < 0 || idx[i] >= ch->n)
+            return set_error(FAST_ERR_INVALID, "fast_chunks_select: index %lld of %lld chunks", (long long)idx[i],
+                             (long long)ch->n);
+    cudaStream_t s = (cudaStream_t)stream;
+    PoolScope scratch(s);
+    fast_chunks* sel = new fast_chunks();
+    sel->c = ch->c; sel->n = n; sel->stream = s;
+    int64_t* d_idx = nullptr;
+    int rc = dalloc_direct(&sel->d, n, s);                       // outlives the call
+    if (rc == FAST_OK && n > 0) rc = dalloc(&d_idx, n, s);
+    if (rc == FAST_OK && n > 0) {
+        cudaError_t e = cudaMemcpyAsync(d_idx, idx, n * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) rc = cuda_status(e, "fast_chunks_select", __FILE__, __LINE__);
+    }
+    if (rc == FAST_OK && n > 0) {
+        k_gather_chunks<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4096), 256, 0, s>>>(ch->d, d_idx, n, sel->d);
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_status(e, "fast_chunks_select", __FILE__, __LINE__);
+    }
+    dfree(d_idx, s);
+    if (rc != FAST_OK) {
+        dfree_direct(sel->d, s);
+        delete sel;
+        return rc;
+    }
+    *out = sel;
+    return FAST_OK;
+}
+
 namespace fast {
 void chunks_release_nosync(fast_chunks* ch) {
     if (!ch) return;

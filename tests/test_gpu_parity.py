@@ -368,8 +368,59 @@ def test_stats_match_oracle(seed):
     want = oracle.match(o, ql, qe, order=oc.order, par=par, allow=allow, want_depth=True, want_balg=True)
     b, depth = F.match_stats(gc)
     assert depth.tolist() == want["depth"].tolist()
-    # the root level reads no list; every extension is inside the floor/ceiling
+    # the floor is exact; the bytes requested lie between floor and ceiling
+    assert F.last_match_floor_bytes() == want["balg"]
     assert want["balg"] <= b <= want["balg_max"]
+
+
+def _oracle_bytes(o, oc, ql, qe):
+    k = len(ql)
+    allow = {u: oc.cand(u).tolist() for u in range(k)}
+    pos = {int(u): i for i, u in enumerate(oc.order)}
+    par = [0] + [pos[int(oc.parent[int(oc.order[i])])] for i in range(1, k)]
+    return oracle.match(o, ql, qe, order=oc.order, par=par, allow=allow, want_balg=True)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_timed_matcher_bytes_match_oracle(seed):
+    """The bytes of the timed matcher variant (no counting pass, the one the
+    bench times), in both matching orders and both filters: its floor equals
+    the oracle's exactly, with work donated between warps or not, and its
+    requested bytes lie between the oracle's floor and ceiling."""
+    import torch
+    n, e, lab, ql, qe = rand_case(5200 + seed)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    for order, filt in (("path", "ldf"), ("greedy", "nlf")):
+        cfg = F.default_config(order_rule=1 if order == "greedy" else 0, filter_rule=1 if filt == "nlf" else 0)
+        gc, oc = F.Cst(g, ql, qe, cfg), oracle.Cst(o, ql, qe, order=order, filter=filt)
+        want = _oracle_bytes(o, oc, ql, qe)
+        r = F.match(gc, cfg=cfg)                                   # donation on
+        assert r["count"] == want["count"]
+        assert F.last_match_floor_bytes() == want["balg"], (order, filt)
+        cc = torch.zeros(1, dtype=torch.int64, device="cuda")      # a chunk count: donation off
+        r = F.match(gc, cfg=cfg, chunk_counts=cc)
+        assert r["count"] == want["count"] == int(cc[0])
+        assert F.last_match_floor_bytes() == want["balg"]
+        assert want["balg"] <= F.last_match_bytes() <= want["balg_max"]
+
+
+def test_timed_matcher_floor_under_heavy_donation():
+    """A hub under every root run: idle warps take runs all the time; the
+    floor counted by the donors and takers together is still the oracle's."""
+    rng = np.random.default_rng(13)
+    n = 2000
+    e = [(0, v) for v in range(1, n)] + [tuple(x) for x in rng.integers(1, n, size=(5000, 2)) if x[0] != x[1]]
+    e = np.array(e, np.int32)
+    lab = np.zeros(n, np.int32)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    for qe in ([[0, 1], [1, 2], [2, 3]], [[0, 1], [1, 2], [0, 2], [2, 3]]):
+        ql = np.zeros(4, np.int32)
+        gc, oc = F.Cst(g, ql, qe), oracle.Cst(o, ql, qe)
+        want = _oracle_bytes(o, oc, ql, qe)
+        for cells in (0, 7):
+            r = F.match(gc, cfg=F.default_config(queue_cells=cells))
+            assert r["count"] == want["count"]
+            assert F.last_match_floor_bytes() == want["balg"], cells
 
 
 def test_time_budget_reports_timeout():

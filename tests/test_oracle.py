@@ -402,14 +402,78 @@ def test_balg_floor_and_ceiling_on_a_triangle_query():
     r = oracle.match(g, [0, 1, 1], [[0, 1], [0, 2], [1, 2]], order=[0, 1, 2], par=[0, 0, 0],
                      want_balg=True, want_depth=True)
     assert r["count"] == 4 and r["depth"].tolist() == [1, 4, 4]
-    # extend {0}: 4 + 16 + list {1,2,3,4} 16 = 36
-    # extend {0,x}: 4 + 16 + 16 (non-tree offsets) + tree list 16 + one entry passes
-    #   the non-tree check and has position 1's label: 4
-    floor = 36 + 4 * (4 + 16 + 16 + 16 + 4)
+    # extend {0}: image 4 + tree offsets 16 + tree list {1,2,3,4} 16 = 36
+    # extend {0,x}, x a leaf: image 4 + two lists' offsets 32; the generator is
+    #   the shorter non-tree list {x's twin} (1 entry, 4 B) rather than the
+    #   4-entry tree list; that entry is in both lists and position 1 has its
+    #   label: its data vertex 4
+    floor = 36 + 4 * (4 + 32 + 4 + 4)
     assert r["balg"] == floor
-    # ceiling: per extension {0,x}, the 1-entry non-tree list plus a tile (33 entries)
-    #   and one segment of ten 32-entry rounds
-    assert r["balg_max"] == floor + 4 * (4 * 33 + 4 * 32 * 10)
+    # ceiling per extension {0,x}: the other list (the tree list, 4 entries)
+    #   merged against one segment: 4 (4 + 32) tile bytes plus one gallop of
+    #   six 32-probe rounds, 4 * 32 * 6
+    assert r["balg_max"] == floor + 4 * (4 * (4 + 32) + 4 * 32 * 6)
+
+
+def _brute_balg(n, edges, labels, ql, qe, order, par, cand):
+    """The floor and ceiling of the extension bytes by brute force: every
+    injective map of the first d positions (d = 1 .. k-1) that keeps labels,
+    candidate sets and every query edge among them is a valid partial, and
+    is extended once; its lists are the CST lists by definition (the
+    neighbours of an image that lie in the next position's candidate set)."""
+    k = len(ql)
+    adj = [set() for _ in range(n)]
+    for a, b in np.asarray(edges).reshape(-1, 2).tolist():
+        if a != b:
+            adj[a].add(b); adj[b].add(a)
+    A = set()
+    for a, b in np.asarray(qe).reshape(-1, 2).tolist():
+        A.add((a, b)); A.add((b, a))
+    lo = hi = 0.0
+    for d in range(1, k):
+        us = [int(order[i]) for i in range(d)]
+        u = int(order[d])
+        back = [i for i in range(d) if (us[i], u) in A and i != par[d]]
+        same = any(ql[x] == ql[u] for x in us)
+        for M in itertools.permutations(range(n), d):
+            if any(M[i] not in cand[us[i]] for i in range(d)):
+                continue
+            if any((us[i], us[j]) in A and M[j] not in adj[M[i]] for i in range(d) for j in range(i)):
+                continue
+            lists = [sorted(w for w in adj[M[i]] if w in cand[u]) for i in [par[d]] + back]
+            gi = min(range(len(lists)), key=lambda j: (len(lists[j]), j))
+            G = lists[gi]
+            inter = sum(all(x in L for L in lists) for x in G)
+            f = 4 + 16 * len(lists) + 4 * len(G) + (4 * inter if same else 0)
+            segs = (len(G) + 31) // 32
+            extra = 0
+            if G:
+                for j, L in enumerate(lists):
+                    if j != gi:
+                        extra += 4 * (len(L) + 32 * segs) + 4 * 32 * 6 * min(len(G), (len(L) + 31) // 32 + segs)
+            lo += f
+            hi += f + extra
+    return lo, hi
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_balg_floor_and_ceiling_by_brute_force(seed):
+    """The oracle's byte floor and ceiling equal a brute-force sum over every
+    valid partial embedding of every prefix of the matching order, both
+    orders, on tiny random cases (allowed sets = the CST's candidate sets)."""
+    rng = np.random.default_rng(7300 + seed)
+    n = int(rng.integers(7, 10))
+    edges, labels = random_graph(rng, n, float(rng.uniform(0.3, 0.7)), int(rng.integers(1, 3)))
+    k = int(rng.integers(3, 5))
+    ql, qe = random_connected_query(rng, k, int(labels.max()) + 1, 0.6)
+    g = oracle.Graph(n, edges, labels)
+    for order_rule in ("path", "greedy"):
+        c = oracle.Cst(g, ql, qe, order=order_rule)
+        cand = [set(c.cand(u).tolist()) for u in range(k)]
+        par = _tree_par(c)
+        r = oracle.match(g, ql, qe, order=c.order, par=par, allow={u: cand[u] for u in range(k)}, want_balg=True)
+        lo, hi = _brute_balg(n, edges, labels, ql, qe, [int(x) for x in c.order], par, cand)
+        assert r["balg"] == lo and r["balg_max"] == hi, (order_rule, r["balg"], lo, r["balg_max"], hi)
 
 
 # ------------------------------------------------------------------- limit
