@@ -30,6 +30,7 @@
 
 #include "internal.cuh"
 #include "prims.cuh"
+#include "seg.cuh"
 #include "cst_funcs.cuh"
 
 using namespace fast;
@@ -506,8 +507,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
             dfree(e_off, s);
             dfree(seg, s);
             rc = dalloc(&td_cand[u], cap_c[u], s); if (rc) break;
-            BitsF bf{bits[u].alive};
-            rc = compact(bf, n, td_cand[u], sz + u, s); if (rc) break;
+            rc = bits_ids_seg({BitsSeg{bits[u].alive, n, td_cand[u], sz + u}}, s); if (rc) break;
         }
         if (rc) break;
 

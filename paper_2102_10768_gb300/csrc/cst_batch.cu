@@ -134,26 +134,56 @@ struct AnyAliveDesc {
     uint8_t* has;
 };
 
+// A tile of a tile-split kernel: its segment, its entry range [tb, te) and
+// the rows of its first and last entries (every entry's row lies between),
+// found once per tile by thread 0.
+struct TileRows {
+    int s;
+    int64_t tb, te, r0, r1;
+};
+
+template <class D>
+__device__ __forceinline__ bool tile_rows(const D* __restrict__ Dd, const int64_t* __restrict__ tile_off, int nseg,
+                                          int64_t t, TileRows* sh) {
+    if (threadIdx.x == 0) {
+        const int s = seg_of_tile(tile_off, nseg, t);
+        const D& d = Dd[s];
+        const int64_t e_end = d.off[d.rows];
+        const int64_t tb = (t - tile_off[s]) * kTileItems;
+        sh->s = s;
+        sh->tb = tb;
+        sh->te = tb + kTileItems < e_end ? tb + kTileItems : e_end;
+        if (tb < e_end) {
+            sh->r0 = row_of(d.off, d.rows, tb);
+            sh->r1 = row_of(d.off, d.rows, sh->te - 1);
+        }
+    }
+    __syncthreads();
+    return sh->tb < sh->te;
+}
+
 __global__ void __launch_bounds__(256) k_any_alive_b(const AnyAliveDesc* __restrict__ D,
                                                      const int64_t* __restrict__ tile_off, int nseg) {
+    __shared__ TileRows tr;
     const int64_t total = tile_off[nseg];
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        const int s = seg_of_tile(tile_off, nseg, t);
-        const AnyAliveDesc& d = D[s];
-        const int64_t* off = d.off;
-        const int64_t rows = d.rows;
-        const int64_t e_end = off[rows];
-        const int64_t i0 = (t - tile_off[s]) * kTileItems + (int64_t)threadIdx.x * kItems;
-        if (i0 >= e_end) continue;
-        int64_t row = row_of(off, rows, i0), done = -1;
-        for (int i = 0; i < kItems; i++) {
-            int64_t e = i0 + i;
-            if (e >= e_end) break;
-            while (e >= off[row + 1]) row++;
-            if (row == done) continue;
-            int32_t x = d.list[e];
-            if ((d.alive[x >> 5] >> (x & 31)) & 1u) { d.has[row] = 1; done = row; }
+        if (tile_rows(D, tile_off, nseg, t, &tr)) {
+            const AnyAliveDesc& d = D[tr.s];
+            const int64_t* off = d.off;
+            const int64_t i0 = tr.tb + (int64_t)threadIdx.x * kItems;
+            if (i0 < tr.te) {
+                int64_t row = row_in(off, tr.r0, tr.r1, i0), done = -1;
+                for (int i = 0; i < kItems; i++) {
+                    int64_t e = i0 + i;
+                    if (e >= tr.te) break;
+                    while (e >= off[row + 1]) row++;
+                    if (row == done) continue;
+                    int32_t x = d.list[e];
+                    if ((d.alive[x >> 5] >> (x & 31)) & 1u) { d.has[row] = 1; done = row; }
+                }
+            }
         }
+        __syncthreads();
     }
 }
 
@@ -252,40 +282,43 @@ struct ChildSumDesc {
 
 __global__ void __launch_bounds__(256) k_child_sums_b(const ChildSumDesc* __restrict__ D,
                                                       const int64_t* __restrict__ tile_off, int nseg) {
+    __shared__ TileRows tr;
     const int64_t total = tile_off[nseg];
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        const int sg = seg_of_tile(tile_off, nseg, t);
-        const ChildSumDesc& d = D[sg];
-        const int64_t* off = d.off;
-        const int64_t e_end = off[d.rows];
-        const int64_t i0 = (t - tile_off[sg]) * kTileItems + (int64_t)threadIdx.x * kItems;
-        if (i0 >= e_end) continue;
-        int64_t row = row_of(off, d.rows, i0);
-        unsigned long long s = 0;
-        double sf = 0.0;
-        bool sat = false;
-        auto flush = [&]() {
-            unsigned long long old = atomicAdd(&d.ssum[row], s);
-            if (old + s < old) sat = true;
-            if (sat) atomicOr(&d.ovf[row], 1u);
-            atomicAdd(&d.sumf[row], sf);
-        };
-        for (int i = 0; i < kItems; i++) {
-            int64_t e = i0 + i;
-            if (e >= e_end) break;
-            if (e >= off[row + 1]) {
+        if (tile_rows(D, tile_off, nseg, t, &tr)) {
+            const ChildSumDesc& d = D[tr.s];
+            const int64_t* off = d.off;
+            const int64_t i0 = tr.tb + (int64_t)threadIdx.x * kItems;
+            if (i0 < tr.te) {
+                int64_t row = row_in(off, tr.r0, tr.r1, i0);
+                unsigned long long s = 0;
+                double sf = 0.0;
+                bool sat = false;
+                auto flush = [&]() {
+                    unsigned long long old = atomicAdd(&d.ssum[row], s);
+                    if (old + s < old) sat = true;
+                    if (sat) atomicOr(&d.ovf[row], 1u);
+                    atomicAdd(&d.sumf[row], sf);
+                };
+                for (int i = 0; i < kItems; i++) {
+                    int64_t e = i0 + i;
+                    if (e >= tr.te) break;
+                    if (e >= off[row + 1]) {
+                        flush();
+                        s = 0; sf = 0.0; sat = false;
+                        do row++; while (e >= off[row + 1]);
+                    }
+                    uint32_t x = d.idx[e];
+                    uint64_t v = d.cv[x];
+                    unsigned long long ns = s + v;
+                    if (ns < s || v == ~0ull) sat = true;
+                    s = ns;
+                    sf += d.cvf[x];
+                }
                 flush();
-                s = 0; sf = 0.0; sat = false;
-                do row++; while (e >= off[row + 1]);
             }
-            uint32_t x = d.idx[e];
-            uint64_t v = d.cv[x];
-            unsigned long long ns = s + v;
-            if (ns < s || v == ~0ull) sat = true;
-            s = ns;
-            sf += d.cvf[x];
         }
-        flush();
+        __syncthreads();
     }
 }
 
@@ -745,13 +778,13 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
                 cv.add(&q.td_cand[u], q.c0[u]);      // C_td(u) lies inside C0(u)
             }
             FAST_TRY(cv.alloc(td, false));
-            std::vector<CompactSeg<BitsF>> cs;
+            std::vector<BitsSeg> bs;
             for (int qi : act) {
                 Q& q = Qs[qi];
                 const int u = q.c->bfs[t];
-                cs.push_back({BitsF{q.alive[u]}, n, q.td_cand[u], zp(F_TD + t, qi)});
+                bs.push_back({q.alive[u], n, q.td_cand[u], zp(F_TD + t, qi)});
             }
-            FAST_TRY(compact_seg(cs, s));
+            FAST_TRY(bits_ids_seg(bs, s));
         }
     }
     // |C_td|, edge spaces and kept entries of every position

@@ -55,6 +55,16 @@ __device__ __forceinline__ int64_t row_of(const int64_t* e_off, int64_t rows, in
     return lo;
 }
 
+// row_of(e_off, rows, i) when it is known to lie in [lo, hi]
+__device__ __forceinline__ int64_t row_in(const int64_t* e_off, int64_t lo, int64_t hi, int64_t i) {
+    hi += 1;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (e_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // The first of the rows whose lists start at index i (row is the last one,
 // the row holding entry i; the others before it are empty).
 __device__ __forceinline__ int64_t first_row_at(const int64_t* e_off, int64_t row, int64_t i) {
@@ -90,10 +100,18 @@ struct TopDownF {
     int64_t row;
     int64_t nbase;
     int64_t e_end;
-    __device__ void begin(int64_t i0) {
+    // the rows of a tile's first and last index, once per tile: each thread
+    // then searches only between them
+    __device__ void tile_hint(int64_t tb, int64_t te, int64_t* h) {
+        const int64_t e = *E;
+        if (te > e) te = e;
+        h[0] = row_of(e_off, rows, tb);
+        h[1] = te > tb ? row_of(e_off, rows, te - 1) : h[0];
+    }
+    __device__ void begin(int64_t i0, const int64_t* h) {
         e_end = *E;
         if (i0 >= e_end) return;
-        row = row_of(e_off, rows, i0);
+        row = row_in(e_off, h[0], h[1], i0);
         nbase = seg[row] - e_off[row];
     }
     __device__ bool eval(int64_t i, int32_t& v) {
@@ -110,7 +128,12 @@ struct TopDownF {
             int32_t kk = key[x];
             hit = (kk >> 8) == want_key_hi && (kk & 255) >= want_dq;
         }
-        if (hit && !counting) atomicOr(&reached[x >> 5], 1u << (x & 31));
+        if (hit && !counting) {
+            // a popular vertex is reached from many rows: test the word
+            // first (a stale copy only costs an atomic) and set the bit once
+            const uint32_t bit = 1u << (x & 31);
+            if (!(__ldcg(&reached[x >> 5]) & bit)) atomicOr(&reached[x >> 5], bit);
+        }
         return hit;
     }
     // rows start at their first entry; a row with no entry (no neighbour of
@@ -136,10 +159,16 @@ struct NonTreeF {
     int64_t row;
     int64_t nbase;
     int64_t e_end;
-    __device__ void begin(int64_t i0) {
+    __device__ void tile_hint(int64_t tb, int64_t te, int64_t* h) {
+        const int64_t e = *E;
+        if (te > e) te = e;
+        h[0] = row_of(e_off, rows, tb);
+        h[1] = te > tb ? row_of(e_off, rows, te - 1) : h[0];
+    }
+    __device__ void begin(int64_t i0, const int64_t* h) {
         e_end = *E;
         if (i0 >= e_end) return;
-        row = row_of(e_off, rows, i0);
+        row = row_in(e_off, h[0], h[1], i0);
         nbase = seg[row] - e_off[row];
     }
     __device__ bool eval(int64_t i, uint32_t& v) {
@@ -153,19 +182,6 @@ struct NonTreeF {
     __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? first_row_at(e_off, row, i) : -1; }
     __device__ void at(int64_t r, int64_t rank_) const { set_rows_at(e_off, rows, r, n_off, rank_); }
     __device__ int64_t end() const { return *E; }
-};
-
-// candidate ids from a bitmap, in id order
-struct BitsF {
-    using value_type = int32_t;
-    const uint32_t* bits;
-    __device__ void begin(int64_t) {}
-    __device__ bool eval(int64_t i, int32_t& v) const {
-        v = (int32_t)i;
-        return (bits[i >> 5] >> (i & 31)) & 1u;
-    }
-    __device__ int64_t tag(int64_t) const { return -1; }
-    __device__ void at(int64_t, int64_t) const {}
 };
 
 // rows kept by a validity mask
@@ -208,10 +224,16 @@ struct WriteAliveF {
     int64_t rows;
     int64_t row;
     int64_t e_end;
-    __device__ void begin(int64_t i0) {
+    __device__ void tile_hint(int64_t tb, int64_t te, int64_t* h) {
+        const int64_t r = *nrows, e = off[r];
+        if (te > e) te = e;
+        h[0] = row_of(off, r, tb);
+        h[1] = te > tb ? row_of(off, r, te - 1) : h[0];
+    }
+    __device__ void begin(int64_t i0, const int64_t* h) {
         rows = *nrows;
         e_end = off[rows];
-        if (i0 < e_end) row = row_of(off, rows, i0);
+        if (i0 < e_end) row = row_in(off, h[0], h[1], i0);
     }
     __device__ bool eval(int64_t i, uint32_t& v) {
         v = 0;

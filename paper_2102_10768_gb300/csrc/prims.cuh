@@ -208,21 +208,71 @@ constexpr unsigned long long kLbAgg = 1ull << 62, kLbPre = 2ull << 62, kLbVal = 
 constexpr int kLbSpins = 1 << 24;
 static __device__ int g_lookback_err;
 
-__device__ __forceinline__ int64_t lookback_prefix(unsigned long long* st, int64_t t) {
+// The exclusive prefix of tile t >= 1, by the 32 lanes of one warp: each
+// round reads the status words of the 32 tiles before the window's end at
+// once, waits (bounded) until each has published, and stops at the nearest
+// one whose inclusive prefix is known, summing the aggregates after it.
+__device__ __forceinline__ int64_t lookback_prefix_warp(unsigned long long* st, int64_t t) {
+    const int lane = threadIdx.x & 31;
     int64_t excl = 0;
-    for (int64_t p = t - 1; p >= 0; p--) {
-        unsigned long long w = 0;
-        int spins = 0;
-        for (;;) {
-            w = *(volatile unsigned long long*)(st + p);
-            if (w >> 62) break;
-            if (++spins > kLbSpins) { atomicExch(&g_lookback_err, 1); return excl; }
-            __nanosleep(32);
+    for (int64_t hi = t - 1;; hi -= 32) {
+        const int64_t p = hi - lane;
+        unsigned long long w = kLbPre;                 // before tile 0: a prefix of 0
+        if (p >= 0) {
+            int spins = 0;
+            for (;;) {
+                w = *(volatile unsigned long long*)(st + p);
+                if (w >> 62) break;
+                if (++spins > kLbSpins) { atomicExch(&g_lookback_err, 1); w = kLbPre; break; }
+                __nanosleep(32);
+            }
         }
-        excl += (int64_t)(w & kLbVal);
-        if ((w >> 62) == 2) break;
+        const unsigned pre = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+        const int stop = pre ? __ffs(pre) - 1 : 31;    // the nearest prefix (lane 0 is tile hi)
+        int64_t v = lane <= stop ? (int64_t)(w & kLbVal) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pre) break;
     }
     return excl;
+}
+
+// Warp 0 of a block: publish tile t's count `tot` (t relative to its
+// index space's first tile, status words st), find its exclusive offset and
+// publish its inclusive prefix.  Returns the offset on every lane of warp 0.
+__device__ __forceinline__ int64_t tile_publish(unsigned long long* st, int64_t t, int64_t tot) {
+    const int lane = threadIdx.x & 31;
+    int64_t excl = 0;
+    if (t == 0) {
+        if (lane == 0) atomicExch(st, kLbPre | (unsigned long long)tot);
+    } else {
+        if (lane == 0) atomicExch(st + t, kLbAgg | (unsigned long long)tot);
+        excl = lookback_prefix_warp(st, t);
+        if (lane == 0) atomicExch(st + t, kLbPre | (unsigned long long)(excl + tot));
+    }
+    return excl;
+}
+
+// A functor may narrow its per-thread setup with a hint computed once per
+// tile: `__device__ void tile_hint(int64_t tb, int64_t te, int64_t* h)` (by
+// one thread, h[0..1]) and `__device__ void begin(int64_t i0, const int64_t*
+// h)` (by every thread).  Functors without it get begin(i0).
+template <class F, class = void>
+struct has_hint : std::false_type {};
+template <class F>
+struct has_hint<F, std::void_t<decltype(std::declval<F&>().tile_hint(int64_t(0), int64_t(0), (int64_t*)nullptr))>>
+    : std::true_type {};
+
+template <class F>
+__device__ __forceinline__ void tile_hint_of(F& g, int64_t tb, int64_t te, int64_t* h) {
+    if constexpr (has_hint<F>::value) g.tile_hint(tb, te, h);
+}
+
+template <class F>
+__device__ __forceinline__ void begin_with(F& g, int64_t i0, const int64_t* h) {
+    if constexpr (has_hint<F>::value) g.begin(i0, h);
+    else g.begin(i0);
 }
 
 template <class F>
@@ -230,10 +280,14 @@ __global__ void __launch_bounds__(kCompBlock) k_compact_1p(F f, int64_t n, typen
                                                            int64_t* __restrict__ count, unsigned long long* __restrict__ st,
                                                            unsigned int* __restrict__ tile_ctr) {
     __shared__ int64_t tmp[kCompBlock / 32 + 1];
-    __shared__ int64_t s_t, s_excl, s_end;
+    __shared__ int64_t s_t, s_excl, s_end, s_hint[2];
     if (threadIdx.x == 0) s_end = index_end(f, n);
     for (;;) {
-        if (threadIdx.x == 0) s_t = (int64_t)atomicAdd(tile_ctr, 1u);
+        if (threadIdx.x == 0) {
+            s_t = (int64_t)atomicAdd(tile_ctr, 1u);
+            const int64_t tb = s_t * kCompTile;
+            if (tb < s_end) tile_hint_of(f, tb, tb + kCompTile < s_end ? tb + kCompTile : s_end, s_hint);
+        }
         __syncthreads();
         const int64_t t = s_t, end = s_end;
         const int64_t tb = t * kCompTile;
@@ -246,7 +300,7 @@ __global__ void __launch_bounds__(kCompBlock) k_compact_1p(F f, int64_t n, typen
         typename F::value_type val[kCompItems];
         int64_t tg[kCompItems];
         F g = f;
-        g.begin(base);
+        begin_with(g, base, s_hint);
 #pragma unroll
         for (int i = 0; i < kCompItems; i++) {
             v[i] = (base + i < end && g.eval(base + i, val[i])) ? 1 : 0;
@@ -256,17 +310,12 @@ __global__ void __launch_bounds__(kCompBlock) k_compact_1p(F f, int64_t n, typen
 #pragma unroll
         for (int i = 0; i < kCompItems; i++) hit[i] = v[i];
         const int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kCompItems>(v, tmp);
-        if (threadIdx.x == 0) {
-            int64_t excl = 0;
-            if (t == 0) {
-                atomicExch(st, kLbPre | (unsigned long long)tot);
-            } else {
-                atomicExch(st + t, kLbAgg | (unsigned long long)tot);
-                excl = lookback_prefix(st, t);
-                atomicExch(st + t, kLbPre | (unsigned long long)(excl + tot));
+        if (threadIdx.x < 32) {
+            const int64_t excl = tile_publish(st, t, tot);
+            if (threadIdx.x == 0) {
+                s_excl = excl;
+                if (tb + kCompTile >= end && count) *count = excl + tot;   // the last tile
             }
-            s_excl = excl;
-            if (tb + kCompTile >= end && count) *count = excl + tot;   // the last tile
         }
         __syncthreads();
         const int64_t off = s_excl;

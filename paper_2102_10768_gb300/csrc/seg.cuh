@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kCompBlock) k_compact_seg(const CompactSeg<F>*
                                                             unsigned long long* __restrict__ st,
                                                             unsigned int* __restrict__ tile_ctr) {
     __shared__ int64_t tmp[kCompBlock / 32 + 1];
-    __shared__ int64_t s_t, s_excl, s_end, s_first;
+    __shared__ int64_t s_t, s_excl, s_end, s_first, s_hint[2];
     __shared__ int s_seg;
     const int64_t total = tile_off[nseg];
     for (;;) {
@@ -92,6 +92,11 @@ __global__ void __launch_bounds__(kCompBlock) k_compact_seg(const CompactSeg<F>*
                 s_seg = sg;
                 s_first = tile_off[sg];
                 s_end = index_end(segs[sg].f, segs[sg].n);
+                const int64_t tb = (t - s_first) * kCompTile;
+                if (tb < s_end) {
+                    F h = segs[sg].f;
+                    tile_hint_of(h, tb, tb + kCompTile < s_end ? tb + kCompTile : s_end, s_hint);
+                }
             }
         }
         __syncthreads();
@@ -110,7 +115,7 @@ __global__ void __launch_bounds__(kCompBlock) k_compact_seg(const CompactSeg<F>*
         typename F::value_type val[kCompItems];
         int64_t tg[kCompItems];
         F g = sd.f;
-        g.begin(base);
+        begin_with(g, base, s_hint);
 #pragma unroll
         for (int i = 0; i < kCompItems; i++) {
             v[i] = (base + i < end && g.eval(base + i, val[i])) ? 1 : 0;
@@ -120,18 +125,12 @@ __global__ void __launch_bounds__(kCompBlock) k_compact_seg(const CompactSeg<F>*
 #pragma unroll
         for (int i = 0; i < kCompItems; i++) hit[i] = v[i];
         const int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kCompItems>(v, tmp);
-        if (threadIdx.x == 0) {
-            unsigned long long* sst = st + s_first;
-            int64_t excl = 0;
-            if (lt == 0) {
-                atomicExch(sst, kLbPre | (unsigned long long)tot);
-            } else {
-                atomicExch(sst + lt, kLbAgg | (unsigned long long)tot);
-                excl = lookback_prefix(sst, lt);
-                atomicExch(sst + lt, kLbPre | (unsigned long long)(excl + tot));
+        if (threadIdx.x < 32) {
+            const int64_t excl = tile_publish(st + s_first, lt, tot);
+            if (threadIdx.x == 0) {
+                s_excl = excl;
+                if (tb + kCompTile >= end && sd.count) *sd.count = excl + tot;
             }
-            s_excl = excl;
-            if (tb + kCompTile >= end && sd.count) *sd.count = excl + tot;
         }
         __syncthreads();
         const int64_t off = s_excl;
@@ -162,6 +161,107 @@ int compact_seg(const std::vector<CompactSeg<F>>& segs, cudaStream_t s) {
             (unsigned long long*)(b.base + b.st_at), (unsigned int*)(b.base + b.st_at + b.tiles * sizeof(unsigned long long)));
         note_launch();
         if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "segmented compaction launch");
+    }
+    dfree(b.base, s);
+    return rc;
+}
+
+// ------------------------------------------------------- bitmap -> ids
+//
+// The ids of the set bits of each segment's bitmap (bits [0, nbits)), in
+// increasing order, and their number: a compaction over 32-bit words, whose
+// tiles count their words' bits, find their offsets by the same look-back,
+// then write each word's ids.
+
+struct BitsSeg {
+    const uint32_t* bits;
+    int64_t nbits;
+    int32_t* out;
+    int64_t* count;                           // device, nullable
+};
+
+constexpr int kBitsItems = 8;                 // words per thread
+constexpr int kBitsTile = kCompBlock * kBitsItems;
+
+static __global__ void __launch_bounds__(kCompBlock) k_bits_ids_seg(const BitsSeg* __restrict__ segs,
+                                                             const int64_t* __restrict__ tile_off, int nseg,
+                                                             unsigned long long* __restrict__ st,
+                                                             unsigned int* __restrict__ tile_ctr) {
+    __shared__ int64_t tmp[kCompBlock / 32 + 1];
+    __shared__ int64_t s_t, s_excl, s_first;
+    __shared__ int s_seg;
+    const int64_t total = tile_off[nseg];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int64_t t = (int64_t)atomicAdd(tile_ctr, 1u);
+            s_t = t;
+            if (t < total) {
+                const int sg = seg_of_tile(tile_off, nseg, t);
+                s_seg = sg;
+                s_first = tile_off[sg];
+            }
+        }
+        __syncthreads();
+        const int64_t t = s_t;
+        if (t >= total) break;
+        const BitsSeg& sd = segs[s_seg];
+        const int64_t lt = t - s_first;
+        const int64_t nw = (sd.nbits + 31) >> 5;
+        const int64_t tb = lt * kBitsTile;
+        if (tb >= nw) {                                   // an empty bitmap
+            if (lt == 0 && threadIdx.x == 0 && sd.count) *sd.count = 0;
+            __syncthreads();
+            continue;
+        }
+        const int64_t base = tb + (int64_t)threadIdx.x * kBitsItems;
+        uint32_t w[kBitsItems];
+        int64_t v[kBitsItems];
+#pragma unroll
+        for (int i = 0; i < kBitsItems; i++) {
+            const int64_t x = base + i;
+            uint32_t b = x < nw ? sd.bits[x] : 0u;
+            if (x == nw - 1 && (sd.nbits & 31)) b &= (1u << (sd.nbits & 31)) - 1u;   // bits past nbits
+            w[i] = b;
+            v[i] = __popc(b);
+        }
+        const int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kBitsItems>(v, tmp);
+        if (threadIdx.x < 32) {
+            const int64_t excl = tile_publish(st + s_first, lt, tot);
+            if (threadIdx.x == 0) {
+                s_excl = excl;
+                if (tb + kBitsTile >= nw && sd.count) *sd.count = excl + tot;
+            }
+        }
+        __syncthreads();
+        int64_t o = s_excl + v[0];
+        int32_t* out = sd.out;
+#pragma unroll
+        for (int i = 0; i < kBitsItems; i++) {
+            uint32_t b = w[i];
+            const int32_t id0 = (int32_t)((base + i) << 5);
+            while (b) {
+                out[o++] = id0 + (__ffs(b) - 1);
+                b &= b - 1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+inline int bits_ids_seg(const std::vector<BitsSeg>& segs, cudaStream_t s) {
+    if (segs.empty()) return FAST_OK;
+    std::vector<int64_t> nw(segs.size());
+    for (size_t i = 0; i < segs.size(); i++) nw[i] = (segs[i].nbits + 31) >> 5;
+    const std::vector<int64_t> toff = seg_tile_offsets(nw, kBitsTile);
+    SegBlock b;
+    int rc = seg_block_upload(segs, toff, &b, s);
+    if (rc == FAST_OK) {
+        const int64_t grid = std::min<int64_t>(b.tiles, (int64_t)num_sms() * 4);
+        k_bits_ids_seg<<<(unsigned)grid, kCompBlock, 0, s>>>(
+            (const BitsSeg*)b.base, (const int64_t*)(b.base + b.off_at), (int)segs.size(),
+            (unsigned long long*)(b.base + b.st_at), (unsigned int*)(b.base + b.st_at + b.tiles * sizeof(unsigned long long)));
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(FAST_ERR_CUDA, "bitmap ids launch");
     }
     dfree(b.base, s);
     return rc;
@@ -219,18 +319,12 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_seg(const ScanSeg<T>* __res
             v[i] = x < n ? (sd.bits ? (T)__popc(sd.bits[x]) : sd.in[x]) : T(0);
         }
         const T tot = block_exclusive_scan<T, kScanBlock, kScanItems>(v, tmp);
-        if (threadIdx.x == 0) {
-            unsigned long long* sst = st + s_first;
-            int64_t excl = 0;
-            if (lt == 0) {
-                atomicExch(sst, kLbPre | (unsigned long long)tot);
-            } else {
-                atomicExch(sst + lt, kLbAgg | (unsigned long long)tot);
-                excl = lookback_prefix(sst, lt);
-                atomicExch(sst + lt, kLbPre | (unsigned long long)(excl + (int64_t)tot));
+        if (threadIdx.x < 32) {
+            const int64_t excl = tile_publish(st + s_first, lt, (int64_t)tot);
+            if (threadIdx.x == 0) {
+                s_excl = excl;
+                if (tb + kScanTile >= n && sd.total) *sd.total = (T)(excl + (int64_t)tot);
             }
-            s_excl = excl;
-            if (tb + kScanTile >= n && sd.total) *sd.total = (T)(excl + (int64_t)tot);
         }
         __syncthreads();
         const T off = (T)s_excl;

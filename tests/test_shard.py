@@ -114,16 +114,18 @@ def test_gpu_chunk_shares_add_up():
     import paper_2102_10768_gb300 as F
     import synth
     F.build()
-    n, e, lab = synth.powerlaw_graph(seed=2000, n=50_000, m=600_000)
-    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
-    wg = synth.WalkGraph(n, e)
-    qs = synth.mixed_queries(wg, lab, (4, 6), 4, 77)
+    w = synth.er_workload()
+    g, o = F.Graph(w.n, w.edges, w.labels), oracle.Graph(w.n, w.edges, w.labels)
+    wg = synth.WalkGraph(w.n, w.edges)
+    qs = [wg.query(w.labels, k, kind, 78, 10 * k + j) for k in (4, 5, 6) for j, kind in enumerate(("induced", "sparse"))]
     wg.close()
-    for ql, qe in qs:
-        r0 = oracle.match(o, ql, qe, budget=20_000_000)
-        if not r0["complete"]:
-            continue
-        cst = F.Cst(g, ql, qe)
+    qs += w.queries
+    compared = 0
+    ch = None
+    for q in qs:
+        r0 = oracle.match(o, q.labels, q.edges, budget=20_000_000)
+        assert r0["complete"]
+        cst = F.Cst(g, q.labels, q.edges)
         ch = F.Chunks(cst, F.default_config(delta_w=max(1, cst.W // 64), max_chunks=512))
         whole = F.match(cst, ch)["count"]
         assert whole == r0["count"]
@@ -137,5 +139,7 @@ def test_gpu_chunk_shares_add_up():
                 tot += F.match(cst, sub)["count"]
                 sub.close()
             assert tot == whole
+        compared += ch.n > 1
+    assert compared >= 4
     with pytest.raises(F.FastError):
         ch.select([ch.n])
