@@ -136,7 +136,7 @@ struct AnyAliveDesc {
 
 // A tile of a tile-split kernel: its segment, its entry range [tb, te) and
 // the rows of its first and last entries (every entry's row lies between),
-// found once per tile by thread 0.
+// found once per tile by warp 0.
 struct TileRows {
     int s;
     int64_t tb, te, r0, r1;
@@ -145,18 +145,18 @@ struct TileRows {
 template <class D>
 __device__ __forceinline__ bool tile_rows(const D* __restrict__ Dd, const int64_t* __restrict__ tile_off, int nseg,
                                           int64_t t, TileRows* sh) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         const int s = seg_of_tile(tile_off, nseg, t);
         const D& d = Dd[s];
         const int64_t e_end = d.off[d.rows];
         const int64_t tb = (t - tile_off[s]) * kTileItems;
-        sh->s = s;
-        sh->tb = tb;
-        sh->te = tb + kTileItems < e_end ? tb + kTileItems : e_end;
-        if (tb < e_end) {
-            sh->r0 = row_of(d.off, d.rows, tb);
-            sh->r1 = row_of(d.off, d.rows, sh->te - 1);
+        const int64_t te = tb + kTileItems < e_end ? tb + kTileItems : e_end;
+        int64_t r0 = 0, r1 = 0;
+        if (tb < te) {
+            r0 = warp_row_of(d.off, d.rows, tb);
+            r1 = warp_row_of(d.off, d.rows, te - 1);
         }
+        if (threadIdx.x == 0) { sh->s = s; sh->tb = tb; sh->te = te; sh->r0 = r0; sh->r1 = r1; }
     }
     __syncthreads();
     return sh->tb < sh->te;

@@ -105,8 +105,9 @@ struct TopDownF {
     __device__ void tile_hint(int64_t tb, int64_t te, int64_t* h) {
         const int64_t e = *E;
         if (te > e) te = e;
-        h[0] = row_of(e_off, rows, tb);
-        h[1] = te > tb ? row_of(e_off, rows, te - 1) : h[0];
+        const int64_t r0 = warp_row_of(e_off, rows, tb);
+        const int64_t r1 = te > tb ? warp_row_of(e_off, rows, te - 1) : r0;
+        if ((threadIdx.x & 31) == 0) { h[0] = r0; h[1] = r1; }
     }
     __device__ void begin(int64_t i0, const int64_t* h) {
         e_end = *E;
@@ -162,8 +163,9 @@ struct NonTreeF {
     __device__ void tile_hint(int64_t tb, int64_t te, int64_t* h) {
         const int64_t e = *E;
         if (te > e) te = e;
-        h[0] = row_of(e_off, rows, tb);
-        h[1] = te > tb ? row_of(e_off, rows, te - 1) : h[0];
+        const int64_t r0 = warp_row_of(e_off, rows, tb);
+        const int64_t r1 = te > tb ? warp_row_of(e_off, rows, te - 1) : r0;
+        if ((threadIdx.x & 31) == 0) { h[0] = r0; h[1] = r1; }
     }
     __device__ void begin(int64_t i0, const int64_t* h) {
         e_end = *E;
@@ -227,8 +229,9 @@ struct WriteAliveF {
     __device__ void tile_hint(int64_t tb, int64_t te, int64_t* h) {
         const int64_t r = *nrows, e = off[r];
         if (te > e) te = e;
-        h[0] = row_of(off, r, tb);
-        h[1] = te > tb ? row_of(off, r, te - 1) : h[0];
+        const int64_t r0 = warp_row_of(off, r, tb);
+        const int64_t r1 = te > tb ? warp_row_of(off, r, te - 1) : r0;
+        if ((threadIdx.x & 31) == 0) { h[0] = r0; h[1] = r1; }
     }
     __device__ void begin(int64_t i0, const int64_t* h) {
         rows = *nrows;

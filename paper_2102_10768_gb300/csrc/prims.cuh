@@ -254,10 +254,32 @@ __device__ __forceinline__ int64_t tile_publish(unsigned long long* st, int64_t 
     return excl;
 }
 
+// The last r in [0, rows) with e_off[r] <= i (e_off non-decreasing,
+// e_off[0] <= i < e_off[rows]), by the 32 lanes of a warp together: each
+// round probes 32 points of the interval at once and keeps the 1/33 between
+// two of them, so a search over a million rows takes four rounds of
+// parallel loads instead of twenty dependent ones.  Every lane returns it.
+__device__ __forceinline__ int64_t warp_row_of(const int64_t* __restrict__ e_off, int64_t rows, int64_t i) {
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = rows;                            // e_off[lo] <= i < e_off[hi]
+    while (hi - lo > 1) {
+        const int64_t span = hi - lo;
+        const int64_t p = lo + (span * (lane + 1)) / 33;  // non-decreasing in the lane, in [lo, hi)
+        const unsigned m = __ballot_sync(0xffffffffu, e_off[p] <= i);
+        const int c = __popc(m);                          // the probes with e_off <= i form a prefix
+        const int64_t plo = __shfl_sync(0xffffffffu, p, c > 0 ? c - 1 : 0);
+        const int64_t phi = __shfl_sync(0xffffffffu, p, c < 32 ? c : 31);
+        if (c > 0) lo = plo;                              // e_off[plo] <= i
+        if (c < 32) hi = phi;                             // e_off[phi] > i, so phi > plo
+    }
+    return lo;
+}
+
 // A functor may narrow its per-thread setup with a hint computed once per
 // tile: `__device__ void tile_hint(int64_t tb, int64_t te, int64_t* h)` (by
-// one thread, h[0..1]) and `__device__ void begin(int64_t i0, const int64_t*
-// h)` (by every thread).  Functors without it get begin(i0).
+// the 32 lanes of warp 0 together; lane 0 writes h[0..1]) and `__device__
+// void begin(int64_t i0, const int64_t* h)` (by every thread).  Functors
+// without it get begin(i0).
 template <class F, class = void>
 struct has_hint : std::false_type {};
 template <class F>
@@ -275,56 +297,80 @@ __device__ __forceinline__ void begin_with(F& g, int64_t i0, const int64_t* h) {
     else g.begin(i0);
 }
 
+// Shared memory of a compaction block.
+struct CompShared {
+    int32_t tmp[kCompBlock / 32 + 1];
+    int64_t t, end, first, excl, hint[2];
+    int seg;
+};
+
+// One tile [tb, tb + kCompTile) of an index space ending at `end`: evaluate,
+// scan (tile-local counts fit in 32 bits), publish and look back through
+// the status words `st` of the index space (tile lt of it), write.  Every
+// thread of the block calls it; `g` has had its begin().
 template <class F>
-__global__ void __launch_bounds__(kCompBlock) k_compact_1p(F f, int64_t n, typename F::value_type* __restrict__ out,
-                                                           int64_t* __restrict__ count, unsigned long long* __restrict__ st,
-                                                           unsigned int* __restrict__ tile_ctr) {
-    __shared__ int64_t tmp[kCompBlock / 32 + 1];
-    __shared__ int64_t s_t, s_excl, s_end, s_hint[2];
-    if (threadIdx.x == 0) s_end = index_end(f, n);
-    for (;;) {
+__device__ __forceinline__ void compact_tile(F& g, int64_t tb, int64_t end, unsigned long long* st, int64_t lt,
+                                             typename F::value_type* __restrict__ out, int64_t* count,
+                                             CompShared& sh) {
+    const int64_t base = tb + (int64_t)threadIdx.x * kCompItems;
+    int32_t v[kCompItems];
+    int32_t tg[kCompItems];
+    typename F::value_type val[kCompItems];
+    uint32_t hit = 0;
+#pragma unroll
+    for (int i = 0; i < kCompItems; i++) {
+        const bool in = base + i < end;
+        const bool k = in && g.eval(base + i, val[i]);
+        v[i] = k ? 1 : 0;
+        hit |= (k ? 1u : 0u) << i;
+        tg[i] = in ? (int32_t)g.tag(base + i) : -1;         // rows and tags are below 2^31
+    }
+    const int32_t tot = block_exclusive_scan<int32_t, kCompBlock, kCompItems>(v, sh.tmp);
+    if (threadIdx.x < 32) {
+        const int64_t excl = tile_publish(st, lt, (int64_t)tot);
         if (threadIdx.x == 0) {
-            s_t = (int64_t)atomicAdd(tile_ctr, 1u);
-            const int64_t tb = s_t * kCompTile;
-            if (tb < s_end) tile_hint_of(f, tb, tb + kCompTile < s_end ? tb + kCompTile : s_end, s_hint);
+            sh.excl = excl;
+            if (tb + kCompTile >= end && count) *count = excl + tot;   // the last tile
+        }
+    }
+    __syncthreads();
+    const int64_t off = sh.excl;
+#pragma unroll
+    for (int i = 0; i < kCompItems; i++) {
+        if (tg[i] >= 0) g.at((int64_t)tg[i], off + v[i]);
+        if ((hit >> i) & 1u) out[off + v[i]] = val[i];
+    }
+    __syncthreads();
+}
+
+template <class F>
+__global__ void __launch_bounds__(kCompBlock, 4) k_compact_1p(F f, int64_t n, typename F::value_type* __restrict__ out,
+                                                              int64_t* __restrict__ count,
+                                                              unsigned long long* __restrict__ st,
+                                                              unsigned int* __restrict__ tile_ctr) {
+    __shared__ CompShared sh;
+    if (threadIdx.x == 0) sh.end = index_end(f, n);
+    __syncthreads();
+    const int64_t end = sh.end;
+    for (;;) {
+        if (threadIdx.x < 32) {                           // warp 0: take a tile, find its hint
+            int64_t t = 0;
+            if (threadIdx.x == 0) t = (int64_t)atomicAdd(tile_ctr, 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            const int64_t tb = t * kCompTile;
+            if (tb < end) tile_hint_of(f, tb, tb + kCompTile < end ? tb + kCompTile : end, sh.hint);
+            if (threadIdx.x == 0) sh.t = t;
         }
         __syncthreads();
-        const int64_t t = s_t, end = s_end;
+        const int64_t t = sh.t;
         const int64_t tb = t * kCompTile;
         if (tb >= end) {
             if (t == 0 && threadIdx.x == 0 && count) *count = 0;     // empty index space
             break;
         }
-        const int64_t base = tb + (int64_t)threadIdx.x * kCompItems;
-        int64_t v[kCompItems];
-        typename F::value_type val[kCompItems];
-        int64_t tg[kCompItems];
         F g = f;
-        begin_with(g, base, s_hint);
-#pragma unroll
-        for (int i = 0; i < kCompItems; i++) {
-            v[i] = (base + i < end && g.eval(base + i, val[i])) ? 1 : 0;
-            tg[i] = (base + i < end) ? g.tag(base + i) : -1;
-        }
-        int64_t hit[kCompItems];
-#pragma unroll
-        for (int i = 0; i < kCompItems; i++) hit[i] = v[i];
-        const int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kCompItems>(v, tmp);
-        if (threadIdx.x < 32) {
-            const int64_t excl = tile_publish(st, t, tot);
-            if (threadIdx.x == 0) {
-                s_excl = excl;
-                if (tb + kCompTile >= end && count) *count = excl + tot;   // the last tile
-            }
-        }
-        __syncthreads();
-        const int64_t off = s_excl;
-#pragma unroll
-        for (int i = 0; i < kCompItems; i++) {
-            if (tg[i] >= 0) g.at(tg[i], off + v[i]);
-            if (hit[i]) out[off + v[i]] = val[i];
-        }
-        __syncthreads();
+        begin_with(g, tb + (int64_t)threadIdx.x * kCompItems, sh.hint);
+        compact_tile(g, tb, end, st, t, out, count, sh);
     }
 }
 

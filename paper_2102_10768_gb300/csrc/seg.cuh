@@ -75,72 +75,49 @@ struct CompactSeg {
 };
 
 template <class F>
-__global__ void __launch_bounds__(kCompBlock) k_compact_seg(const CompactSeg<F>* __restrict__ segs,
-                                                            const int64_t* __restrict__ tile_off, int nseg,
-                                                            unsigned long long* __restrict__ st,
-                                                            unsigned int* __restrict__ tile_ctr) {
-    __shared__ int64_t tmp[kCompBlock / 32 + 1];
-    __shared__ int64_t s_t, s_excl, s_end, s_first, s_hint[2];
-    __shared__ int s_seg;
+__global__ void __launch_bounds__(kCompBlock, 4) k_compact_seg(const CompactSeg<F>* __restrict__ segs,
+                                                               const int64_t* __restrict__ tile_off, int nseg,
+                                                               unsigned long long* __restrict__ st,
+                                                               unsigned int* __restrict__ tile_ctr) {
+    __shared__ CompShared sh;
     const int64_t total = tile_off[nseg];
     for (;;) {
-        if (threadIdx.x == 0) {
-            const int64_t t = (int64_t)atomicAdd(tile_ctr, 1u);
-            s_t = t;
-            if (t < total) {
-                const int sg = seg_of_tile(tile_off, nseg, t);
-                s_seg = sg;
-                s_first = tile_off[sg];
-                s_end = index_end(segs[sg].f, segs[sg].n);
-                const int64_t tb = (t - s_first) * kCompTile;
-                if (tb < s_end) {
-                    F h = segs[sg].f;
-                    tile_hint_of(h, tb, tb + kCompTile < s_end ? tb + kCompTile : s_end, s_hint);
+        if (threadIdx.x < 32) {                           // warp 0: take a tile, find its segment and hint
+            int64_t t = 0, first = 0, end = 0;
+            int sg = 0;
+            if (threadIdx.x == 0) {
+                t = (int64_t)atomicAdd(tile_ctr, 1u);
+                if (t < total) {
+                    sg = seg_of_tile(tile_off, nseg, t);
+                    first = tile_off[sg];
+                    end = index_end(segs[sg].f, segs[sg].n);
                 }
             }
+            t = __shfl_sync(0xffffffffu, t, 0);
+            sg = __shfl_sync(0xffffffffu, sg, 0);
+            first = __shfl_sync(0xffffffffu, first, 0);
+            end = __shfl_sync(0xffffffffu, end, 0);
+            const int64_t tb = (t - first) * kCompTile;
+            if (t < total && tb < end) {
+                F h = segs[sg].f;
+                tile_hint_of(h, tb, tb + kCompTile < end ? tb + kCompTile : end, sh.hint);
+            }
+            if (threadIdx.x == 0) { sh.t = t; sh.seg = sg; sh.first = first; sh.end = end; }
         }
         __syncthreads();
-        const int64_t t = s_t;
+        const int64_t t = sh.t;
         if (t >= total) break;
-        const CompactSeg<F>& sd = segs[s_seg];
-        const int64_t lt = t - s_first, end = s_end;
+        const CompactSeg<F>& sd = segs[sh.seg];
+        const int64_t lt = t - sh.first, end = sh.end;
         const int64_t tb = lt * kCompTile;
         if (tb >= end) {                                   // past the segment's real end
             if (lt == 0 && threadIdx.x == 0 && sd.count) *sd.count = 0;
             __syncthreads();
             continue;
         }
-        const int64_t base = tb + (int64_t)threadIdx.x * kCompItems;
-        int64_t v[kCompItems];
-        typename F::value_type val[kCompItems];
-        int64_t tg[kCompItems];
         F g = sd.f;
-        begin_with(g, base, s_hint);
-#pragma unroll
-        for (int i = 0; i < kCompItems; i++) {
-            v[i] = (base + i < end && g.eval(base + i, val[i])) ? 1 : 0;
-            tg[i] = (base + i < end) ? g.tag(base + i) : -1;
-        }
-        int64_t hit[kCompItems];
-#pragma unroll
-        for (int i = 0; i < kCompItems; i++) hit[i] = v[i];
-        const int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kCompItems>(v, tmp);
-        if (threadIdx.x < 32) {
-            const int64_t excl = tile_publish(st + s_first, lt, tot);
-            if (threadIdx.x == 0) {
-                s_excl = excl;
-                if (tb + kCompTile >= end && sd.count) *sd.count = excl + tot;
-            }
-        }
-        __syncthreads();
-        const int64_t off = s_excl;
-        typename F::value_type* out = sd.out;
-#pragma unroll
-        for (int i = 0; i < kCompItems; i++) {
-            if (tg[i] >= 0) g.at(tg[i], off + v[i]);
-            if (hit[i]) out[off + v[i]] = val[i];
-        }
-        __syncthreads();
+        begin_with(g, tb + (int64_t)threadIdx.x * kCompItems, sh.hint);
+        compact_tile(g, tb, end, st + sh.first, lt, sd.out, sd.count, sh);
     }
 }
 
