@@ -141,6 +141,54 @@ struct TopDownF {
     // the label) starts where the next one does, so the first entry of a
     // row tags it and every empty row just before it
     __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? first_row_at(e_off, row, i) : -1; }
+    // eval and tag of N consecutive indices: positions first (the row walk),
+    // then every neighbour id, every filter word, every reached word at once
+    template <int N>
+    __device__ void eval_n(int64_t i0, int64_t end, uint32_t& keep, int32_t (&val)[N], int32_t (&tg)[N]) {
+        int64_t pos[N];
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            const int64_t i = i0 + j;
+            pos[j] = -1;
+            tg[j] = -1;
+            if (i < end) {
+                while (i >= e_off[row + 1]) { row++; nbase = seg[row] - e_off[row]; }
+                pos[j] = nbase + i;
+                if (i == e_off[row]) tg[j] = (int32_t)first_row_at(e_off, row, i);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < N; j++) val[j] = pos[j] >= 0 ? __ldg(col + pos[j]) : 0;
+        uint32_t k = 0;
+        if (pass) {
+            uint32_t w[N];
+#pragma unroll
+            for (int j = 0; j < N; j++) w[j] = pos[j] >= 0 ? __ldg(pass + (val[j] >> 5)) : 0u;
+#pragma unroll
+            for (int j = 0; j < N; j++) k |= ((w[j] >> (val[j] & 31)) & 1u) << j;
+        } else if (label_known && want_dq <= 1) {
+#pragma unroll
+            for (int j = 0; j < N; j++) k |= (pos[j] >= 0 ? 1u : 0u) << j;
+        } else {
+            int32_t kk[N];
+#pragma unroll
+            for (int j = 0; j < N; j++) kk[j] = pos[j] >= 0 ? __ldg(key + val[j]) : -1;
+#pragma unroll
+            for (int j = 0; j < N; j++)
+                k |= ((pos[j] >= 0 && (kk[j] >> 8) == want_key_hi && (kk[j] & 255) >= want_dq) ? 1u : 0u) << j;
+        }
+        if (!counting) {
+            uint32_t r[N];
+#pragma unroll
+            for (int j = 0; j < N; j++) r[j] = ((k >> j) & 1u) ? __ldcg(reached + (val[j] >> 5)) : ~0u;
+#pragma unroll
+            for (int j = 0; j < N; j++) {
+                const uint32_t bit = 1u << (val[j] & 31);
+                if (!(r[j] & bit)) atomicOr(&reached[val[j] >> 5], bit);
+            }
+        }
+        keep = k;
+    }
     __device__ void at(int64_t r, int64_t rank) const { set_rows_at(e_off, rows, r, t_off, rank); }
     __device__ int64_t end() const { return *E; }
 };
@@ -182,6 +230,38 @@ struct NonTreeF {
         return (w & bit) != 0;
     }
     __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? first_row_at(e_off, row, i) : -1; }
+    template <int N>
+    __device__ void eval_n(int64_t i0, int64_t end, uint32_t& keep, uint32_t (&val)[N], int32_t (&tg)[N]) {
+        int64_t pos[N];
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            const int64_t i = i0 + j;
+            pos[j] = -1;
+            tg[j] = -1;
+            if (i < end) {
+                while (i >= e_off[row + 1]) { row++; nbase = seg[row] - e_off[row]; }
+                pos[j] = nbase + i;
+                if (i == e_off[row]) tg[j] = (int32_t)first_row_at(e_off, row, i);
+            }
+        }
+        int32_t x[N];
+#pragma unroll
+        for (int j = 0; j < N; j++) x[j] = pos[j] >= 0 ? __ldg(col + pos[j]) : 0;
+        uint32_t w[N], rk[N];
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            w[j] = pos[j] >= 0 ? __ldg(alive + (x[j] >> 5)) : 0u;
+            rk[j] = pos[j] >= 0 ? __ldg(rank + (x[j] >> 5)) : 0u;
+        }
+        uint32_t k = 0;
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            const uint32_t bit = 1u << (x[j] & 31);
+            val[j] = rk[j] + __popc(w[j] & (bit - 1));
+            k |= ((w[j] & bit) ? 1u : 0u) << j;
+        }
+        keep = k;
+    }
     __device__ void at(int64_t r, int64_t rank_) const { set_rows_at(e_off, rows, r, n_off, rank_); }
     __device__ int64_t end() const { return *E; }
 };
@@ -249,6 +329,38 @@ struct WriteAliveF {
         return (wd & bit) != 0;
     }
     __device__ int64_t tag(int64_t i) const { return (i < e_end && i == off[row] && valid[row]) ? row : -1; }
+    template <int N>
+    __device__ void eval_n(int64_t i0, int64_t end, uint32_t& keep, uint32_t (&val)[N], int32_t (&tg)[N]) {
+        bool ok[N];
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            const int64_t i = i0 + j;
+            ok[j] = false;
+            tg[j] = -1;
+            if (i < end) {
+                while (i >= off[row + 1]) row++;
+                ok[j] = valid[row] != 0;
+                if (ok[j] && i == off[row]) tg[j] = (int32_t)row;
+            }
+        }
+        int32_t x[N];
+#pragma unroll
+        for (int j = 0; j < N; j++) x[j] = ok[j] ? __ldg(list + i0 + j) : 0;
+        uint32_t w[N], rk[N];
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            w[j] = ok[j] ? __ldg(alive + (x[j] >> 5)) : 0u;
+            rk[j] = ok[j] ? __ldg(rank + (x[j] >> 5)) : 0u;
+        }
+        uint32_t k = 0;
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            const uint32_t bit = 1u << (x[j] & 31);
+            val[j] = rk[j] + __popc(w[j] & (bit - 1));
+            k |= ((w[j] & bit) ? 1u : 0u) << j;
+        }
+        keep = k;
+    }
     __device__ void at(int64_t r, int64_t rk) const { new_off[newrow[r]] = rk; }
     __device__ int64_t end() const { return off[*nrows]; }
 };

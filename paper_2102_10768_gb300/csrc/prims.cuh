@@ -122,7 +122,8 @@ int scan_exclusive(const T* in, T* out, int64_t n, T* total, cudaStream_t s) {
 // starts); F::at(tag, rank) then receives the number of kept indices before
 // i (used to write list offsets).
 
-constexpr int kCompBlock = 256;
+constexpr int kCompBlock = 128;
+constexpr int kCompBlocksPerSM = 8;            // small blocks: one waiting on its look-back leaves 7 running
 constexpr int kCompItems = 8;
 constexpr int kCompTile = kCompBlock * kCompItems;
 
@@ -297,6 +298,20 @@ __device__ __forceinline__ void begin_with(F& g, int64_t i0, const int64_t* h) {
     else g.begin(i0);
 }
 
+// A functor may also evaluate a thread's kCompItems consecutive indices at
+// once, so that their independent loads are in flight together:
+//   template <int N> __device__ void eval_n(int64_t i0, int64_t end,
+//       uint32_t& keep, value_type (&val)[N], int32_t (&tag)[N])
+// sets bit j of keep, val[j] and tag[j] (-1: none) as eval(i0 + j) and
+// tag(i0 + j) would, for i0 + j < end (bits and tags of the others clear).
+template <class F, class = void>
+struct has_eval_n : std::false_type {};
+template <class F>
+struct has_eval_n<F, std::void_t<decltype(std::declval<F&>().template eval_n<kCompItems>(
+                         int64_t(0), int64_t(0), std::declval<uint32_t&>(),
+                         std::declval<typename F::value_type (&)[kCompItems]>(), std::declval<int32_t (&)[kCompItems]>()))>>
+    : std::true_type {};
+
 // Shared memory of a compaction block.
 struct CompShared {
     int32_t tmp[kCompBlock / 32 + 1];
@@ -317,13 +332,19 @@ __device__ __forceinline__ void compact_tile(F& g, int64_t tb, int64_t end, unsi
     int32_t tg[kCompItems];
     typename F::value_type val[kCompItems];
     uint32_t hit = 0;
+    if constexpr (has_eval_n<F>::value) {
+        g.template eval_n<kCompItems>(base, end, hit, val, tg);
 #pragma unroll
-    for (int i = 0; i < kCompItems; i++) {
-        const bool in = base + i < end;
-        const bool k = in && g.eval(base + i, val[i]);
-        v[i] = k ? 1 : 0;
-        hit |= (k ? 1u : 0u) << i;
-        tg[i] = in ? (int32_t)g.tag(base + i) : -1;         // rows and tags are below 2^31
+        for (int i = 0; i < kCompItems; i++) v[i] = (hit >> i) & 1u;
+    } else {
+#pragma unroll
+        for (int i = 0; i < kCompItems; i++) {
+            const bool in = base + i < end;
+            const bool k = in && g.eval(base + i, val[i]);
+            v[i] = k ? 1 : 0;
+            hit |= (k ? 1u : 0u) << i;
+            tg[i] = in ? (int32_t)g.tag(base + i) : -1;     // rows and tags are below 2^31
+        }
     }
     const int32_t tot = block_exclusive_scan<int32_t, kCompBlock, kCompItems>(v, sh.tmp);
     if (threadIdx.x < 32) {
@@ -344,7 +365,7 @@ __device__ __forceinline__ void compact_tile(F& g, int64_t tb, int64_t end, unsi
 }
 
 template <class F>
-__global__ void __launch_bounds__(kCompBlock, 4) k_compact_1p(F f, int64_t n, typename F::value_type* __restrict__ out,
+__global__ void __launch_bounds__(kCompBlock, kCompBlocksPerSM) k_compact_1p(F f, int64_t n, typename F::value_type* __restrict__ out,
                                                               int64_t* __restrict__ count,
                                                               unsigned long long* __restrict__ st,
                                                               unsigned int* __restrict__ tile_ctr) {
@@ -384,7 +405,7 @@ int compact(const F& f, int64_t n, typename F::value_type* out, int64_t* count_d
     unsigned long long* st = nullptr;                     // [nt] tile status, then the tile counter
     FAST_TRY(dalloc(&st, nt + 1, s));
     cudaMemsetAsync(st, 0, (nt + 1) * sizeof(unsigned long long), s);
-    const int64_t grid = std::min<int64_t>(nt, (int64_t)num_sms() * 4);
+    const int64_t grid = std::min<int64_t>(nt, (int64_t)num_sms() * kCompBlocksPerSM);
     k_compact_1p<F><<<(unsigned)grid, kCompBlock, 0, s>>>(f, n, out, count_dev, st, (unsigned int*)(st + nt));
     note_launch();
     int rc = cudaGetLastError() == cudaSuccess ? FAST_OK : set_error(FAST_ERR_CUDA, "compaction launch");

@@ -75,7 +75,7 @@ struct CompactSeg {
 };
 
 template <class F>
-__global__ void __launch_bounds__(kCompBlock, 4) k_compact_seg(const CompactSeg<F>* __restrict__ segs,
+__global__ void __launch_bounds__(kCompBlock, kCompBlocksPerSM) k_compact_seg(const CompactSeg<F>* __restrict__ segs,
                                                                const int64_t* __restrict__ tile_off, int nseg,
                                                                unsigned long long* __restrict__ st,
                                                                unsigned int* __restrict__ tile_ctr) {
@@ -132,7 +132,7 @@ int compact_seg(const std::vector<CompactSeg<F>>& segs, cudaStream_t s) {
     SegBlock b;
     int rc = seg_block_upload(segs, toff, &b, s);
     if (rc == FAST_OK) {
-        const int64_t grid = std::min<int64_t>(b.tiles, (int64_t)num_sms() * 4);
+        const int64_t grid = std::min<int64_t>(b.tiles, (int64_t)num_sms() * kCompBlocksPerSM);
         k_compact_seg<F><<<(unsigned)grid, kCompBlock, 0, s>>>(
             (const CompactSeg<F>*)b.base, (const int64_t*)(b.base + b.off_at), (int)segs.size(),
             (unsigned long long*)(b.base + b.st_at), (unsigned int*)(b.base + b.st_at + b.tiles * sizeof(unsigned long long)));
@@ -160,7 +160,7 @@ struct BitsSeg {
 constexpr int kBitsItems = 8;                 // words per thread
 constexpr int kBitsTile = kCompBlock * kBitsItems;
 
-static __global__ void __launch_bounds__(kCompBlock) k_bits_ids_seg(const BitsSeg* __restrict__ segs,
+static __global__ void __launch_bounds__(kCompBlock, kCompBlocksPerSM) k_bits_ids_seg(const BitsSeg* __restrict__ segs,
                                                              const int64_t* __restrict__ tile_off, int nseg,
                                                              unsigned long long* __restrict__ st,
                                                              unsigned int* __restrict__ tile_ctr) {
@@ -233,7 +233,7 @@ inline int bits_ids_seg(const std::vector<BitsSeg>& segs, cudaStream_t s) {
     SegBlock b;
     int rc = seg_block_upload(segs, toff, &b, s);
     if (rc == FAST_OK) {
-        const int64_t grid = std::min<int64_t>(b.tiles, (int64_t)num_sms() * 4);
+        const int64_t grid = std::min<int64_t>(b.tiles, (int64_t)num_sms() * kCompBlocksPerSM);
         k_bits_ids_seg<<<(unsigned)grid, kCompBlock, 0, s>>>(
             (const BitsSeg*)b.base, (const int64_t*)(b.base + b.off_at), (int)segs.size(),
             (unsigned long long*)(b.base + b.st_at), (unsigned int*)(b.base + b.st_at + b.tiles * sizeof(unsigned long long)));
