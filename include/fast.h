@@ -131,10 +131,20 @@ typedef struct {
      * embeddings.  Rule 2 is built by fast_build_cst_batch only (the batch
      * with build_rule >= 1); fast_build_cst and build_rule 0 reject it. */
     int32_t refine_rule;
+    /* The matcher kernel (Sec. V-A semantics either way).  0: fused -- every
+     * warp runs the whole search.  1: warp-specialised (the task-generator
+     * separation of Sec. V-D): in every CTA `validators` warps take, from a
+     * ring in shared memory, the last-position extensions that the other
+     * warps (the expanders) hand them, and count those positions' embeddings.
+     * Rule 1 applies to counting launches (no per-chunk counts, no embeddings
+     * written, no counting pass); the others run the fused kernel.  Results
+     * never depend on it. */
+    int32_t matcher_rule;
+    int32_t validators;      /* rule 1: validator warps per CTA (0: half of warps_per_block) */
 } fast_config;
 
 /* Default tunables: delta_w = 2^20, no sampling, max_chunks = 2^16,
- * 8 warps per CTA, 4 CTAs per SM, no time budget, no limit. */
+ * 8 warps per CTA, 4 CTAs per SM, no time budget, no limit, every rule 0. */
 void fast_config_default(fast_config* cfg);
 
 /* Thread-local message for the last failing call ("" if none). */

@@ -44,7 +44,8 @@ class Config(ctypes.Structure):
                 ("max_chunks", ctypes.c_int64), ("warps_per_block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("time_budget_s", ctypes.c_double),
                 ("limit", ctypes.c_uint64), ("queue_cells", ctypes.c_int64), ("order_rule", ctypes.c_int32),
-                ("filter_rule", ctypes.c_int32), ("build_rule", ctypes.c_int32), ("refine_rule", ctypes.c_int32)]
+                ("filter_rule", ctypes.c_int32), ("build_rule", ctypes.c_int32), ("refine_rule", ctypes.c_int32),
+                ("matcher_rule", ctypes.c_int32), ("validators", ctypes.c_int32)]
 
 
 class QueryDesc(ctypes.Structure):

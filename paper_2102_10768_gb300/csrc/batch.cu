@@ -36,7 +36,7 @@ size_t match_chunk_bytes();
 int match_batched_enqueue(const void* d_plans, int warp_words, const void* d_chunks, const int64_t* d_nchunks,
                           int max_q, unsigned long long* d_qtotal, int* d_qstop, unsigned long long* d_ctr,
                           void* d_dq, uint32_t* d_dq_state, uint64_t dq_cap, uint64_t limit, double budget_s,
-                          int warps, int bps, cudaStream_t s);
+                          int warps, int bps, int validators, cudaStream_t s);
 int match_smem_optin(size_t bytes);
 int match_status_of(const unsigned long long* h_ctr, uint64_t* bytes, uint64_t* floor);
 }  // namespace fast
@@ -77,7 +77,7 @@ struct fast_batch {
     unsigned char* d_dq = nullptr;
     uint32_t* d_dq_state = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int g_warp_words = -1, g_warps = -1, g_bps = -1;
+    int g_warp_words = -1, g_warps = -1, g_bps = -1, g_val = -1;
     double g_budget = -1.0;
     uint64_t g_limit = ~0ull;
     uint64_t g_cells = 0;
@@ -175,12 +175,14 @@ int batch_create(const fast_graph* g, const fast_config* cfg, int32_t max_q, int
 // (Re)capture the matcher launch as a graph when its shape changed.
 int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream_t s) {
     const uint64_t cells = lc.queue_cells > 0 ? std::min<uint64_t>((uint64_t)lc.queue_cells, kBatchQueue) : kBatchQueue;
+    int warps = lc.warps_per_block > 0 ? std::min(lc.warps_per_block, 8) : 8;
+    const int nval = lc.matcher_rule == 1 && warps >= 2 ? (lc.validators > 0 ? std::min(lc.validators, warps - 1) : warps / 2) : 0;
     if (b->exec && b->g_warp_words == warp_words && b->g_warps == lc.warps_per_block && b->g_bps == lc.blocks_per_sm &&
+        b->g_val == nval &&
         b->g_budget == lc.time_budget_s && b->g_limit == lc.limit && b->g_chunks == b->d_chunks &&
         b->g_cells == cells)
         return FAST_OK;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-    int warps = lc.warps_per_block > 0 ? std::min(lc.warps_per_block, 8) : 8;
     int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : 4;
     FAST_TRY(match_smem_optin((size_t)warps * warp_words * sizeof(uint32_t)));
     cudaStream_t cap;
@@ -192,7 +194,7 @@ int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream
     if (rc == FAST_OK) {
         int rc2 = match_batched_enqueue(b->d_plans, warp_words, b->d_chunks, b->d_nchunks, b->max_q, b->d_qtotal,
                                         b->d_qstop, b->d_ctr, b->d_dq, b->d_dq_state, cells, lc.limit,
-                                        lc.time_budget_s, warps, bps, cap);
+                                        lc.time_budget_s, warps, bps, nval, cap);
         e = cudaStreamEndCapture(cap, &graph);
         if (rc2 != FAST_OK) rc = rc2;
         else if (e != cudaSuccess) rc = cuda_status(e, "end capture", __FILE__, __LINE__);
@@ -225,6 +227,7 @@ int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream
         b->g_warp_words = warp_words; b->g_warps = lc.warps_per_block; b->g_bps = lc.blocks_per_sm;
         b->g_budget = lc.time_budget_s; b->g_limit = lc.limit; b->g_chunks = b->d_chunks; b->g_cells = cells;
         b->g_kernels = recorded;
+        b->g_val = nval;
     }
     return rc;
 }
@@ -341,6 +344,8 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
         fast_config lc = b->base;
         lc.warps_per_block = b->cls[0].warps_per_block;
         lc.blocks_per_sm = b->cls[0].blocks_per_sm;
+        lc.matcher_rule = b->cls[0].matcher_rule;
+        lc.validators = b->cls[0].validators;
         rc = batch_graph(b, warp_words, lc, s); if (rc) break;
         FAST_CUDA_BREAK(rc, cudaEventRecord(b->ev0, s));
         FAST_CUDA_BREAK(rc, cudaGraphLaunch(b->exec, s));

@@ -64,6 +64,8 @@ extern "C" void fast_config_default(fast_config* cfg) {
     cfg->filter_rule = 0;
     cfg->build_rule = 0;
     cfg->refine_rule = 0;
+    cfg->matcher_rule = 0;
+    cfg->validators = 0;
 }
 
 namespace {

@@ -28,6 +28,19 @@
 // a run of a list with a fixed prefix, i.e. again a chunk.  An outstanding-
 // work counter ends the launch.  No warp waits on another: the only wait, an
 // idle warp looking for work, is bounded by %globaltimer.
+//
+// Warp-specialised variant (the GPU form of the task-generator separation
+// of Sec. V-D): a CTA's warps split into expanders and validators.  The
+// expanders run the search above, but a partial result that reaches the
+// last position is not scanned there: its extension (the offsets of every
+// list into that position, the chosen generator list and the images so
+// far) goes into a ring in shared memory as a task, and the expander goes
+// on with the next partial result.  Validator warps take tasks and run the
+// last position's Generator, EdgeValidator, VisitedValidator and count.
+// The last position holds most of the work (hundreds of embeddings per
+// partial result on the workloads here), so the expanders' branchy,
+// latency-bound descent and the validators' streaming list scans overlap.
+// A full ring never blocks an expander: it scans that extension itself.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -114,7 +127,34 @@ struct MatchOut {
     unsigned long long* dq_tail;
     unsigned long long* outstanding;  // work items not yet finished
     unsigned int* idle;               // warps waiting for work
+    int validators;                   // warp-specialised variant: validator warps per CTA
 };
+
+// One last-position extension handed from an expander to a validator warp
+// (the warp-specialised variant): the lists into position k-1 -- index 0
+// the tree list, 1 + e the e-th non-tree edge into it -- as index ranges of
+// their arrays, which of them generates, and the images of positions
+// 0..k-2.
+struct VTask {
+    uint32_t q;                       // query (batched launches)
+    int32_t src;                      // the generator: 0 the tree list, s > 0 non-tree edge s-1
+    int64_t lo[kMaxK];
+    int64_t hi[kMaxK];
+    int32_t g[kMaxK];
+};
+constexpr int kRing = 8;                          // tasks per CTA
+constexpr unsigned long long kValidatorWaitNs = 30ull * 1000 * 1000 * 1000;   // never expected: error after
+// the ring's shared words: tickets of producers (tail) and consumers (head),
+// per cell a state (2g free for generation g, 2g+1 published), and the
+// expanders still running
+struct VRing {
+    unsigned long long head, tail;
+    uint32_t state[kRing];
+    int active;
+    int pad;
+    VTask task[kRing];
+};
+enum : int { kStatusValidator = 8 };
 
 __global__ void k_set_deadline(unsigned long long* d, unsigned long long budget_ns) {
     *d = budget_ns ? global_timer_ns() + budget_ns : 0ull;
@@ -264,9 +304,136 @@ __device__ int acquire(const MatchOut& O, int64_t nchunks, unsigned long long de
     return kind;
 }
 
+// lane 0: claim the ring's next cell for a producer, if it is free (a cell
+// still holding an older task means the ring is full).  Returns the ticket,
+// or ~0 when full.
+__device__ __forceinline__ unsigned long long ring_claim(VRing* ring) {
+    unsigned long long t = *(volatile unsigned long long*)&ring->tail;
+    for (int tries = 0; tries < 8; tries++) {
+        const uint32_t st = *(volatile uint32_t*)&ring->state[t % kRing];
+        if (st == (uint32_t)(2 * (t / kRing))) {
+            const unsigned long long prev = atomicCAS(&ring->tail, t, t + 1);
+            if (prev == t) return t;
+            t = prev;
+            continue;
+        }
+        const unsigned long long now = *(volatile unsigned long long*)&ring->tail;
+        if (now == t) break;                                   // full
+        t = now;
+    }
+    return ~0ull;
+}
+
+// A validator warp of the warp-specialised matcher: take published tasks
+// from the CTA's ring and count the embeddings of their last position --
+// the Generator over the chosen list, the EdgeValidator's merges against
+// the other lists (cursors in `cur`, one per list), the VisitedValidator
+// against the task's images.  Returns once every expander of the CTA has
+// left and the ring is empty.  Its bytes go to lb (each lane) and fb (lane
+// 0) as the fused search counts them.
+template <bool BATCH>
+__device__ void validate_tasks(const MatchPlan& P0, const MatchPlan* __restrict__ plans, VRing* ring, int64_t* cur,
+                               const MatchOut& O, unsigned long long deadline, unsigned long long& lb,
+                               unsigned long long& fb) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long waited_since = 0;
+    for (;;) {
+        long long got = -1;
+        if (lane == 0) {
+            for (;;) {
+                unsigned long long h = *(volatile unsigned long long*)&ring->head;
+                if (*(volatile uint32_t*)&ring->state[h % kRing] == (uint32_t)(2 * (h / kRing) + 1)) {
+                    if (atomicCAS(&ring->head, h, h + 1) == h) { got = (long long)h; break; }
+                    continue;
+                }
+                if (*(volatile int*)&ring->active == 0) {
+                    // every expander published its last task before it left: look once more
+                    h = *(volatile unsigned long long*)&ring->head;
+                    if (*(volatile uint32_t*)&ring->state[h % kRing] == (uint32_t)(2 * (h / kRing) + 1)) continue;
+                    got = -2;
+                    break;
+                }
+                const unsigned long long now = global_timer_ns();
+                if (!waited_since) waited_since = now;
+                else if (now - waited_since > kValidatorWaitNs) { atomicOr(O.status, kStatusValidator); got = -2; break; }
+                __nanosleep(128);
+            }
+            __threadfence_block();
+        }
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got < 0) return;
+        waited_since = 0;
+        __syncwarp();
+        const VTask& T = ring->task[got % kRing];
+        const uint32_t q = T.q;
+        const MatchPlan& P = BATCH ? plans[q] : P0;
+        const int d = P.k - 1;
+        const int e0 = P.nt_begin[d], ne = P.nt_begin[d + 1] - e0;
+        const int src = T.src;
+        const int64_t glo = T.lo[src], ghi = T.hi[src];
+        const uint32_t* gen = src == 0 ? P.t_idx[d] : P.n_idx[e0 + src - 1];
+        if (lane <= ne) cur[lane] = 0;
+        __syncwarp();
+        unsigned long long local = 0;
+        int it = 0;
+        bool stop = false;
+        for (int64_t sn = glo; sn < ghi && !stop; sn += 32) {
+            if ((++it & 255) == 0) {
+                int st = 0;
+                if (lane == 0) {
+                    flush_count(O, q, local);
+                    if (deadline && global_timer_ns() > deadline) atomicOr(O.status, kStatusTimeout);
+                    st = vload(O.status) & (kStatusTimeout | kStatusLimit);
+                    if (BATCH && *(volatile int*)&O.qstop[q]) st = 1;
+                }
+                stop = __shfl_sync(0xffffffffu, st, 0) != 0;
+                if (stop) break;
+            }
+            const int64_t idx = sn + lane;
+            bool ok = idx < ghi;
+            uint32_t cnd = 0;
+            if (ok) { cnd = __ldg(gen + idx); lb += 4; }
+            if (lane == 0) fb += 4ull * (unsigned long long)(ghi - sn < 32 ? ghi - sn : 32);
+            for (int x = 0; x <= ne; x++) {                     // the tree list, then the non-tree lists
+                if (x == src) continue;
+                if (!__any_sync(0xffffffffu, ok)) break;
+                const uint32_t* L = x == 0 ? P.t_idx[d] : P.n_idx[e0 + x - 1];
+                const int64_t lo = T.lo[x], hi = T.hi[x];
+                int64_t c = lo + cur[x];
+                ok = warp_member(L, lo, hi, &c, cnd, ok, &lb);
+                __syncwarp();
+                if (lane == 0) cur[x] = c - lo;
+                __syncwarp();
+            }
+            uint32_t sl = P.same_lab[d];
+            if (sl) {
+                const uint32_t pm = __ballot_sync(0xffffffffu, ok);
+                if (lane == 0) fb += 4ull * __popc(pm);
+                int32_t gc = -1;
+                if (ok) { gc = __ldg(P.cand[d] + cnd); lb += 4; }
+                while (sl) {
+                    const int p = __ffs(sl) - 1;
+                    sl &= sl - 1;
+                    if (T.g[p] == gc) ok = false;
+                }
+            }
+            const uint32_t mask = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) local += __popc(mask);
+        }
+        if (lane == 0) flush_count(O, q, local);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            atomicExch(&ring->state[got % kRing], (uint32_t)(2 * (got / kRing) + 2));   // free for ticket + kRing
+        }
+    }
+}
+
 // BATCH: plans[q] per query (chunk flags carry q, nchunks is read from
 // *nchunks_dev); otherwise the single plan P0 and the nchunks argument.
-template <bool STATS, bool EMIT, bool BATCH>
+// WS: the warp-specialised variant (O.validators validator warps per CTA,
+// the last warps; no counting pass, no embeddings written).
+template <bool STATS, bool EMIT, bool BATCH, bool WS = false>
 __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchPlan P0,
                                                const MatchPlan* __restrict__ plans,
                                                const Chunk* __restrict__ chunks, int64_t nchunks,
@@ -296,7 +463,23 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
     // way; a donated run counts only what it scans.
     unsigned long long fb = 0;
     unsigned long long local = 0;          // lane 0: count not yet flushed
+    // warp-specialised: the ring after the warps' regions; expanders first
+    VRing* ring = nullptr;
+    const int nexp = WS ? (int)(blockDim.x >> 5) - O.validators : (int)(blockDim.x >> 5);
+    if (WS) {
+        ring = (VRing*)(smem + (((size_t)(blockDim.x >> 5) * warp_words + 3) & ~(size_t)3));
+        if (threadIdx.x == 0) {
+            ring->head = 0;
+            ring->tail = 0;
+            for (int i = 0; i < kRing; i++) ring->state[i] = 0;
+            ring->active = nexp;
+        }
+        __syncthreads();
+    }
 
+    if (WS && warp >= nexp) {
+        validate_tasks<BATCH>(P0, plans, ring, tcur, O, deadline, lb, fb);
+    } else {
     for (;;) {
         unsigned long long ci = 0;
         int kind = 0;
@@ -476,26 +659,47 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                     // C(u_d).  Scan the shortest (ties to the tree list, then to the
                     // earlier non-tree edge) and check the others: the same set.
                     int src = 0;
-                    {
-                        const int e0 = P.nt_begin[d], ne = P.nt_begin[d + 1] - e0;
-                        if (ne > 0) {
-                            uint32_t mf = __shfl_sync(0xffffffffu, m_reg, lane < ne ? P.nt_from[e0 + lane] : 0);
-                            int64_t elo = 0, elen = 0;
-                            uint32_t key = 0xFFFFFFFFu;           // (length, lane), lists shorter than the tree list
-                            if (lane < ne) {
-                                elo = P.n_off[e0 + lane][mf];
-                                elen = P.n_off[e0 + lane][mf + 1] - elo;
-                                if (elen < hi - lo)
-                                    key = ((uint32_t)(elen < (1 << 26) ? elen : (1 << 26) - 1) << 5) | (uint32_t)lane;
-                            }
-                            uint32_t best = __reduce_min_sync(0xffffffffu, key);
-                            if (best != 0xFFFFFFFFu) {
-                                int bi = (int)(best & 31u);
-                                src = bi + 1;
-                                lo = __shfl_sync(0xffffffffu, elo, bi);
-                                hi = lo + __shfl_sync(0xffffffffu, elen, bi);
-                            }
+                    const int64_t tlo = lo, thi = hi;     // the tree list's range
+                    const int e0 = P.nt_begin[d], ne = P.nt_begin[d + 1] - e0;
+                    int64_t elo = 0, elen = 0;            // lane e < ne: non-tree edge e0 + e's range
+                    if (ne > 0) {
+                        uint32_t mf = __shfl_sync(0xffffffffu, m_reg, lane < ne ? P.nt_from[e0 + lane] : 0);
+                        uint32_t key = 0xFFFFFFFFu;           // (length, lane), lists shorter than the tree list
+                        if (lane < ne) {
+                            elo = P.n_off[e0 + lane][mf];
+                            elen = P.n_off[e0 + lane][mf + 1] - elo;
+                            if (elen < hi - lo)
+                                key = ((uint32_t)(elen < (1 << 26) ? elen : (1 << 26) - 1) << 5) | (uint32_t)lane;
                         }
+                        uint32_t best = __reduce_min_sync(0xffffffffu, key);
+                        if (best != 0xFFFFFFFFu) {
+                            int bi = (int)(best & 31u);
+                            src = bi + 1;
+                            lo = __shfl_sync(0xffffffffu, elo, bi);
+                            hi = lo + __shfl_sync(0xffffffffu, elen, bi);
+                        }
+                    }
+                    if (WS && d == k - 1) {
+                        // the last position: hand the extension to a validator warp
+                        unsigned long long t = ~0ull;
+                        if (lane == 0) t = ring_claim(ring);
+                        t = __shfl_sync(0xffffffffu, t, 0);
+                        if (t != ~0ull) {
+                            VTask& T = ring->task[t % kRing];
+                            if (lane == 0) { T.q = q; T.src = src; T.lo[0] = tlo; T.hi[0] = thi; }
+                            if (lane < ne) { T.lo[1 + lane] = elo; T.hi[1 + lane] = elo + elen; }
+                            if (lane < d) T.g[lane] = g_reg;
+                            __threadfence_block();
+                            __syncwarp();
+                            if (lane == 0) {
+                                atomicExch(&ring->state[t % kRing], (uint32_t)(2 * (t / kRing) + 1));
+                                lb += 16 + 16ull * ne;
+                                fb += 4 + 16 + 16ull * ne;
+                            }
+                            d--;
+                            continue;
+                        }
+                        // a full ring: this warp scans the extension itself
                     }
                     if (lane == d) { seg_next = lo; seg_end = hi; seg_base = lo; bcnt = 0; bcur = 0; }
                     if (lane == 0) {
@@ -602,6 +806,11 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
         }
         __syncwarp();
     }
+    if (WS && lane == 0) {                     // this expander's tasks are all published
+        __threadfence_block();
+        atomicSub(&ring->active, 1);
+    }
+    }
     for (int o = 16; o > 0; o >>= 1) lb += __shfl_xor_sync(0xffffffffu, lb, o);
     if (lane == 0 && lb) atomicAdd(O.bytes, lb);
     if (lane == 0 && fb) atomicAdd(O.floor, fb);
@@ -652,12 +861,25 @@ MatchPlan make_plan(const fast_cst* c) {
 
 size_t smem_bytes(const MatchPlan& P, int warps) { return (size_t)warps * P.warp_words * sizeof(uint32_t); }
 
+// the warp-specialised variant: its validator warps per CTA (0: the fused kernel)
+int ws_validators(const fast_config& cfg, int warps) {
+    if (cfg.matcher_rule != 1 || warps < 2) return 0;
+    return cfg.validators > 0 ? std::min(cfg.validators, warps - 1) : warps / 2;
+}
+
+// dynamic shared memory of a launch: the warps' regions, then (warp-
+// specialised) the task ring on a 16-byte boundary
+size_t launch_smem(int warps, int warp_words, bool ws) {
+    const size_t words = ((size_t)warps * warp_words + 3) & ~(size_t)3;
+    return words * sizeof(uint32_t) + (ws ? sizeof(VRing) : 0);
+}
+
 // Opt every matcher variant in to the largest dynamic shared memory any
 // query can ask for (8 warps of a 32-vertex query with all its non-tree
 // cursors), once per device.  The attribute is process-wide: setting it per
 // launch to that launch's size would let a concurrent caller on another
 // thread lower it between someone else's set and launch.
-constexpr size_t kMatcherSmemMax = (size_t)8 * (kWarpBaseWords + 2 * kMaxNT) * sizeof(uint32_t);
+constexpr size_t kMatcherSmemMax = (size_t)8 * (kWarpBaseWords + 2 * kMaxNT) * sizeof(uint32_t) + 16 + sizeof(VRing);
 
 int matcher_smem_optin(size_t bytes) {
     if (bytes > kMatcherSmemMax) return set_error(FAST_ERR_INVALID, "matcher: %zu bytes of shared memory per CTA", bytes);
@@ -672,6 +894,8 @@ int matcher_smem_optin(size_t bytes) {
     FAST_CUDA(cudaFuncSetAttribute(k_match<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
     FAST_CUDA(cudaFuncSetAttribute(k_match<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
     FAST_CUDA(cudaFuncSetAttribute(k_match<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+    FAST_CUDA(cudaFuncSetAttribute(k_match<false, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+    FAST_CUDA(cudaFuncSetAttribute(k_match<false, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
     if (dev < 64) done |= 1ull << dev;
     return FAST_OK;
 }
@@ -762,18 +986,22 @@ int run_match(const fast_cst* c, const fast_chunks* chunks, const fast_config* c
         O.dq = dq; O.dq_state = dq_state; O.dq_cap = donate ? cells : 0;
         O.dq_head = ctr + kHead; O.dq_tail = ctr + kTail; O.outstanding = ctr + kOut;
         O.idle = (unsigned int*)(ctr + kIdle);
+        // the warp-specialised kernel for counting launches that ask for it
+        const int nval = (!stats_out && kemb == 0 && chunk_counts == nullptr) ? ws_validators(cfg, warps) : 0;
+        O.validators = nval;
         unsigned long long budget_ns = cfg.time_budget_s > 0 ? (unsigned long long)(cfg.time_budget_s * 1e9) : 0ull;
         if (budget_ns) { k_set_deadline<<<1, 1, 0, s>>>(ctr + kDeadline, budget_ns); note_launch(); }
         if (nchunks > 0) {
             int64_t grid = (int64_t)num_sms() * bps;
             if (!donate) grid = std::max<int64_t>(1, std::min<int64_t>(grid, ceil_div(nchunks, warps)));
-            size_t sh = smem_bytes(P, warps);
+            size_t sh = launch_smem(warps, P.warp_words, nval > 0);
             rc = matcher_smem_optin(sh);
             if (rc == FAST_OK) {
                 EventPair& ev = match_events();
                 if (ev.ok) cudaEventRecord(ev.a, s);
                 if (stats_out) { k_match<true, false, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, nullptr, dchunks, nchunks, nullptr, O); note_launch(); }
                 else if (kemb > 0) { k_match<false, true, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, nullptr, dchunks, nchunks, nullptr, O); note_launch(); }
+                else if (nval > 0) { k_match<false, false, false, true><<<(unsigned)grid, warps * 32, sh, s>>>(P, nullptr, dchunks, nchunks, nullptr, O); note_launch(); }
                 else { k_match<false, false, false><<<(unsigned)grid, warps * 32, sh, s>>>(P, nullptr, dchunks, nchunks, nullptr, O); note_launch(); }
                 cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess) rc = cuda_status(e, "matcher launch", __FILE__, __LINE__);
@@ -958,6 +1186,7 @@ int run_match_noalloc(const fast_cst* c, const fast_chunks* chunks, const fast_c
     O.dq = dq; O.dq_state = dq_state; O.dq_cap = cells;
     O.dq_head = ctr + kHead; O.dq_tail = ctr + kTail; O.outstanding = ctr + kOut;
     O.idle = (unsigned int*)(ctr + kIdle);
+    O.validators = 0;                                  // the fused kernel
     unsigned long long budget_ns = cfg.time_budget_s > 0 ? (unsigned long long)(cfg.time_budget_s * 1e9) : 0ull;
     if (budget_ns) { k_set_deadline<<<1, 1, 0, s>>>(ctr + kDeadline, budget_ns); note_launch(); }
     if (nchunks > 0) {
@@ -1015,11 +1244,12 @@ size_t match_chunk_bytes() { return sizeof(Chunk); }
 int match_batched_enqueue(const void* d_plans, int warp_words, const void* d_chunks, const int64_t* d_nchunks,
                           int max_q, unsigned long long* d_qtotal, int* d_qstop, unsigned long long* d_ctr,
                           void* d_dq, uint32_t* d_dq_state, uint64_t dq_cap, uint64_t limit, double budget_s,
-                          int warps, int bps, cudaStream_t s) {
+                          int warps, int bps, int validators, cudaStream_t s) {
     MatchPlan dummy;
     memset(&dummy, 0, sizeof(dummy));
     dummy.warp_words = warp_words;
-    size_t sh = (size_t)warps * warp_words * sizeof(uint32_t);
+    const int nval = validators > 0 && warps >= 2 ? std::min(validators, warps - 1) : 0;
+    size_t sh = launch_smem(warps, warp_words, nval > 0);
     FAST_CUDA(cudaMemsetAsync(d_ctr, 0, kCtrWords * sizeof(unsigned long long), s));
     FAST_CUDA(cudaMemsetAsync(d_qtotal, 0, (size_t)max_q * sizeof(unsigned long long), s));
     FAST_CUDA(cudaMemsetAsync(d_qstop, 0, (size_t)max_q * sizeof(int), s));
@@ -1033,14 +1263,19 @@ int match_batched_enqueue(const void* d_plans, int warp_words, const void* d_chu
     O.dq = (Chunk*)d_dq; O.dq_state = d_dq_state; O.dq_cap = dq_cap;
     O.dq_head = d_ctr + kHead; O.dq_tail = d_ctr + kTail; O.outstanding = d_ctr + kOut;
     O.idle = (unsigned int*)(d_ctr + kIdle);
+    O.validators = nval;
     // outstanding = number of chunks, read on the device from *d_nchunks
     k_copy_word<<<1, 1, 0, s>>>(d_ctr + kOut, d_nchunks);
     note_launch();
     unsigned long long budget_ns = budget_s > 0 ? (unsigned long long)(budget_s * 1e9) : 0ull;
     if (budget_ns) { k_set_deadline<<<1, 1, 0, s>>>(d_ctr + kDeadline, budget_ns); note_launch(); }
     int64_t grid = (int64_t)num_sms() * bps;
-    k_match<false, false, true><<<(unsigned)grid, warps * 32, sh, s>>>(dummy, (const MatchPlan*)d_plans,
-                                                                       (const Chunk*)d_chunks, 0, d_nchunks, O);
+    if (nval > 0)
+        k_match<false, false, true, true><<<(unsigned)grid, warps * 32, sh, s>>>(dummy, (const MatchPlan*)d_plans,
+                                                                                 (const Chunk*)d_chunks, 0, d_nchunks, O);
+    else
+        k_match<false, false, true><<<(unsigned)grid, warps * 32, sh, s>>>(dummy, (const MatchPlan*)d_plans,
+                                                                           (const Chunk*)d_chunks, 0, d_nchunks, O);
     note_launch();
     FAST_CUDA(cudaGetLastError());
     return FAST_OK;

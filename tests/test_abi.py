@@ -36,13 +36,13 @@ def test_config_default_without_gpu():
     c = F.default_config()
     assert c.delta_w == 1 << 20 and c.warps_per_block == 8 and c.max_chunks == 1 << 16 and c.limit == 0
     assert c.queue_cells == 0 and c.order_rule == 0 and c.filter_rule == 0 and c.build_rule == 0
-    assert c.refine_rule == 0
+    assert c.refine_rule == 0 and c.matcher_rule == 0 and c.validators == 0
     # fast_config_default zeroes exactly sizeof(fast_config) bytes, so a
     # sentinel-filled buffer shows the C size; it must be the binding's
     buf = (ctypes.c_ubyte * 256)(*([0xAB] * 256))
     F.lib().fast_config_default(ctypes.byref(buf))
     c_size = next(i for i in range(256) if buf[i] == 0xAB)
-    assert c_size == ctypes.sizeof(F.Config) == 88
+    assert c_size == ctypes.sizeof(F.Config) == 96
     assert F.lib().fast_last_error() == b""
 
 
