@@ -617,6 +617,10 @@ def run_ours(args):
             if name != args.build:
                 legs[f"build_{name}"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads,
                                                   build_rule=rule)
+        # the warp-specialised matcher (expander and validator warps) on the same step
+        legs["matcher_ws"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads,
+                                       matcher_rule=1, validators=1)
+        legs["matcher_ws"]["validators_per_cta"] = 1
         per_query = per_query_leg(F, torch, g, qs, cfg, stream, flush)
     else:
         per_query = None

@@ -356,7 +356,7 @@ __device__ void validate_tasks(const MatchPlan& P0, const MatchPlan* __restrict_
                 const unsigned long long now = global_timer_ns();
                 if (!waited_since) waited_since = now;
                 else if (now - waited_since > kValidatorWaitNs) { atomicOr(O.status, kStatusValidator); got = -2; break; }
-                __nanosleep(128);
+                __nanosleep(2000);
             }
             __threadfence_block();
         }
