@@ -469,7 +469,7 @@ def serve_leg(F, torch, args):
         m = int(min(max(50, rate * args.serve_seconds), 2000))
         stream_q = [qs[(pos + i) % len(qs)] for i in range(m)]
         pos += m
-        srv = F.Server(g, budget_bytes=120 << 30, cfg=scfg, workers=2)
+        srv = F.Server(g, budget_bytes=120 << 30, cfg=scfg, workers=4)
         gaps = srng.exponential(1.0 / rate, size=m)
         done = []
         ts = time.perf_counter()
@@ -496,7 +496,7 @@ def serve_leg(F, torch, args):
     return {"workload": (f"RMAT a=.57 b=c=.19 scale 23 (n=8,388,608, m=134,217,728), 32 Zipf(1.0) labels "
                          f"(seed {SERVE_SEED}); a stream of {len(qs)} random-walk queries of "
                          f"{'/'.join(map(str, SERVE_SIZES))} vertices in random order; limit "
-                         f"{args.serve_limit} per query; 120 GB admission budget; 2 group workers, "
+                         f"{args.serve_limit} per query; 120 GB admission budget; 4 group workers, "
                          f"CSTs and partitions of a group built together; each rate takes the next "
                          f"min(2000, rate x {args.serve_seconds:.0f} s) queries of the stream"),
             "setup_s": setup_s, "per_query": per_query, "rates": out}

@@ -444,7 +444,7 @@ typedef struct {
 /*
  * A request loop over the resident data graph g (the host/accelerator task
  * flow of Sec. IV, kept on one GPU) with continuous batching: requests wait
- * in a FIFO queue; each of `workers` group workers (<= 0: 2), with its own
+ * in a FIFO queue; each of `workers` group workers (<= 0: 4), with its own
  * CUDA stream and its own batch (as fast_batch_create with cfg, up to 1024
  * requests), takes every request at the head of the queue whose projected
  * device bytes -- label buckets and neighbour lists its CST can hold, plus

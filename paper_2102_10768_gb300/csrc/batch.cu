@@ -76,13 +76,19 @@ struct fast_batch {
     int* d_qstop = nullptr;
     unsigned char* d_dq = nullptr;
     uint32_t* d_dq_state = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int g_warp_words = -1, g_warps = -1, g_bps = -1, g_val = -1;
-    double g_budget = -1.0;
-    uint64_t g_limit = ~0ull;
-    uint64_t g_cells = 0;
-    unsigned char* g_chunks = nullptr;
-    int g_kernels = 0;                    // kernels in the captured graph (launched per replay)
+    // captured matcher launches, by launch shape (a batch's shared-memory
+    // stride takes a few values, so each shape is captured once)
+    struct Captured {
+        int warp_words, warps, bps, val;
+        double budget;
+        uint64_t limit, cells;
+        unsigned char* chunks;
+        cudaGraphExec_t exec;
+        int kernels;                      // kernels in the graph (launched per replay)
+    };
+    std::vector<Captured> graphs;
+    cudaGraphExec_t exec = nullptr;       // the one chosen for this run
+    int g_kernels = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<ScratchPool*> pools;      // per build thread: scratch of its CSTs and partitions
     double last_build_ms = 0.0, last_match_ms = 0.0;
@@ -107,7 +113,8 @@ __global__ void k_tag_chunks(Chunk* chunks, const int64_t* off, int nq) {
 void batch_release(fast_batch* b) {
     if (!b) return;
     cudaSetDevice(b->device);
-    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto& c : b->graphs) cudaGraphExecDestroy(c.exec);
+    b->graphs.clear();
     cudaStream_t s = nullptr;
     dfree(b->d_plans, s); dfree(b->d_off, s); dfree(b->d_nchunks, s); dfree(b->d_chunks, s);
     dfree(b->d_ctr, s); dfree(b->d_qtotal, s); dfree(b->d_qstop, s); dfree(b->d_dq, s); dfree(b->d_dq_state, s);
@@ -177,17 +184,32 @@ int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream
     const uint64_t cells = lc.queue_cells > 0 ? std::min<uint64_t>((uint64_t)lc.queue_cells, kBatchQueue) : kBatchQueue;
     int warps = lc.warps_per_block > 0 ? std::min(lc.warps_per_block, 8) : 8;
     const int nval = lc.matcher_rule == 1 && warps >= 2 ? (lc.validators > 0 ? std::min(lc.validators, warps - 1) : warps / 2) : 0;
-    if (b->exec && b->g_warp_words == warp_words && b->g_warps == lc.warps_per_block && b->g_bps == lc.blocks_per_sm &&
-        b->g_val == nval &&
-        b->g_budget == lc.time_budget_s && b->g_limit == lc.limit && b->g_chunks == b->d_chunks &&
-        b->g_cells == cells)
-        return FAST_OK;
-    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-    int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : 4;
+    const int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : 4;
+    for (auto& c : b->graphs)
+        if (c.warp_words == warp_words && c.warps == warps && c.bps == bps && c.val == nval && c.budget == lc.time_budget_s &&
+            c.limit == lc.limit && c.cells == cells && c.chunks == b->d_chunks) {
+            b->exec = c.exec;
+            b->g_kernels = c.kernels;
+            return FAST_OK;
+        }
+    // a new shape; graphs over an older chunk array can never run again
+    for (size_t i = 0; i < b->graphs.size();) {
+        if (b->graphs[i].chunks != b->d_chunks) {
+            cudaGraphExecDestroy(b->graphs[i].exec);
+            b->graphs.erase(b->graphs.begin() + i);
+        } else {
+            i++;
+        }
+    }
+    if (b->graphs.size() >= 8) {
+        cudaGraphExecDestroy(b->graphs.front().exec);
+        b->graphs.erase(b->graphs.begin());
+    }
     FAST_TRY(match_smem_optin((size_t)warps * warp_words * sizeof(uint32_t)));
     cudaStream_t cap;
     FAST_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
     int rc = FAST_OK;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) rc = cuda_status(e, "begin capture", __FILE__, __LINE__);
@@ -200,7 +222,7 @@ int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream
         else if (e != cudaSuccess) rc = cuda_status(e, "end capture", __FILE__, __LINE__);
     }
     if (rc == FAST_OK) {
-        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        e = cudaGraphInstantiate(&exec, graph, 0);
         if (e != cudaSuccess) rc = cuda_status(e, "graph instantiate", __FILE__, __LINE__);
     }
     // the enqueue counted each kernel it recorded (one kernel node each);
@@ -224,10 +246,11 @@ int batch_graph(fast_batch* b, int warp_words, const fast_config& lc, cudaStream
     cudaStreamDestroy(cap);
     (void)s;
     if (rc == FAST_OK) {
-        b->g_warp_words = warp_words; b->g_warps = lc.warps_per_block; b->g_bps = lc.blocks_per_sm;
-        b->g_budget = lc.time_budget_s; b->g_limit = lc.limit; b->g_chunks = b->d_chunks; b->g_cells = cells;
+        b->graphs.push_back({warp_words, warps, bps, nval, lc.time_budget_s, lc.limit, cells, b->d_chunks, exec, recorded});
+        b->exec = exec;
         b->g_kernels = recorded;
-        b->g_val = nval;
+    } else if (exec) {
+        cudaGraphExecDestroy(exec);
     }
     return rc;
 }
@@ -315,6 +338,9 @@ int batch_run(fast_batch* b, int32_t nq, const fast_query_desc* qs, uint64_t* co
     total = b->h_off[nq];
     b->last_chunks = total;
     if (warp_words == 0) warp_words = 32 * 32 + 64;
+    // one stride for every query of the launch, rounded up to 256 words so
+    // that batches of other mixes reuse a captured launch
+    warp_words = (warp_words + 255) / 256 * 256;
     match_plan_set_stride(b->h_plans, nq, warp_words);
     do {
         if (total > b->chunk_cap) {

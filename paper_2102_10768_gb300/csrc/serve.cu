@@ -194,7 +194,7 @@ extern "C" int fast_server_create(const fast_graph* g, const fast_config* cfg, u
     if (cfg) S->cfg = *cfg; else fast_config_default(&S->cfg);
     S->budget = budget_bytes;
     cudaGetDevice(&S->device);
-    int W = workers > 0 ? workers : 2;
+    int W = workers > 0 ? workers : 4;
     // mean degree per label, for the admission estimate
     unsigned long long* sum = nullptr;
     cudaStream_t s0 = nullptr;
