@@ -451,8 +451,9 @@ typedef struct {
  * the matcher's scratch -- fit in what budget_bytes leaves (the head
  * request is always admitted when nothing runs) and runs them as one batch:
  * their CSTs and partitions are built together (cfg->build_rule) and one
- * matcher launch (cfg->warps_per_block x cfg->blocks_per_sm per SM)
- * enumerates all of them.  Requests arriving while a group is on the GPU
+ * matcher launch enumerates all of them (cfg->warps_per_block warps per
+ * CTA; cfg->blocks_per_sm CTAs per SM, or one for a group of at most four
+ * requests, so that the launches of several small groups share the SMs).  Requests arriving while a group is on the GPU
  * form the next group; with two or more workers one group's build overlaps
  * another's matcher on the device.  cfg NULL: defaults.  Errors as
  * fast_batch_create.

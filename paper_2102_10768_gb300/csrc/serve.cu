@@ -93,6 +93,8 @@ uint64_t projected_bytes(const fast_server* S, const Req& r) {
     return (uint64_t)b;
 }
 
+constexpr int kSmallGroup = 4;           // requests: at most this many run on one CTA per SM
+
 // One group worker: take the admissible head of the queue, run it as one
 // batch, report every request of it.
 void worker_main(fast_server* S, int w) {
@@ -151,6 +153,18 @@ void worker_main(fast_server* S, int w) {
             qd[i].m = (int32_t)(grp[i].edges.size() / 2);
             qd[i].labels = grp[i].labels.data();
             qd[i].edges = grp[i].edges.data();
+        }
+        // a small group's matcher launch takes one CTA per SM, leaving room on
+        // every SM for the other workers' kernels; a large group takes the
+        // configured shape
+        {
+            fast_config lc;
+            fast_batch_config(b, 4, &lc, nullptr);
+            const int32_t bps = n <= kSmallGroup ? 1 : S->cfg.blocks_per_sm;
+            if (lc.blocks_per_sm != bps) {
+                lc.blocks_per_sm = bps;
+                fast_batch_config(b, 4, nullptr, &lc);
+            }
         }
         int rc = fast_batch_run(b, n, qd.data(), counts.data(), status.data(), st);
         const uint64_t t_done = now_ns();
