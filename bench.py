@@ -53,6 +53,7 @@ GRAPH_SEED = 2000
 QUERY_SEED = 3000
 SERVE_SIZES = (4, 8, 12, 16, 20, 24, 28, 32)
 SERVE_SEED = 4000
+ORDERS = {"path": 0, "greedy": 1, "bfs": 2, "mincand": 3}
 
 
 def parse(argv=None):
@@ -77,9 +78,9 @@ def parse(argv=None):
                         "on a separate sample of queries (seed + 1)")
     p.add_argument("--filter", choices=["ldf", "nlf"], default="nlf",
                    help="candidate filter: label frequencies (nlf, default) or label and degree only (ldf)")
-    p.add_argument("--order", choices=["path", "greedy"], default="greedy",
-                   help="matching order: the greedy rule (default) or the paper's path-based order "
-                        "(also reported beside the headline as path_order)")
+    p.add_argument("--order", choices=list(ORDERS), default="greedy",
+                   help="matching order: greedy (default), the paper's path-based order, the BFS order of t_q, "
+                        "or fewest candidates first (the others are reported beside the headline)")
     p.add_argument("--build", choices=["threads", "batched", "batched-all"], default="batched-all",
                    help="how the batched step builds its CSTs and partitions: the CSTs and the partitions "
                         "of all queries together (batched-all, default), the CSTs together and the "
@@ -385,7 +386,8 @@ def batch_leg(F, torch, g, bq, cfg, stream, flush, steps, threads, **over):
         bt.close()
     return {"value": t["emb"] / (t["ms"] / 1000.0), "unit": UNIT, "steps": steps, "ms_per_step": t["ms"] / steps,
             "build_ms_per_step": t["build_ms"] / steps, "match_ms_per_step": t["match_ms"] / steps,
-            "gpu_launches_per_step": launches / steps,
+            "gpu_launches_per_step": launches / steps, "queries_cut_by_budget_per_step": t["cut"] / steps,
+            "matcher_budget_s": c2.time_budget_s,
             "counts_sha1": hashlib.sha1(t["counts"].astype("int64").tobytes()).hexdigest()}
 
 
@@ -445,7 +447,7 @@ def serve_leg(F, torch, args):
     del e
     setup_s = time.perf_counter() - t0
     cfg = F.default_config(delta_w=args.delta_w, max_chunks=1024, limit=args.serve_limit, time_budget_s=10.0,
-                           order_rule=1 if args.order == "greedy" else 0, filter_rule=1 if args.filter == "nlf" else 0)
+                           order_rule=ORDERS[args.order], filter_rule=1 if args.filter == "nlf" else 0)
     # per query, back to back (closed loop): the rate the offered rates scale
     nb = min(200, len(qs))
     lat, emb = [], 0
@@ -529,7 +531,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     g = F.Graph(n, e, lab)
     cfg = F.default_config(delta_w=args.delta_w, max_chunks=args.max_chunks, limit=args.limit,
-                           time_budget_s=args.budget, order_rule=1 if args.order == "greedy" else 0,
+                           time_budget_s=args.budget, order_rule=ORDERS[args.order],
                            filter_rule=1 if args.filter == "nlf" else 0)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
     bq = qs
@@ -613,10 +615,12 @@ def run_ours(args):
 
     legs = {}
     if args.legs and world == 1:
-        # the paper's path-based order, and the other build rules, on the same step
-        other = "path" if args.order == "greedy" else "greedy"
-        legs[f"{other}_order"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads,
-                                           order_rule=1 if other == "greedy" else 0)
+        # the other matching orders (the paper's path-based one among them)
+        # and the other build rules, on the same step
+        for name, rule in ORDERS.items():
+            if name != args.order:
+                legs[f"{name}_order"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 1, args.threads,
+                                                  order_rule=rule, time_budget_s=10.0)
         for rule, name in ((0, "threads"), (1, "batched"), (2, "batched-all")):
             if name != args.build:
                 legs[f"build_{name}"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads,

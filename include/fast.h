@@ -107,8 +107,12 @@ typedef struct {
      * (Sec. IV-B): a depth-first walk of t_q, children by increasing
      * (|C(u)|, u).  1: greedy: after the root, repeatedly the vertex whose
      * t_q parent is placed with the most query edges to placed vertices
-     * (ties: smaller |C(u)|, then smaller u).  The paper's method takes any
-     * connected order; embeddings and counts never depend on it. */
+     * (ties: smaller |C(u)|, then smaller u).  2: the BFS order of t_q.
+     * 3: after the root, repeatedly the vertex whose t_q parent is placed
+     * with the fewest candidates (ties: smaller u).  The paper's method
+     * takes any connected order (Sec. IV-B, and its order study of
+     * Sec. VI); every rule places a vertex after its t_q parent, and
+     * embeddings and counts never depend on the rule. */
     int32_t order_rule;
     /* Candidate filter of fast_build_cst (Sec. IV-A, local features).  0:
      * label and degree, C0(u) = { v : l(v) = l_q(u), d(v) >= d_q(u) }.  1:

@@ -191,13 +191,14 @@ def count(g: Graph, qlabels, qedges, **kw) -> int:
 class Cst:
     """Candidate search tree of Algorithm 1, restated on the CPU."""
 
-    ORDERS = {"path": 0, "greedy": 1}
+    ORDERS = {"path": 0, "greedy": 1, "bfs": 2, "mincand": 3}
     FILTERS = {"ldf": 0, "nlf": 1}
     REFINES = {"once": 0, "fixpoint": 1, "once_nt": 2}
 
     def __init__(self, g: Graph, qlabels, qedges, order: str = "path", filter: str = "ldf", refine: str = "once"):
-        """order: "path" (the paper's path-based order) or "greedy" (edges
-        to already placed vertices first); filter: "ldf" (label and degree)
+        """order: "path" (the paper's path-based order), "greedy" (edges
+        to already placed vertices first), "bfs" (the BFS order of t_q) or
+        "mincand" (the placeable vertex with the fewest candidates); filter: "ldf" (label and degree)
         or "nlf" (also neighbour label frequencies); refine: "once" (the
         paper's single bottom-up pass), "fixpoint" (repeated, with the
         non-tree neighbour test) or "once_nt" (one pass with that test); see

@@ -41,7 +41,12 @@
  *            Sec. IV-B): after the root, repeatedly the unplaced vertex whose
  *            t_q parent is placed with the most query edges to placed
  *            vertices; ties to the smaller |C(u)|, then the smaller id.
- *            Either way every vertex follows its t_q parent.
+ *            rule 2 (breadth-first): the BFS order of t_q itself, the order
+ *            in which the tree was built.
+ *            rule 3 (smallest candidate set first): after the root,
+ *            repeatedly the unplaced vertex whose t_q parent is placed with
+ *            the fewest candidates; ties to the smaller id.
+ *            Every rule places every vertex after its t_q parent.
  *   non-tree for each query edge outside t_q, from its earlier endpoint u_j
  *            to its later endpoint u_i in the order: N^{u_j}_{u_i}(v) =
  *            N_G(v) n C(u_i) for v in C(u_j).  Only this direction is read
@@ -120,7 +125,7 @@ void oracle_cst_free(ocst* c) {
  */
 ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int32_t* qe, int order_rule,
                        int filter_rule, int refine_rule) {
-    if (k < 1 || k > CMAXK || order_rule < 0 || order_rule > 1 || filter_rule < 0 || filter_rule > 1 ||
+    if (k < 1 || k > CMAXK || order_rule < 0 || order_rule > 3 || filter_rule < 0 || filter_rule > 1 ||
         refine_rule < 0 || refine_rule > 2)
         return NULL;
     int A[CMAXK][CMAXK];
@@ -270,6 +275,25 @@ ocst* oracle_cst_build(const og* g, int k, const int32_t* ql, int nqe, const int
     }
     } while (refine_rule == 1 && removed > 0);
 
+    /* matching order, rule 2: the BFS order of t_q */
+    if (order_rule == 2) {
+        for (int i = 0; i < k; i++) c->order[i] = c->bfs[i];
+    } else
+    /* matching order, rule 3: the placeable vertex with the fewest candidates */
+    if (order_rule == 3) {
+        int placed[CMAXK] = {0};
+        c->order[0] = r;
+        placed[r] = 1;
+        for (int no = 1; no < k; no++) {
+            int best = -1;
+            for (int u = 0; u < k; u++) {
+                if (placed[u] || !placed[c->parent[u]]) continue;
+                if (best < 0 || c->cand[u].n < c->cand[best].n || (c->cand[u].n == c->cand[best].n && u < best)) best = u;
+            }
+            c->order[no] = best;
+            placed[best] = 1;
+        }
+    } else
     /* matching order, rule 1: greedy by edges to the placed vertices */
     if (order_rule == 1) {
         int placed[CMAXK] = {0};

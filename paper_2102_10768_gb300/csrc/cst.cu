@@ -362,8 +362,9 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
     if (!g) return set_error(FAST_ERR_INVALID, "fast_build_cst: graph is NULL");
     int A[kMaxK][kMaxK], dq[kMaxK];
     FAST_TRY(validate_query(q, A, dq));
-    if (cfg_in && (cfg_in->order_rule < 0 || cfg_in->order_rule > 1))
-        return set_error(FAST_ERR_INVALID, "fast_build_cst: order_rule %d (0 path-based, 1 greedy)", cfg_in->order_rule);
+    if (cfg_in && (cfg_in->order_rule < 0 || cfg_in->order_rule > 3))
+        return set_error(FAST_ERR_INVALID, "fast_build_cst: order_rule %d (0 path-based, 1 greedy, 2 BFS, 3 fewest candidates)",
+                         cfg_in->order_rule);
     if (cfg_in && (cfg_in->filter_rule < 0 || cfg_in->filter_rule > 1))
         return set_error(FAST_ERR_INVALID, "fast_build_cst: filter_rule %d (0 label and degree, 1 label frequencies)",
                          cfg_in->filter_rule);
@@ -579,7 +580,7 @@ int build_cst(const fast_graph* g, const fast_query_desc* q, const fast_config* 
         }
 
         // ------------------------------------------------ matching order
-        matching_order(k, A, r, c->parent, c->ncand, c->cfg.order_rule, c->order, c->pos);
+        matching_order(k, A, r, c->parent, c->bfs, c->ncand, c->cfg.order_rule, c->order, c->pos);
 
         // ------------------------------------------------------ non-tree
         c->nnt = nontree_edges(k, A, c->order, c->parent, c->nt_from, c->nt_to);

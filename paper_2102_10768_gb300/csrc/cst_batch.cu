@@ -531,7 +531,7 @@ struct Q {
 // Matching order and non-tree edges of one query from its refined candidate
 // counts, by the rules the per-query build uses.
 void order_and_nontree(const Q& q, fast_cst* c) {
-    fast::matching_order(q.k, q.A, c->root, c->parent, c->ncand, c->cfg.order_rule, c->order, c->pos);
+    fast::matching_order(q.k, q.A, c->root, c->parent, c->bfs, c->ncand, c->cfg.order_rule, c->order, c->pos);
     c->nnt = nontree_edges(q.k, q.A, c->order, c->parent, c->nt_from, c->nt_to);
 }
 
@@ -1205,8 +1205,9 @@ int build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, 
             Q q;
             int rc = validate_query(&qs[i], q.A, q.dq);
             const fast_config* cf = cfgs[i];
-            if (rc == FAST_OK && cf && (cf->order_rule < 0 || cf->order_rule > 1))
-                rc = set_error(FAST_ERR_INVALID, "fast_build_cst_batch: order_rule %d (0 path-based, 1 greedy)",
+            if (rc == FAST_OK && cf && (cf->order_rule < 0 || cf->order_rule > 3))
+                rc = set_error(FAST_ERR_INVALID,
+                               "fast_build_cst_batch: order_rule %d (0 path-based, 1 greedy, 2 BFS, 3 fewest candidates)",
                                cf->order_rule);
             if (rc == FAST_OK && cf && (cf->filter_rule < 0 || cf->filter_rule > 1))
                 rc = set_error(FAST_ERR_INVALID,

@@ -441,11 +441,29 @@ inline void bfs_tree(int k, const int A[kMaxK][kMaxK], int r, int* bfs, int* par
 // depth-first preorder of t_q, children by increasing (|C|, id), so whole
 // root-to-leaf paths come in turn.  rule 1 (greedy): after the root, the
 // unplaced vertex whose t_q parent is placed with the most query edges to
-// placed vertices; ties to the smaller |C|, then the smaller id.  Writes
+// placed vertices; ties to the smaller |C|, then the smaller id.  rule 2:
+// the BFS order of t_q (bfs[]).  rule 3: after the root, the unplaced
+// vertex whose t_q parent is placed with the fewest candidates; ties to the
+// smaller id.  Every rule places a vertex after its t_q parent.  Writes
 // order[position] and pos[vertex].
-inline void matching_order(int k, const int A[kMaxK][kMaxK], int r, const int* parent, const int64_t* ncand, int rule,
-                           int* order, int* pos) {
-    if (rule == 1) {
+inline void matching_order(int k, const int A[kMaxK][kMaxK], int r, const int* parent, const int* bfs,
+                           const int64_t* ncand, int rule, int* order, int* pos) {
+    if (rule == 2) {
+        for (int i = 0; i < k; i++) order[i] = bfs[i];
+    } else if (rule == 3) {
+        bool placed[kMaxK] = {false};
+        order[0] = r;
+        placed[r] = true;
+        for (int no = 1; no < k; no++) {
+            int best = -1;
+            for (int u = 0; u < k; u++) {
+                if (placed[u] || !placed[parent[u]]) continue;
+                if (best < 0 || ncand[u] < ncand[best] || (ncand[u] == ncand[best] && u < best)) best = u;
+            }
+            order[no] = best;
+            placed[best] = true;
+        }
+    } else if (rule == 1) {
         bool placed[kMaxK] = {false};
         order[0] = r;
         placed[r] = true;

@@ -232,6 +232,22 @@ def test_match_random_greedy_order(seed):
         assert np.array_equal(sorted_rows(r2["emb"][:r2["written"]].astype(np.int32)), want["emb"])
 
 
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("rule,name", [(2, "bfs"), (3, "mincand")])
+def test_cst_and_counts_bfs_and_fewest_candidate_orders(seed, rule, name):
+    """Order rules 2 (BFS order of t_q) and 3 (fewest candidates first):
+    every CST array equals the oracle's restatement, and the counts the
+    oracle's."""
+    n, e, lab, ql, qe = rand_case(2400 + seed)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    cfg = F.default_config(order_rule=rule)
+    gc = F.Cst(g, ql, qe, cfg)
+    compare_cst(gc, oracle.Cst(o, ql, qe, order=name), len(ql))
+    assert F.match(gc, F.Chunks(gc, F.default_config(delta_w=max(1, gc.W // 16))))["count"] == oracle.count(o, ql, qe)
+    csts, st = F.build_csts(g, [(ql, qe)], cfg)                  # the batched build, same rules
+    compare_cst(csts[0], oracle.Cst(o, ql, qe, order=name), len(ql))
+
+
 def test_er_queries_greedy_order(er):
     w, g, o = er
     for q in w.queries:

@@ -556,6 +556,67 @@ def test_greedy_order_house_in_k6():
         assert oracle.count(g, ql, qe, order=c.order.tolist(), par=_tree_par(c)) == 720
 
 
+def test_bfs_and_fewest_candidate_orders_house_in_k6():
+    """Hand-worked, the house in K6 again (t_q: 0 -> {1, 3, 4}, 1 -> {2}).
+    BFS order (rule 2): the order t_q was built in, 0 1 3 4 2.  Fewest
+    candidates first (rule 3): every |C| is 6, so ties go by id along the
+    frontier: 0, then 1 (of 1, 3, 4), then 2 (of 2, 3, 4), then 3, 4."""
+    n = 6
+    edges = [[a, b] for a in range(n) for b in range(a + 1, n)]
+    g = oracle.Graph(n, edges, [0] * n)
+    ql, qe = [0] * 5, [[0, 1], [1, 2], [2, 3], [3, 0], [0, 4], [1, 4]]
+    bfs = oracle.Cst(g, ql, qe, order="bfs")
+    few = oracle.Cst(g, ql, qe, order="mincand")
+    assert bfs.order.tolist() == [0, 1, 3, 4, 2] == bfs.bfs.tolist()
+    assert few.order.tolist() == [0, 1, 2, 3, 4]
+    for c in (bfs, few):
+        assert oracle.count(g, ql, qe, order=c.order.tolist(), par=_tree_par(c)) == 720
+
+
+def test_fewest_candidates_against_greedy_by_hand():
+    """A labelled case where the rules part: q0 (label 0) joined to q1, q2,
+    q3 (labels 1, 2, 3) and q1-q2.  G: vertex 0 (label 0) joined to 1
+    (label 1), to 3..7 (label 2) and to 8..10 (label 3); vertex 1 joined to
+    3..7.  |C| = 1, 1, 5, 3; the root is q0 (1/3 below 1/2) and t_q is the
+    star q0 -> q1, q2, q3.  Greedy (rule 1): q1 (fewest candidates among one
+    edge each), then q2 (two edges to placed vertices), then q3: 0 1 2 3.
+    Fewest candidates (rule 3): q1, then q3 (3 < 5), then q2: 0 1 3 2, which
+    is also the path-based order (children by |C|).  BFS: 0 1 2 3.  Every
+    order finds 1 x 1 x 5 x 3 = 15 embeddings."""
+    labels = [0, 1] + [9] + [2] * 5 + [3] * 3
+    edges = [[0, 1]] + [[0, v] for v in range(3, 8)] + [[0, v] for v in range(8, 11)] + [[1, v] for v in range(3, 8)]
+    g = oracle.Graph(11, edges, labels)
+    ql, qe = [0, 1, 2, 3], [[0, 1], [0, 2], [0, 3], [1, 2]]
+    want = {"path": [0, 1, 3, 2], "greedy": [0, 1, 2, 3], "bfs": [0, 1, 2, 3], "mincand": [0, 1, 3, 2]}
+    for rule, order in want.items():
+        c = oracle.Cst(g, ql, qe, order=rule)
+        assert c.root == 0 and c.parent.tolist() == [-1, 0, 0, 0]
+        assert [len(c.cand(u)) for u in range(4)] == [1, 1, 5, 3]
+        assert c.order.tolist() == order, rule
+        assert oracle.count(g, ql, qe, order=c.order.tolist(), par=_tree_par(c)) == 15
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_all_order_rules_connected_and_count_invariant(seed):
+    """Every rule places each vertex after its t_q parent, rule 2 is exactly
+    the BFS order, and matching in any of the four orders finds the same
+    number of embeddings."""
+    n, edges, labels, ql, qe = _cst_case(seed)
+    g = oracle.Graph(n, edges, labels)
+    want = oracle.count(g, ql, qe)
+    k = len(ql)
+    for rule in ("bfs", "mincand"):
+        c = oracle.Cst(g, ql, qe, order=rule)
+        pos = {int(u): i for i, u in enumerate(c.order)}
+        assert sorted(pos) == list(range(k)) and int(c.order[0]) == c.root
+        for u in range(k):
+            if c.parent[u] >= 0:
+                assert pos[int(c.parent[u])] < pos[u]
+        if rule == "bfs":
+            assert c.order.tolist() == c.bfs.tolist()
+        assert oracle.count(g, ql, qe, order=c.order.tolist(), par=_tree_par(c)) == want
+
+
 @pytest.mark.parametrize("seed", range(25))
 def test_greedy_order_is_connected_and_count_invariant(seed):
     """Every vertex follows its t_q parent (so the CST's tree lists apply);
