@@ -625,6 +625,10 @@ def run_ours(args):
             if name != args.build:
                 legs[f"build_{name}"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads,
                                                   build_rule=rule)
+        # refine rule 2 (the bottom-up pass with the non-tree neighbour test):
+        # build time spent against matcher time saved
+        if args.refine != "once_nt" and args.build != "threads":
+            legs["refine_once_nt"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads, refine_rule=2)
         # the warp-specialised matcher (expander and validator warps) on the same step
         legs["matcher_ws"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads,
                                        matcher_rule=1, validators=1)
