@@ -180,6 +180,9 @@ int fast_graph_info(const fast_graph* g, int64_t* n, int64_t* nadj, int32_t* num
  * layout above (a test aid). */
 int fast_graph_copy_csr(const fast_graph* g, int64_t* row_ptr, int32_t* col, void* stream);
 
+/* Free G.  Device memory the library frees stays pooled in this process
+ * (the stream-ordered allocator's default pool, kept from one batched step
+ * to the next); freeing a graph also hands the pooled memory back. */
 void fast_free_graph(fast_graph* g);
 
 /* ----------------------------------------------------------------- CST */

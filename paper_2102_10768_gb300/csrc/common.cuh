@@ -59,6 +59,8 @@ bool alloc_fault_due();
 struct ScratchPool;
 ScratchPool* pool_new();
 void pool_delete(ScratchPool* p);
+void retain_freed_memory();                                  // once per device: keep freed memory pooled
+void trim_freed_memory();                                    // give the pooled memory back
 ScratchPool* pool_active();                                  // bound to this thread, or null
 int pool_alloc(ScratchPool* p, void** out, size_t bytes);
 bool pool_free(ScratchPool* p, void* ptr);                   // false: not from this pool
@@ -92,6 +94,7 @@ inline int dalloc_direct(T** p, size_t n, cudaStream_t s) {
         *p = nullptr;
         return set_error(FAST_ERR_OOM, "device allocation of %zu bytes failed: injected", bytes);
     }
+    retain_freed_memory();
     cudaError_t e = cudaMallocAsync((void**)p, bytes, s);
     if (e != cudaSuccess) {
         *p = nullptr;

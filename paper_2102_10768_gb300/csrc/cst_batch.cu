@@ -290,6 +290,18 @@ __global__ void __launch_bounds__(256) k_child_sums_b(const ChildSumDesc* __rest
             const int64_t* off = d.off;
             const int64_t i0 = tr.tb + (int64_t)threadIdx.x * kItems;
             if (i0 < tr.te) {
+                // the thread's entries' child indices, then their values, all in flight at once
+                uint32_t x[kItems];
+#pragma unroll
+                for (int i = 0; i < kItems; i++) x[i] = i0 + i < tr.te ? __ldg(d.idx + i0 + i) : 0u;
+                uint64_t v[kItems];
+                double vf[kItems];
+#pragma unroll
+                for (int i = 0; i < kItems; i++) {
+                    const bool in = i0 + i < tr.te;
+                    v[i] = in ? __ldg(d.cv + x[i]) : 0ull;
+                    vf[i] = in ? __ldg(d.cvf + x[i]) : 0.0;
+                }
                 int64_t row = row_in(off, tr.r0, tr.r1, i0);
                 unsigned long long s = 0;
                 double sf = 0.0;
@@ -308,12 +320,10 @@ __global__ void __launch_bounds__(256) k_child_sums_b(const ChildSumDesc* __rest
                         s = 0; sf = 0.0; sat = false;
                         do row++; while (e >= off[row + 1]);
                     }
-                    uint32_t x = d.idx[e];
-                    uint64_t v = d.cv[x];
-                    unsigned long long ns = s + v;
-                    if (ns < s || v == ~0ull) sat = true;
+                    unsigned long long ns = s + v[i];
+                    if (ns < s || v[i] == ~0ull) sat = true;
                     s = ns;
-                    sf += d.cvf[x];
+                    sf += vf[i];
                 }
                 flush();
             }

@@ -388,4 +388,5 @@ extern "C" void fast_free_graph(fast_graph* g) {
     if (!g) return;
     graph_release(g, nullptr);
     cudaStreamSynchronize(nullptr);
+    trim_freed_memory();                 // a workload ended: hand its pooled memory back
 }

@@ -58,6 +58,37 @@ ScratchPool* default_pool() {
 
 }  // namespace
 
+// The stream-ordered allocator's default pool returns freed memory to the
+// device at every synchronisation unless told to keep it.  A batched step
+// allocates and frees tens of GB of CSTs, so that round trip through the
+// driver's page tables would come back every step: keep freed memory in the
+// pool, once per device (a setting of this process only).
+void retain_freed_memory() {
+    static std::atomic<uint64_t> done{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return; }
+    if (dev < 0 || dev >= 64) return;
+    const uint64_t bit = 1ull << dev;
+    if (done.load(std::memory_order_relaxed) & bit) return;
+    cudaMemPool_t mp;
+    if (cudaDeviceGetDefaultMemPool(&mp, dev) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.fetch_or(bit, std::memory_order_relaxed);
+}
+
+// Give the pool's unused memory back to the device (after a large workload
+// ends, e.g. when its graph is freed).
+void trim_freed_memory() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return; }
+    cudaMemPool_t mp;
+    if (cudaDeviceGetDefaultMemPool(&mp, dev) == cudaSuccess) cudaMemPoolTrimTo(mp, 0);
+    cudaGetLastError();
+}
+
 ScratchPool* pool_new() {
     ScratchPool* p = new ScratchPool();
     cudaGetDevice(&p->device);
@@ -159,6 +190,7 @@ int Arena::grow(size_t bytes, cudaStream_t s) {
     size_t sz = bytes;
     if (sz < next_) sz = next_;
     void* b = nullptr;
+    retain_freed_memory();
     cudaError_t e = cudaMallocAsync(&b, sz, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
