@@ -275,8 +275,11 @@ def test_order_rule_rejected_when_unknown(er):
     w, g, o = er
     q = w.queries[0]
     with pytest.raises(F.FastError) as ei:
-        F.Cst(g, q.labels, q.edges, F.default_config(order_rule=2))
+        F.Cst(g, q.labels, q.edges, F.default_config(order_rule=4))
     assert ei.value.code == F.FAST_ERR_INVALID
+    for bad in (-1, 4):
+        csts, status = F.build_csts(g, [(q.labels, q.edges)], F.default_config(order_rule=bad))
+        assert status.tolist() == [F.FAST_ERR_INVALID] and csts == [None]
 
 
 # ------------------------------------ candidate filter: label frequencies
