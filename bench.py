@@ -53,6 +53,8 @@ GRAPH_SEED = 2000
 QUERY_SEED = 3000
 SERVE_SIZES = (4, 8, 12, 16, 20, 24, 28, 32)
 SERVE_SEED = 4000
+BILLION_SIZES = (8, 12, 16)
+BILLION_SEED = 5000
 ORDERS = {"path": 0, "greedy": 1, "bfs": 2, "mincand": 3}
 
 
@@ -63,6 +65,10 @@ def parse(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--per-size", type=int, default=200, help="queries per size (4, 8, 16, 24, 32 vertices)")
+    p.add_argument("--workload", choices=["powerlaw", "rmat26"], default="powerlaw",
+                   help="the headline's graph and queries: the 1M/16M power-law graph with the 1,000-query mix "
+                        "(default), or RMAT scale 26 (67M vertices, 1.07B edges, 64 Zipf labels) with 50 queries "
+                        "each of 8, 12 and 16 vertices (per-size sets the count; minutes of host time to generate)")
     p.add_argument("--delta-w", type=int, default=1 << 20)
     p.add_argument("--max-chunks", type=int, default=4096)
     p.add_argument("--limit", type=int, default=1 << 22, help="embeddings per query (exact min(total, limit))")
@@ -119,6 +125,17 @@ def reduce_over_ranks(values, dist, device):
 
 def workload(args, rank: int):
     import synth
+    if args.workload == "rmat26":
+        n, e, lab = synth.rmat_graph(26, 16, 64, BILLION_SEED)
+        wg = synth.WalkGraph(n, e)
+        qs = synth.mixed_queries(wg, lab, BILLION_SIZES, args.per_size, BILLION_SEED + 7919 * rank)
+        wg.close()
+        desc = (f"RMAT a=.57 b=c=.19 scale 26 (n=67,108,864, m=1,073,741,824, 64-bit offsets), 64 Zipf(1.0) labels "
+                f"(seed {BILLION_SEED}); {len(qs)} random-walk queries, {args.per_size} each of "
+                f"{'/'.join(map(str, BILLION_SIZES))} vertices (seed {BILLION_SEED + 7919 * rank}); per query: CST "
+                f"({args.filter} filter, {args.order} order), Alg. 2 partition (delta_w={args.delta_w}, "
+                f"max_chunks={args.max_chunks}), match until limit={args.limit} embeddings")
+        return n, e, lab, qs, desc
     n, e, lab = synth.powerlaw_graph(seed=GRAPH_SEED)
     wg = synth.WalkGraph(n, e)
     qs = synth.mixed_queries(wg, lab, SIZES, args.per_size, query_seed(rank))
