@@ -1207,8 +1207,16 @@ namespace fast {
 int build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, const fast_config* const* cfgs,
                     cudaStream_t s, fast_cst** outs, int32_t* status) {
     for (int i = 0; i < nq; i++) outs[i] = nullptr;
-    for (int g0 = 0; g0 < nq; g0 += kGroup) {
-        const int g1 = std::min(nq, g0 + kGroup);
+    // Ranges of queries built together: groups of kGroup; a range whose
+    // build runs out of device memory (its bound-sized buffers did not fit)
+    // is released and built as two halves, down to single queries.  The
+    // CSTs do not depend on how the queries are grouped.
+    std::vector<std::pair<int, int>> todo;
+    for (int g0 = nq - (nq % kGroup == 0 ? kGroup : nq % kGroup); g0 >= 0; g0 -= kGroup)
+        todo.push_back({g0, std::min(nq, g0 + kGroup)});
+    while (!todo.empty()) {
+        const int g0 = todo.back().first, g1 = todo.back().second;
+        todo.pop_back();
         std::vector<Q> Qs;
         Qs.reserve(g1 - g0);
         for (int i = g0; i < g1; i++) {
@@ -1246,9 +1254,18 @@ int build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, 
             Qs.push_back(q);
         }
         int rc = Qs.empty() ? FAST_OK : build_all(g, Qs, s);
+        if (rc == FAST_ERR_OOM && Qs.size() > 1) {
+            for (auto& q : Qs) cst_release_nosync(q.c);
+            cudaStreamSynchronize(s);              // the freed buffers are reusable by the halves
+            set_error(FAST_OK, "%s", "");
+            const int mid = g0 + (g1 - g0) / 2;
+            todo.push_back({mid, g1});
+            todo.push_back({g0, mid});
+            continue;
+        }
         if (rc != FAST_OK) {
             for (auto& q : Qs) cst_release_nosync(q.c);
-            for (int i = 0; i < g0; i++) { cst_release_nosync(outs[i]); outs[i] = nullptr; }
+            for (int i = 0; i < nq; i++) { cst_release_nosync(outs[i]); outs[i] = nullptr; }
             return rc;
         }
         for (auto& q : Qs) outs[q.idx] = q.c;

@@ -138,6 +138,12 @@ int pool_alloc(ScratchPool* p, void** out, size_t bytes) {
         ScratchPool::Block nb;
         nb.size = bytes > kPoolBlock ? bytes : kPoolBlock;
         cudaError_t e = cudaMalloc((void**)&nb.base, nb.size);
+        if (e == cudaErrorMemoryAllocation) {
+            // the stream-ordered pool may be holding freed memory: hand it back, try once more
+            cudaGetLastError();
+            trim_freed_memory();
+            e = cudaMalloc((void**)&nb.base, nb.size);
+        }
         if (e != cudaSuccess) {
             cudaGetLastError();
             *out = nullptr;
