@@ -60,6 +60,7 @@ struct ScratchPool;
 ScratchPool* pool_new();
 void pool_delete(ScratchPool* p);
 void retain_freed_memory();                                  // once per device: keep freed memory pooled
+void pool_release_unused(ScratchPool* p);                    // free the scratch blocks with no live region
 void trim_freed_memory();                                    // give the pooled memory back
 ScratchPool* pool_active();                                  // bound to this thread, or null
 int pool_alloc(ScratchPool* p, void** out, size_t bytes);

@@ -1257,6 +1257,8 @@ int build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, 
         if (rc == FAST_ERR_OOM && Qs.size() > 1) {
             for (auto& q : Qs) cst_release_nosync(q.c);
             cudaStreamSynchronize(s);              // the freed buffers are reusable by the halves
+            pool_release_unused(pool_active());    // and the scratch the attempt grew goes back
+            trim_freed_memory();
             set_error(FAST_OK, "%s", "");
             const int mid = g0 + (g1 - g0) / 2;
             todo.push_back({mid, g1});

@@ -103,6 +103,24 @@ void pool_delete(ScratchPool* p) {
 
 ScratchPool* pool_active() { return tl_active; }
 
+// Free the blocks of p that hold no live region (their memory back to the
+// device), e.g. after a build that ran out of memory left them large.
+void pool_release_unused(ScratchPool* p) {
+    if (!p) return;
+    std::vector<ScratchPool::Block> keep;
+    for (auto& b : p->blocks) {
+        const bool empty = b.free_.size() == 1 && b.free_.begin()->first == 0 && b.free_.begin()->second == b.size;
+        if (empty) cudaFree(b.base);
+        else keep.push_back(std::move(b));
+    }
+    // live regions record their block's index: renumber
+    for (auto& kv : p->live) {
+        for (int i = 0; i < (int)keep.size(); i++)
+            if (kv.first >= keep[i].base && kv.first < keep[i].base + keep[i].size) { kv.second.first = i; break; }
+    }
+    p->blocks = std::move(keep);
+}
+
 // Allocations left before the injected failure; negative: disarmed.
 std::atomic<int64_t> g_alloc_countdown{-1};
 
