@@ -124,8 +124,12 @@ int scan_exclusive(const T* in, T* out, int64_t n, T* total, cudaStream_t s) {
 
 constexpr int kCompBlock = 128;
 constexpr int kCompBlocksPerSM = 8;            // small blocks: one waiting on its look-back leaves 7 running
-constexpr int kCompItems = 8;
+constexpr int kCompItems = 16;               // single-pass compaction: indices per thread
 constexpr int kCompTile = kCompBlock * kCompItems;
+constexpr int kEvalN = 8;                    // indices a functor's eval_n takes at once
+static_assert(kCompItems % kEvalN == 0 && kCompItems <= 32, "a thread's kept indices form one 32-bit mask");
+constexpr int kComp2Items = 8;               // the two-pass form (compact_alloc)
+constexpr int kComp2Tile = kCompBlock * kComp2Items;
 
 // A functor with a member `bool counting` has it set in the count pass, so
 // that side effects of eval (marking a bitmap) happen once, in the write pass.
@@ -137,17 +141,17 @@ struct has_counting<F, std::void_t<decltype(std::declval<F&>().counting)>> : std
 template <class F>
 __global__ void k_compact_count(F f, int64_t n, int64_t* __restrict__ counts) {
     __shared__ int64_t tmp[kCompBlock / 32 + 1];
-    int64_t base = (int64_t)blockIdx.x * kCompTile + (int64_t)threadIdx.x * kCompItems;
-    int64_t v[kCompItems];
+    int64_t base = (int64_t)blockIdx.x * kComp2Tile + (int64_t)threadIdx.x * kComp2Items;
+    int64_t v[kComp2Items];
     F g = f;
     if constexpr (has_counting<F>::value) g.counting = true;
     g.begin(base);
 #pragma unroll
-    for (int i = 0; i < kCompItems; i++) {
+    for (int i = 0; i < kComp2Items; i++) {
         typename F::value_type x;
         v[i] = (base + i < n && g.eval(base + i, x)) ? 1 : 0;
     }
-    int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kCompItems>(v, tmp);
+    int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kComp2Items>(v, tmp);
     if (threadIdx.x == 0) counts[blockIdx.x] = tot;
 }
 
@@ -155,24 +159,24 @@ template <class F>
 __global__ void k_compact_write(F f, int64_t n, const int64_t* __restrict__ offs,
                                 typename F::value_type* __restrict__ out, int64_t* __restrict__ count) {
     __shared__ int64_t tmp[kCompBlock / 32 + 1];
-    int64_t base = (int64_t)blockIdx.x * kCompTile + (int64_t)threadIdx.x * kCompItems;
-    int64_t v[kCompItems];
-    typename F::value_type val[kCompItems];
-    int64_t tg[kCompItems];
+    int64_t base = (int64_t)blockIdx.x * kComp2Tile + (int64_t)threadIdx.x * kComp2Items;
+    int64_t v[kComp2Items];
+    typename F::value_type val[kComp2Items];
+    int64_t tg[kComp2Items];
     F g = f;
     g.begin(base);
 #pragma unroll
-    for (int i = 0; i < kCompItems; i++) {
+    for (int i = 0; i < kComp2Items; i++) {
         v[i] = (base + i < n && g.eval(base + i, val[i])) ? 1 : 0;
         tg[i] = (base + i < n) ? g.tag(base + i) : -1;
     }
-    int64_t hit[kCompItems];
+    int64_t hit[kComp2Items];
 #pragma unroll
-    for (int i = 0; i < kCompItems; i++) hit[i] = v[i];
-    int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kCompItems>(v, tmp);
+    for (int i = 0; i < kComp2Items; i++) hit[i] = v[i];
+    int64_t tot = block_exclusive_scan<int64_t, kCompBlock, kComp2Items>(v, tmp);
     int64_t off = offs[blockIdx.x];
 #pragma unroll
-    for (int i = 0; i < kCompItems; i++) {
+    for (int i = 0; i < kComp2Items; i++) {
         if (tg[i] >= 0) g.at(tg[i], off + v[i]);
         if (hit[i]) out[off + v[i]] = val[i];
     }
@@ -298,8 +302,8 @@ __device__ __forceinline__ void begin_with(F& g, int64_t i0, const int64_t* h) {
     else g.begin(i0);
 }
 
-// A functor may also evaluate a thread's kCompItems consecutive indices at
-// once, so that their independent loads are in flight together:
+// A functor may also evaluate kEvalN consecutive indices at once, so that
+// their independent loads are in flight together:
 //   template <int N> __device__ void eval_n(int64_t i0, int64_t end,
 //       uint32_t& keep, value_type (&val)[N], int32_t (&tag)[N])
 // sets bit j of keep, val[j] and tag[j] (-1: none) as eval(i0 + j) and
@@ -307,46 +311,61 @@ __device__ __forceinline__ void begin_with(F& g, int64_t i0, const int64_t* h) {
 template <class F, class = void>
 struct has_eval_n : std::false_type {};
 template <class F>
-struct has_eval_n<F, std::void_t<decltype(std::declval<F&>().template eval_n<kCompItems>(
+struct has_eval_n<F, std::void_t<decltype(std::declval<F&>().template eval_n<kEvalN>(
                          int64_t(0), int64_t(0), std::declval<uint32_t&>(),
-                         std::declval<typename F::value_type (&)[kCompItems]>(), std::declval<int32_t (&)[kCompItems]>()))>>
+                         std::declval<typename F::value_type (&)[kEvalN]>(), std::declval<int32_t (&)[kEvalN]>()))>>
     : std::true_type {};
 
-// Shared memory of a compaction block.
+// Shared memory of a compaction block: the scan's warp totals, the tile's
+// description, and each index's value and tag staged between evaluation
+// and writing (so that a thread's 16 indices need few registers).
 struct CompShared {
     int32_t tmp[kCompBlock / 32 + 1];
     int64_t t, end, first, excl, hint[2];
     int seg;
+    uint32_t val[kCompBlock * kCompItems];
+    int32_t tag[kCompBlock * kCompItems];
 };
 
-// One tile [tb, tb + kCompTile) of an index space ending at `end`: evaluate,
-// scan (tile-local counts fit in 32 bits), publish and look back through
-// the status words `st` of the index space (tile lt of it), write.  Every
-// thread of the block calls it; `g` has had its begin().
+// One tile [tb, tb + kCompTile) of an index space ending at `end`: evaluate
+// (values and tags staged in shared memory, the kept indices as a bit mask),
+// scan the threads' kept counts, publish and look back through the status
+// words `st` of the index space (tile lt of it), write.  Every thread of the
+// block calls it; `g` has had its begin().
 template <class F>
 __device__ __forceinline__ void compact_tile(F& g, int64_t tb, int64_t end, unsigned long long* st, int64_t lt,
                                              typename F::value_type* __restrict__ out, int64_t* count,
                                              CompShared& sh) {
+    using V = typename F::value_type;
+    static_assert(sizeof(V) == 4, "staged values are 32-bit");
     const int64_t base = tb + (int64_t)threadIdx.x * kCompItems;
-    int32_t v[kCompItems];
-    int32_t tg[kCompItems];
-    typename F::value_type val[kCompItems];
+    V* sv = (V*)(sh.val + threadIdx.x);          // index i of this thread at [i * kCompBlock]:
+    int32_t* st_ = sh.tag + threadIdx.x;         // a warp's stores hit 32 distinct banks
     uint32_t hit = 0;
     if constexpr (has_eval_n<F>::value) {
-        g.template eval_n<kCompItems>(base, end, hit, val, tg);
 #pragma unroll
-        for (int i = 0; i < kCompItems; i++) v[i] = (hit >> i) & 1u;
+        for (int h = 0; h < kCompItems; h += kEvalN) {
+            V val[kEvalN];
+            int32_t tg[kEvalN];
+            uint32_t k = 0;
+            g.template eval_n<kEvalN>(base + h, end, k, val, tg);
+#pragma unroll
+            for (int i = 0; i < kEvalN; i++) { sv[(h + i) * kCompBlock] = val[i]; st_[(h + i) * kCompBlock] = tg[i]; }
+            hit |= k << h;
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < kCompItems; i++) {
             const bool in = base + i < end;
-            const bool k = in && g.eval(base + i, val[i]);
-            v[i] = k ? 1 : 0;
+            V x{};
+            const bool k = in && g.eval(base + i, x);
+            sv[i * kCompBlock] = x;
             hit |= (k ? 1u : 0u) << i;
-            tg[i] = in ? (int32_t)g.tag(base + i) : -1;     // rows and tags are below 2^31
+            st_[i * kCompBlock] = in ? (int32_t)g.tag(base + i) : -1;    // rows and tags are below 2^31
         }
     }
-    const int32_t tot = block_exclusive_scan<int32_t, kCompBlock, kCompItems>(v, sh.tmp);
+    int32_t mine[1] = {__popc(hit)};
+    const int32_t tot = block_exclusive_scan<int32_t, kCompBlock, 1>(mine, sh.tmp);
     if (threadIdx.x < 32) {
         const int64_t excl = tile_publish(st, lt, (int64_t)tot);
         if (threadIdx.x == 0) {
@@ -355,11 +374,13 @@ __device__ __forceinline__ void compact_tile(F& g, int64_t tb, int64_t end, unsi
         }
     }
     __syncthreads();
-    const int64_t off = sh.excl;
+    const int64_t off = sh.excl + mine[0];
+    int32_t r = 0;
 #pragma unroll
     for (int i = 0; i < kCompItems; i++) {
-        if (tg[i] >= 0) g.at((int64_t)tg[i], off + v[i]);
-        if ((hit >> i) & 1u) out[off + v[i]] = val[i];
+        const int32_t t = st_[i * kCompBlock];
+        if (t >= 0) g.at((int64_t)t, off + r);
+        if ((hit >> i) & 1u) out[off + r++] = sv[i * kCompBlock];
     }
     __syncthreads();
 }
@@ -419,7 +440,7 @@ int compact_alloc(const F& f, int64_t n, typename F::value_type** out, int64_t* 
     *out = nullptr;
     *kept_host = 0;
     if (n <= 0) return FAST_OK;
-    int64_t nb = ceil_div(n, kCompTile);
+    int64_t nb = ceil_div(n, kComp2Tile);
     int64_t* offs = nullptr;
     int64_t* tot = nullptr;
     FAST_TRY(dalloc(&offs, nb + 1, s));
