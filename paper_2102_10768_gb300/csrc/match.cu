@@ -180,10 +180,10 @@ __device__ __forceinline__ bool bsearch_u32(const uint32_t* __restrict__ a, int6
 
 // Warp-cooperative membership test.  Each lane with `act` holds a candidate
 // c; over those lanes the candidates ascend with the lane index (they come
-// from the generator list, sorted).  L[lo, hi) is another sorted list over
-// the same candidate set and *pos a cursor into it that never passes the
-// lower bound of any candidate still to come, so successive 32-entry
-// segments of the generator walk L once, merge-style:
+// from the generator list, sorted).  L[0, n) is another sorted list over the
+// same candidate set (one CST list: n < 2^31) and *pos a cursor into it that
+// never passes the lower bound of any candidate still to come, so successive
+// 32-entry segments of the generator walk L once, merge-style:
 //   - load the tile L[pos, pos+32) with one coalesced read;
 //   - every pending lane whose candidate is <= the tile's last entry finds
 //     its lower bound inside the tile by a 5-step shuffle search;
@@ -192,41 +192,41 @@ __device__ __forceinline__ bool bsearch_u32(const uint32_t* __restrict__ a, int6
 //     single parallel read, until a 32-entry window holds its lower bound.
 // Returns whether this lane's candidate is in the list; *lb counts the
 // entries this lane read (4 B each).
-__device__ __forceinline__ bool warp_member(const uint32_t* __restrict__ L, int64_t lo, int64_t hi, int64_t* pos,
+__device__ __forceinline__ bool warp_member(const uint32_t* __restrict__ L, uint32_t n, uint32_t* pos,
                                             uint32_t c, bool act, unsigned long long* lb) {
     const int lane = threadIdx.x & 31;
     bool found = false;
     uint32_t pend = __ballot_sync(0xffffffffu, act);
-    int64_t p0 = *pos < lo ? lo : *pos;
-    int64_t last = p0;
+    uint32_t p0 = *pos;
+    uint32_t last = p0;
     while (pend) {
-        if (p0 >= hi) break;                               // list exhausted: the rest are absent
+        if (p0 >= n) break;                                // list exhausted: the rest are absent
         int tl = __ffs(pend) - 1;
         uint32_t ct = __shfl_sync(0xffffffffu, c, tl);     // smallest pending candidate
         uint32_t v = 0xFFFFFFFFu;
-        if (p0 + lane < hi) { v = __ldg(L + p0 + lane); *lb += 4; }
+        if (p0 + lane < n) { v = __ldg(L + p0 + lane); *lb += 4; }
         uint32_t tmax = __shfl_sync(0xffffffffu, v, 31);
         if (tmax < ct) {
             // gallop: the lower bound of ct lies past this (full) tile
-            int64_t a = p0 + 32;                            // first index that may hold it
-            int64_t probe = p0 + 31 + ((int64_t)32 << (lane < 25 ? lane : 25));
-            if (probe > hi - 1) probe = hi - 1;
+            uint32_t a = p0 + 32;                           // first index that may hold it
+            uint32_t probe = p0 + 31 + (32u << (lane < 25 ? lane : 25));   // below 2^32: p0 < 2^31
+            if (probe > n - 1) probe = n - 1;
             uint32_t pv = __ldg(L + probe);
             *lb += 4;
             uint32_t ge = __ballot_sync(0xffffffffu, pv >= ct);
-            if (!ge) { p0 = hi; break; }                    // everything left is smaller: all absent
+            if (!ge) { p0 = n; break; }                     // everything left is smaller: all absent
             int f = __ffs(ge) - 1;
-            int64_t b = __shfl_sync(0xffffffffu, probe, f);            // L[b] >= ct
+            uint32_t b = __shfl_sync(0xffffffffu, probe, f);            // L[b] >= ct
             if (f > 0) a = __shfl_sync(0xffffffffu, probe, f - 1) + 1; // L[a-1] < ct
             while (b - a > 31) {                            // 33-way refinement of [a, b]
-                int64_t span = b - a + 1;
-                int64_t q = a + ((int64_t)(lane + 1) * span) / 33;
+                const uint64_t span = b - a + 1;
+                uint32_t q = a + (uint32_t)(((uint64_t)(lane + 1) * span) / 33);
                 uint32_t qv = __ldg(L + q);
                 *lb += 4;
                 uint32_t g2 = __ballot_sync(0xffffffffu, qv >= ct);
                 int f2 = g2 ? __ffs(g2) - 1 : 32;
-                int64_t nb = f2 < 32 ? __shfl_sync(0xffffffffu, q, f2 < 32 ? f2 : 0) : b;
-                int64_t na = f2 > 0 ? __shfl_sync(0xffffffffu, q, f2 > 0 ? f2 - 1 : 0) + 1 : a;
+                uint32_t nb = f2 < 32 ? __shfl_sync(0xffffffffu, q, f2 < 32 ? f2 : 0) : b;
+                uint32_t na = f2 > 0 ? __shfl_sync(0xffffffffu, q, f2 > 0 ? f2 - 1 : 0) + 1 : a;
                 a = na;
                 b = nb;
             }
@@ -399,10 +399,10 @@ __device__ void validate_tasks(const MatchPlan& P0, const MatchPlan* __restrict_
                 if (!__any_sync(0xffffffffu, ok)) break;
                 const uint32_t* L = x == 0 ? P.t_idx[d] : P.n_idx[e0 + x - 1];
                 const int64_t lo = T.lo[x], hi = T.hi[x];
-                int64_t c = lo + cur[x];
-                ok = warp_member(L, lo, hi, &c, cnd, ok, &lb);
+                uint32_t c = (uint32_t)cur[x];
+                ok = warp_member(L + lo, (uint32_t)(hi - lo), &c, cnd, ok, &lb);
                 __syncwarp();
-                if (lane == 0) cur[x] = c - lo;
+                if (lane == 0) cur[x] = c;
                 __syncwarp();
             }
             uint32_t sl = P.same_lab[d];
@@ -714,6 +714,73 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                 }
                 int64_t sn = __shfl_sync(0xffffffffu, seg_next, d);
                 int64_t se = __shfl_sync(0xffffffffu, seg_end, d);
+                if (!EMIT && d == k - 1 && d > 0 && sn < se) {
+                    // The last position: its segments one after another in a
+                    // loop of their own, the same Generator, EdgeValidator and
+                    // VisitedValidator steps as below, with each list's first
+                    // entry, length and merge cursor held by one lane (lane 0
+                    // the tree list, lane x the x-th non-tree list into d).
+                    // Back to the main loop when the run ends and before every
+                    // 64th step, where the periodic checks and donations are.
+                    const int src = gsrc[d];
+                    const int e0 = P.nt_begin[d], ne = P.nt_begin[d + 1] - e0;
+                    const int from = lane == 0 ? P.par[d] : (lane <= ne ? P.nt_from[e0 + lane - 1] : 0);
+                    const uint32_t mf = __shfl_sync(0xffffffffu, m_reg, from);
+                    const uint32_t* lp = nullptr;
+                    uint32_t ln = 0, lc = 0;
+                    if (lane <= ne) {
+                        const int64_t* off = lane == 0 ? P.t_off[d] : P.n_off[e0 + lane - 1];
+                        const int64_t lo = off[mf];
+                        lp = (lane == 0 ? P.t_idx[d] : P.n_idx[e0 + lane - 1]) + lo;
+                        ln = (uint32_t)(off[mf + 1] - lo);
+                        lc = (uint32_t)(lane == 0 ? tcur[d] : ncur[e0 + lane - 1]);
+                    }
+                    const uint32_t* gp = (const uint32_t*)__shfl_sync(0xffffffffu, (unsigned long long)lp, src);
+                    const int64_t sb = __shfl_sync(0xffffffffu, seg_base, d);
+                    uint32_t r = (uint32_t)(sn - sb);
+                    const uint32_t re = (uint32_t)(se - sb);
+                    const uint32_t sl0 = P.same_lab[d];
+                    const int32_t* cd = P.cand[d];
+                    for (;;) {
+                        const uint32_t i = r + lane;
+                        bool ok = i < re;
+                        uint32_t cnd = 0;
+                        if (ok) { cnd = __ldg(gp + i); lb += 4; }
+                        if (lane == 0) fb += 4ull * (re - r < 32 ? re - r : 32);
+                        for (int x = 0; x <= ne; x++) {
+                            if (x == src) continue;
+                            if (!__any_sync(0xffffffffu, ok)) break;
+                            const uint32_t* L = (const uint32_t*)__shfl_sync(0xffffffffu, (unsigned long long)lp, x);
+                            const uint32_t n = __shfl_sync(0xffffffffu, ln, x);
+                            uint32_t c = __shfl_sync(0xffffffffu, lc, x);
+                            ok = warp_member(L, n, &c, cnd, ok, &lb);
+                            if (lane == x) lc = c;
+                        }
+                        if (sl0) {
+                            const uint32_t pm = __ballot_sync(0xffffffffu, ok);
+                            if (lane == 0) fb += 4ull * __popc(pm);
+                            int32_t gc = -1;
+                            if (ok) { gc = __ldg(cd + cnd); lb += 4; }
+                            uint32_t sl = sl0;
+                            while (sl) {
+                                const int p = __ffs(sl) - 1;
+                                sl &= sl - 1;
+                                if (__shfl_sync(0xffffffffu, g_reg, p) == gc) ok = false;
+                            }
+                        }
+                        const uint32_t mask = __ballot_sync(0xffffffffu, ok);
+                        if (STATS && lane == 0) atomicAdd(&O.stats[d], (unsigned long long)__popc(mask));
+                        if (lane == 0) { local += __popc(mask); ccount += __popc(mask); }
+                        r += 32;
+                        if (r >= re || ((iter + 1) & 63) == 0) break;
+                        ++iter;
+                    }
+                    if (lane == d) seg_next = sb + r;
+                    if (lane == 0) tcur[d] = lc;
+                    else if (lane <= ne) ncur[e0 + lane - 1] = lc;
+                    __syncwarp();
+                    continue;
+                }
                 if (sn < se) {
                     // Generator: next 32 entries of depth d's list
                     int64_t idx = sn + lane;
@@ -730,10 +797,10 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                     if (src != 0 && __any_sync(0xffffffffu, ok)) {
                         uint32_t mp = __shfl_sync(0xffffffffu, m_reg, P.par[d]);
                         int64_t lo = P.t_off[d][mp], hi = P.t_off[d][mp + 1];
-                        int64_t cur = lo + tcur[d];
-                        ok = warp_member(P.t_idx[d], lo, hi, &cur, cnd, ok, &lb);
+                        uint32_t cur = (uint32_t)tcur[d];
+                        ok = warp_member(P.t_idx[d] + lo, (uint32_t)(hi - lo), &cur, cnd, ok, &lb);
                         __syncwarp();
-                        if (lane == 0) tcur[d] = cur - lo;
+                        if (lane == 0) tcur[d] = cur;
                         __syncwarp();
                     }
                     // EdgeValidator (most selective edge first; stop once no lane is pending)
@@ -742,10 +809,10 @@ __global__ void __launch_bounds__(256, 4) k_match(const __grid_constant__ MatchP
                         if (!__any_sync(0xffffffffu, ok)) break;
                         uint32_t mf = __shfl_sync(0xffffffffu, m_reg, P.nt_from[e]);
                         int64_t lo = P.n_off[e][mf], hi = P.n_off[e][mf + 1];
-                        int64_t cur = lo + ncur[e];
-                        ok = warp_member(P.n_idx[e], lo, hi, &cur, cnd, ok, &lb);
+                        uint32_t cur = (uint32_t)ncur[e];
+                        ok = warp_member(P.n_idx[e] + lo, (uint32_t)(hi - lo), &cur, cnd, ok, &lb);
                         __syncwarp();
-                        if (lane == 0) ncur[e] = cur - lo;
+                        if (lane == 0) ncur[e] = cur;
                         __syncwarp();
                     }
                     // VisitedValidator
