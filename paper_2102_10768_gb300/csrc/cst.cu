@@ -129,9 +129,11 @@ __global__ void k_set_bits_n(const int32_t* __restrict__ ids, const int64_t* __r
 //
 // The lists of a CST level are one flattened entry space (offsets over the
 // rows of a candidate set).  On a power-law graph a few hub rows hold most
-// entries, so these kernels split the entry space, not the rows: a block
-// takes tiles of kTileItems entries (grid-stride), each thread kItems
-// consecutive entries, finds its first row by binary search and advances it.
+// entries, so these kernels split the entry space, not the rows: a warp
+// takes tiles of kWarpTileItems entries (grid-stride), finds the rows of the
+// tile's ends by a 33-way search of the 32 lanes together, and each thread
+// takes kItems consecutive entries, finds its first row between those two
+// by binary search and advances it.
 
 inline unsigned tile_grid(int64_t entries_bound) {
     int64_t t = ceil_div(entries_bound, (int64_t)kTileItems);
@@ -140,24 +142,34 @@ inline unsigned tile_grid(int64_t entries_bound) {
     return (unsigned)(t < 1 ? 1 : t);
 }
 
-// has[r] = 1 if row r (of *nrows) keeps an entry alive in `alive`
+// has[r] = 1 if row r (of *nrows) keeps an entry alive in `alive`.  Each
+// warp takes tiles of kWarpTileItems entries (grid-stride over the warps),
+// finds the rows of its first and last entries, and each thread its kItems.
 __global__ void __launch_bounds__(256) k_any_alive(const int64_t* __restrict__ off, const int64_t* __restrict__ nrows,
                                                    const int32_t* __restrict__ list, const uint32_t* __restrict__ alive,
                                                    uint8_t* __restrict__ has) {
     const int64_t rows = *nrows;
     const int64_t e_end = off[rows];
-    for (int64_t t = blockIdx.x; t * kTileItems < e_end; t += gridDim.x) {
-        int64_t i0 = t * kTileItems + (int64_t)threadIdx.x * kItems;
-        if (i0 >= e_end) continue;
-        int64_t row = row_of(off, rows, i0), done = -1;
-        for (int i = 0; i < kItems; i++) {
-            int64_t e = i0 + i;
-            if (e >= e_end) break;
-            while (e >= off[row + 1]) row++;
-            if (row == done) continue;
-            int32_t x = list[e];
-            if ((alive[x >> 5] >> (x & 31)) & 1u) { has[row] = 1; done = row; }
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t t = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); t * kWarpTileItems < e_end;
+         t += (int64_t)gridDim.x * wpb) {
+        const int64_t tb = t * kWarpTileItems;
+        const int64_t te = tb + kWarpTileItems < e_end ? tb + kWarpTileItems : e_end;
+        int64_t r0, r1;
+        warp_rows_of(off, rows, tb, te - 1, &r0, &r1);
+        const int64_t i0 = tb + (int64_t)(threadIdx.x & 31) * kItems;
+        if (i0 < te) {
+            int64_t row = row_in(off, r0, r1, i0), done = -1;
+            for (int i = 0; i < kItems; i++) {
+                int64_t e = i0 + i;
+                if (e >= te) break;
+                while (e >= off[row + 1]) row++;
+                if (row == done) continue;
+                int32_t x = list[e];
+                if ((alive[x >> 5] >> (x & 31)) & 1u) { has[row] = 1; done = row; }
+            }
         }
+        __syncwarp();
     }
 }
 
@@ -173,45 +185,23 @@ __global__ void k_valid_rows_n(ChildFlags cf, const int64_t* __restrict__ nrows,
 }
 
 // Workload, first half (Sec. IV-C): per row r of C(u) and one child c, the
-// sum of c_c over r's list into c.  Entries are split as above; a thread
-// adds each row segment it covers with one atomic.  Saturation: a segment
-// that wrapped or carried a saturated term, or an atomic that wrapped, sets
-// ovf[r], and the row's sum then reads as 2^64 - 1.
-__global__ void __launch_bounds__(256) k_child_sums(const int64_t* __restrict__ off, int64_t rows,
-                                                    const uint32_t* __restrict__ idx,
-                                                    const uint64_t* __restrict__ cv, const double* __restrict__ cvf,
-                                                    unsigned long long* __restrict__ ssum, double* __restrict__ sumf,
-                                                    uint32_t* __restrict__ ovf) {
+// sum of c_c over r's list into c.  Warp tiles as in k_any_alive; each
+// thread adds its kItems entries row by row (child_sum_entries).
+__global__ void __launch_bounds__(256, 4) k_child_sums(const int64_t* __restrict__ off, int64_t rows,
+                                                       const uint32_t* __restrict__ idx,
+                                                       const uint64_t* __restrict__ cv, const double* __restrict__ cvf,
+                                                       unsigned long long* __restrict__ ssum, double* __restrict__ sumf,
+                                                       uint32_t* __restrict__ ovf) {
     const int64_t e_end = off[rows];
-    for (int64_t t = blockIdx.x; t * kTileItems < e_end; t += gridDim.x) {
-        int64_t i0 = t * kTileItems + (int64_t)threadIdx.x * kItems;
-        if (i0 >= e_end) continue;
-        int64_t row = row_of(off, rows, i0);
-        unsigned long long s = 0;
-        double sf = 0.0;
-        bool sat = false;
-        auto flush = [&]() {
-            unsigned long long old = atomicAdd(&ssum[row], s);
-            if (old + s < old) sat = true;
-            if (sat) atomicOr(&ovf[row], 1u);
-            atomicAdd(&sumf[row], sf);
-        };
-        for (int i = 0; i < kItems; i++) {
-            int64_t e = i0 + i;
-            if (e >= e_end) break;
-            if (e >= off[row + 1]) {
-                flush();
-                s = 0; sf = 0.0; sat = false;
-                do row++; while (e >= off[row + 1]);
-            }
-            uint32_t x = idx[e];
-            uint64_t v = cv[x];
-            unsigned long long ns = s + v;
-            if (ns < s || v == ~0ull) sat = true;
-            s = ns;
-            sf += cvf[x];
-        }
-        flush();
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t t = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); t * kWarpTileItems < e_end;
+         t += (int64_t)gridDim.x * wpb) {
+        const int64_t tb = t * kWarpTileItems;
+        const int64_t te = tb + kWarpTileItems < e_end ? tb + kWarpTileItems : e_end;
+        int64_t r0, r1;
+        warp_rows_of(off, rows, tb, te - 1, &r0, &r1);
+        child_sum_entries(off, r0, r1, tb + (int64_t)(threadIdx.x & 31) * kItems, te, idx, cv, cvf, ssum, sumf, ovf);
+        __syncwarp();
     }
 }
 

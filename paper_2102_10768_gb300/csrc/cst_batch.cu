@@ -137,53 +137,53 @@ struct AnyAliveDesc {
 // A tile of a tile-split kernel: its segment, its entry range [tb, te) and
 // the rows of its first and last entries (every entry's row lies between),
 // found once per tile by warp 0.
-struct TileRows {
+// A warp's tile t of a tile-split batched step: its segment, its entries
+// [tb, te) and the rows r0, r1 of its first and last entries, found by the
+// 32 lanes together (every lane returns them).
+struct WarpTile {
     int s;
     int64_t tb, te, r0, r1;
 };
 
 template <class D>
-__device__ __forceinline__ bool tile_rows(const D* __restrict__ Dd, const int64_t* __restrict__ tile_off, int nseg,
-                                          int64_t t, TileRows* sh) {
-    if (threadIdx.x < 32) {
-        const int s = seg_of_tile(tile_off, nseg, t);
-        const D& d = Dd[s];
-        const int64_t e_end = d.off[d.rows];
-        const int64_t tb = (t - tile_off[s]) * kTileItems;
-        const int64_t te = tb + kTileItems < e_end ? tb + kTileItems : e_end;
-        int64_t r0 = 0, r1 = 0;
-        if (tb < te) {
-            r0 = warp_row_of(d.off, d.rows, tb);
-            r1 = warp_row_of(d.off, d.rows, te - 1);
-        }
-        if (threadIdx.x == 0) { sh->s = s; sh->tb = tb; sh->te = te; sh->r0 = r0; sh->r1 = r1; }
-    }
-    __syncthreads();
-    return sh->tb < sh->te;
+__device__ __forceinline__ WarpTile warp_tile(const D* __restrict__ Dd, const int64_t* __restrict__ tile_off, int nseg,
+                                              int64_t t) {
+    WarpTile w;
+    w.s = seg_of_tile(tile_off, nseg, t);
+    const D& d = Dd[w.s];
+    const int64_t e_end = d.off[d.rows];
+    w.tb = (t - tile_off[w.s]) * kWarpTileItems;
+    w.te = w.tb + kWarpTileItems < e_end ? w.tb + kWarpTileItems : e_end;
+    w.r0 = w.r1 = 0;
+    if (w.tb < w.te) warp_rows_of(d.off, d.rows, w.tb, w.te - 1, &w.r0, &w.r1);
+    return w;
 }
+
+// grid-stride over the warps of the grid
+#define FOR_WARP_TILES(t, total)                                                                        \
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < (total);       \
+         t += (int64_t)gridDim.x * (blockDim.x >> 5))
 
 __global__ void __launch_bounds__(256) k_any_alive_b(const AnyAliveDesc* __restrict__ D,
                                                      const int64_t* __restrict__ tile_off, int nseg) {
-    __shared__ TileRows tr;
     const int64_t total = tile_off[nseg];
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        if (tile_rows(D, tile_off, nseg, t, &tr)) {
-            const AnyAliveDesc& d = D[tr.s];
-            const int64_t* off = d.off;
-            const int64_t i0 = tr.tb + (int64_t)threadIdx.x * kItems;
-            if (i0 < tr.te) {
-                int64_t row = row_in(off, tr.r0, tr.r1, i0), done = -1;
-                for (int i = 0; i < kItems; i++) {
-                    int64_t e = i0 + i;
-                    if (e >= tr.te) break;
-                    while (e >= off[row + 1]) row++;
-                    if (row == done) continue;
-                    int32_t x = d.list[e];
-                    if ((d.alive[x >> 5] >> (x & 31)) & 1u) { d.has[row] = 1; done = row; }
-                }
+    FOR_WARP_TILES(t, total) {
+        const WarpTile w = warp_tile(D, tile_off, nseg, t);
+        const AnyAliveDesc& d = D[w.s];
+        const int64_t* off = d.off;
+        const int64_t i0 = w.tb + (int64_t)(threadIdx.x & 31) * kItems;
+        if (i0 < w.te) {
+            int64_t row = row_in(off, w.r0, w.r1, i0), done = -1;
+            for (int i = 0; i < kItems; i++) {
+                int64_t e = i0 + i;
+                if (e >= w.te) break;
+                while (e >= off[row + 1]) row++;
+                if (row == done) continue;
+                int32_t x = d.list[e];
+                if ((d.alive[x >> 5] >> (x & 31)) & 1u) { d.has[row] = 1; done = row; }
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -280,55 +280,15 @@ struct ChildSumDesc {
     uint32_t* ovf;
 };
 
-__global__ void __launch_bounds__(256) k_child_sums_b(const ChildSumDesc* __restrict__ D,
-                                                      const int64_t* __restrict__ tile_off, int nseg) {
-    __shared__ TileRows tr;
+__global__ void __launch_bounds__(256, 4) k_child_sums_b(const ChildSumDesc* __restrict__ D,
+                                                         const int64_t* __restrict__ tile_off, int nseg) {
     const int64_t total = tile_off[nseg];
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        if (tile_rows(D, tile_off, nseg, t, &tr)) {
-            const ChildSumDesc& d = D[tr.s];
-            const int64_t* off = d.off;
-            const int64_t i0 = tr.tb + (int64_t)threadIdx.x * kItems;
-            if (i0 < tr.te) {
-                // the thread's entries' child indices, then their values, all in flight at once
-                uint32_t x[kItems];
-#pragma unroll
-                for (int i = 0; i < kItems; i++) x[i] = i0 + i < tr.te ? __ldg(d.idx + i0 + i) : 0u;
-                uint64_t v[kItems];
-                double vf[kItems];
-#pragma unroll
-                for (int i = 0; i < kItems; i++) {
-                    const bool in = i0 + i < tr.te;
-                    v[i] = in ? __ldg(d.cv + x[i]) : 0ull;
-                    vf[i] = in ? __ldg(d.cvf + x[i]) : 0.0;
-                }
-                int64_t row = row_in(off, tr.r0, tr.r1, i0);
-                unsigned long long s = 0;
-                double sf = 0.0;
-                bool sat = false;
-                auto flush = [&]() {
-                    unsigned long long old = atomicAdd(&d.ssum[row], s);
-                    if (old + s < old) sat = true;
-                    if (sat) atomicOr(&d.ovf[row], 1u);
-                    atomicAdd(&d.sumf[row], sf);
-                };
-                for (int i = 0; i < kItems; i++) {
-                    int64_t e = i0 + i;
-                    if (e >= tr.te) break;
-                    if (e >= off[row + 1]) {
-                        flush();
-                        s = 0; sf = 0.0; sat = false;
-                        do row++; while (e >= off[row + 1]);
-                    }
-                    unsigned long long ns = s + v[i];
-                    if (ns < s || v[i] == ~0ull) sat = true;
-                    s = ns;
-                    sf += vf[i];
-                }
-                flush();
-            }
-        }
-        __syncthreads();
+    FOR_WARP_TILES(t, total) {
+        const WarpTile w = warp_tile(D, tile_off, nseg, t);
+        const ChildSumDesc& d = D[w.s];
+        child_sum_entries(d.off, w.r0, w.r1, w.tb + (int64_t)(threadIdx.x & 31) * kItems, w.te, d.idx, d.cv, d.cvf,
+                          d.ssum, d.sumf, d.ovf);
+        __syncwarp();
     }
 }
 
@@ -484,14 +444,14 @@ int run_tiles(void (*kernel)(const D*, const int64_t*, int), const std::vector<D
               const std::vector<int64_t>& entries, cudaStream_t s) {
     if (desc.empty()) return FAST_OK;
     std::vector<int64_t> t(entries.size());
-    for (size_t i = 0; i < entries.size(); i++) t[i] = ceil_div(entries[i], (int64_t)kTileItems);
+    for (size_t i = 0; i < entries.size(); i++) t[i] = ceil_div(entries[i], (int64_t)kWarpTileItems);
     const std::vector<int64_t> off = prefix(t);
     if (off.back() == 0) return FAST_OK;
     Scratch sc(s);
     const D* dd = nullptr;
     const int64_t* doff = nullptr;
     FAST_TRY(upload(desc, off, sc, &dd, &doff));
-    const int64_t grid = std::min<int64_t>(off.back(), (int64_t)num_sms() * 8);
+    const int64_t grid = std::min<int64_t>(ceil_div(off.back(), (int64_t)8), (int64_t)num_sms() * 8);
     kernel<<<(unsigned)grid, 256, 0, s>>>(dd, doff, (int)desc.size());
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return set_error(FAST_ERR_CUDA, "batched CST step launch");

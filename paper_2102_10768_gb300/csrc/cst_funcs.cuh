@@ -105,8 +105,8 @@ struct TopDownF {
     __device__ void tile_hint(int64_t tb, int64_t te, int64_t* h) {
         const int64_t e = *E;
         if (te > e) te = e;
-        const int64_t r0 = warp_row_of(e_off, rows, tb);
-        const int64_t r1 = te > tb ? warp_row_of(e_off, rows, te - 1) : r0;
+        int64_t r0, r1;
+        warp_rows_of(e_off, rows, tb, te > tb ? te - 1 : tb, &r0, &r1);
         if ((threadIdx.x & 31) == 0) { h[0] = r0; h[1] = r1; }
     }
     __device__ void begin(int64_t i0, const int64_t* h) {
@@ -211,8 +211,8 @@ struct NonTreeF {
     __device__ void tile_hint(int64_t tb, int64_t te, int64_t* h) {
         const int64_t e = *E;
         if (te > e) te = e;
-        const int64_t r0 = warp_row_of(e_off, rows, tb);
-        const int64_t r1 = te > tb ? warp_row_of(e_off, rows, te - 1) : r0;
+        int64_t r0, r1;
+        warp_rows_of(e_off, rows, tb, te > tb ? te - 1 : tb, &r0, &r1);
         if ((threadIdx.x & 31) == 0) { h[0] = r0; h[1] = r1; }
     }
     __device__ void begin(int64_t i0, const int64_t* h) {
@@ -283,7 +283,68 @@ struct KeepRowsF {
 };
 
 constexpr int kItems = 8;
-constexpr int kTileItems = 256 * kItems;
+constexpr int kTileItems = 256 * kItems;     // a block's tile (8 warps)
+constexpr int kWarpTileItems = 32 * kItems;  // a warp's tile
+
+// Child sums over the entries [i0, iend) of one thread (Sec. IV-C, first
+// half of the workload DP: per row r and child c, the sum of c_c over r's
+// list into c), rows found between r0 and r1.  A row whose entries all lie
+// in the range is written with plain stores; a row shared with another
+// thread is added with atomics.  Saturation: a sum that wrapped or carried a
+// saturated term, or an atomic that wrapped, sets ovf[r], and the row's sum
+// then reads as 2^64 - 1.
+__device__ __forceinline__ void child_sum_entries(const int64_t* __restrict__ off, int64_t r0, int64_t r1, int64_t i0,
+                                                  int64_t iend, const uint32_t* __restrict__ idx,
+                                                  const uint64_t* __restrict__ cv, const double* __restrict__ cvf,
+                                                  unsigned long long* __restrict__ ssum, double* __restrict__ sumf,
+                                                  uint32_t* __restrict__ ovf) {
+    if (i0 >= iend) return;
+    // the thread's entries' child indices, then their values, all in flight at once
+    uint32_t x[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; i++) x[i] = i0 + i < iend ? __ldg(idx + i0 + i) : 0u;
+    uint64_t v[kItems];
+    double vf[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; i++) {
+        const bool in = i0 + i < iend;
+        v[i] = in ? __ldg(cv + x[i]) : 0ull;
+        vf[i] = in ? __ldg(cvf + x[i]) : 0.0;
+    }
+    int64_t row = row_in(off, r0, r1, i0);
+    int64_t rend = off[row + 1];
+    bool own = off[row] == i0;           // the row starts in this range
+    unsigned long long s = 0;
+    double sf = 0.0;
+    bool sat = false;
+    auto flush = [&](bool whole) {
+        if (whole) {
+            ssum[row] = s;
+            sumf[row] = sf;
+            if (sat) ovf[row] = 1u;
+        } else {
+            const unsigned long long old = atomicAdd(&ssum[row], s);
+            if (old + s < old) sat = true;
+            if (sat) atomicOr(&ovf[row], 1u);
+            atomicAdd(&sumf[row], sf);
+        }
+    };
+    for (int i = 0; i < kItems; i++) {
+        const int64_t e = i0 + i;
+        if (e >= iend) break;
+        if (e >= rend) {
+            flush(own);                  // the row ended inside the range
+            s = 0; sf = 0.0; sat = false;
+            do { row++; rend = off[row + 1]; } while (e >= rend);
+            own = true;                  // a later row starts at e (empty rows between share the offset)
+        }
+        const unsigned long long ns = s + v[i];
+        if (ns < s || v[i] == ~0ull) sat = true;
+        s = ns;
+        sf += vf[i];
+    }
+    flush(own && rend == (i0 + kItems < iend ? i0 + kItems : iend));
+}
 
 struct ChildFlags {
     const uint8_t* has[kMaxK];
@@ -309,8 +370,8 @@ struct WriteAliveF {
     __device__ void tile_hint(int64_t tb, int64_t te, int64_t* h) {
         const int64_t r = *nrows, e = off[r];
         if (te > e) te = e;
-        const int64_t r0 = warp_row_of(off, r, tb);
-        const int64_t r1 = te > tb ? warp_row_of(off, r, te - 1) : r0;
+        int64_t r0, r1;
+        warp_rows_of(off, r, tb, te > tb ? te - 1 : tb, &r0, &r1);
         if ((threadIdx.x & 31) == 0) { h[0] = r0; h[1] = r1; }
     }
     __device__ void begin(int64_t i0, const int64_t* h) {

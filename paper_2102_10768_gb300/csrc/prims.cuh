@@ -280,6 +280,33 @@ __device__ __forceinline__ int64_t warp_row_of(const int64_t* __restrict__ e_off
     return lo;
 }
 
+// The rows of two indices i <= j of the same offsets at once: the two
+// 33-way searches of warp_row_of advance together, so each round's probes
+// of both are loaded in one go.  A search that has finished keeps probing
+// its own row, which leaves it where it is.
+__device__ __forceinline__ void warp_rows_of(const int64_t* __restrict__ e_off, int64_t rows, int64_t i, int64_t j,
+                                             int64_t* ri, int64_t* rj) {
+    const int lane = threadIdx.x & 31;
+    int64_t alo = 0, ahi = rows, blo = 0, bhi = rows;
+    while (ahi - alo > 1 || bhi - blo > 1) {
+        const int64_t pa = alo + ((ahi - alo) * (lane + 1)) / 33;
+        const int64_t pb = blo + ((bhi - blo) * (lane + 1)) / 33;
+        const int64_t va = e_off[pa], vb = e_off[pb];
+        const int ca = __popc(__ballot_sync(0xffffffffu, va <= i));
+        const int cb = __popc(__ballot_sync(0xffffffffu, vb <= j));
+        const int64_t alo2 = __shfl_sync(0xffffffffu, pa, ca > 0 ? ca - 1 : 0);
+        const int64_t ahi2 = __shfl_sync(0xffffffffu, pa, ca < 32 ? ca : 31);
+        const int64_t blo2 = __shfl_sync(0xffffffffu, pb, cb > 0 ? cb - 1 : 0);
+        const int64_t bhi2 = __shfl_sync(0xffffffffu, pb, cb < 32 ? cb : 31);
+        if (ca > 0) alo = alo2;
+        if (ca < 32) ahi = ahi2;
+        if (cb > 0) blo = blo2;
+        if (cb < 32) bhi = bhi2;
+    }
+    *ri = alo;
+    *rj = blo;
+}
+
 // A functor may narrow its per-thread setup with a hint computed once per
 // tile: `__device__ void tile_hint(int64_t tb, int64_t te, int64_t* h)` (by
 // the 32 lanes of warp 0 together; lane 0 writes h[0..1]) and `__device__
