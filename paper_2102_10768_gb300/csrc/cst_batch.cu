@@ -164,26 +164,54 @@ __device__ __forceinline__ WarpTile warp_tile(const D* __restrict__ Dd, const in
     for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < (total);       \
          t += (int64_t)gridDim.x * (blockDim.x >> 5))
 
+// A block's tile t (kTileItems entries): warp 0 finds its segment and the
+// rows of its first and last entries, the block waits for them.
+struct TileRows {
+    int s;
+    int64_t tb, te, r0, r1;
+};
+
+template <class D>
+__device__ __forceinline__ bool tile_rows(const D* __restrict__ Dd, const int64_t* __restrict__ tile_off, int nseg,
+                                          int64_t t, TileRows* sh) {
+    if (threadIdx.x < 32) {
+        const int s = seg_of_tile(tile_off, nseg, t);
+        const D& d = Dd[s];
+        const int64_t e_end = d.off[d.rows];
+        const int64_t tb = (t - tile_off[s]) * kTileItems;
+        const int64_t te = tb + kTileItems < e_end ? tb + kTileItems : e_end;
+        int64_t r0 = 0, r1 = 0;
+        if (tb < te) warp_rows_of(d.off, d.rows, tb, te - 1, &r0, &r1);
+        if (threadIdx.x == 0) { sh->s = s; sh->tb = tb; sh->te = te; sh->r0 = r0; sh->r1 = r1; }
+    }
+    __syncthreads();
+    return sh->tb < sh->te;
+}
+
+// Block tiles here: the per-entry work (one list entry, one bitmap word) is
+// small next to a row search per warp tile.
 __global__ void __launch_bounds__(256) k_any_alive_b(const AnyAliveDesc* __restrict__ D,
                                                      const int64_t* __restrict__ tile_off, int nseg) {
+    __shared__ TileRows tr;
     const int64_t total = tile_off[nseg];
-    FOR_WARP_TILES(t, total) {
-        const WarpTile w = warp_tile(D, tile_off, nseg, t);
-        const AnyAliveDesc& d = D[w.s];
-        const int64_t* off = d.off;
-        const int64_t i0 = w.tb + (int64_t)(threadIdx.x & 31) * kItems;
-        if (i0 < w.te) {
-            int64_t row = row_in(off, w.r0, w.r1, i0), done = -1;
-            for (int i = 0; i < kItems; i++) {
-                int64_t e = i0 + i;
-                if (e >= w.te) break;
-                while (e >= off[row + 1]) row++;
-                if (row == done) continue;
-                int32_t x = d.list[e];
-                if ((d.alive[x >> 5] >> (x & 31)) & 1u) { d.has[row] = 1; done = row; }
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        if (tile_rows(D, tile_off, nseg, t, &tr)) {
+            const AnyAliveDesc& d = D[tr.s];
+            const int64_t* off = d.off;
+            const int64_t i0 = tr.tb + (int64_t)threadIdx.x * kItems;
+            if (i0 < tr.te) {
+                int64_t row = row_in(off, tr.r0, tr.r1, i0), done = -1;
+                for (int i = 0; i < kItems; i++) {
+                    int64_t e = i0 + i;
+                    if (e >= tr.te) break;
+                    while (e >= off[row + 1]) row++;
+                    if (row == done) continue;
+                    int32_t x = d.list[e];
+                    if ((d.alive[x >> 5] >> (x & 31)) & 1u) { d.has[row] = 1; done = row; }
+                }
             }
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -438,20 +466,22 @@ int run_items(void (*kernel)(const D*, const int64_t*, int, X...), const std::ve
     return FAST_OK;
 }
 
-// A tile-split batched kernel over segments of e_s list entries.
+// A tile-split batched kernel over segments of e_s list entries, in tiles
+// of `tile` entries, `per_block` tiles to a block of 256 threads (8: warp
+// tiles; 1: block tiles).
 template <class D>
 int run_tiles(void (*kernel)(const D*, const int64_t*, int), const std::vector<D>& desc,
-              const std::vector<int64_t>& entries, cudaStream_t s) {
+              const std::vector<int64_t>& entries, int tile, int per_block, cudaStream_t s) {
     if (desc.empty()) return FAST_OK;
     std::vector<int64_t> t(entries.size());
-    for (size_t i = 0; i < entries.size(); i++) t[i] = ceil_div(entries[i], (int64_t)kWarpTileItems);
+    for (size_t i = 0; i < entries.size(); i++) t[i] = ceil_div(entries[i], (int64_t)tile);
     const std::vector<int64_t> off = prefix(t);
     if (off.back() == 0) return FAST_OK;
     Scratch sc(s);
     const D* dd = nullptr;
     const int64_t* doff = nullptr;
     FAST_TRY(upload(desc, off, sc, &dd, &doff));
-    const int64_t grid = std::min<int64_t>(ceil_div(off.back(), (int64_t)8), (int64_t)num_sms() * 8);
+    const int64_t grid = std::min<int64_t>(ceil_div(off.back(), (int64_t)per_block), (int64_t)num_sms() * 8);
     kernel<<<(unsigned)grid, 256, 0, s>>>(dd, doff, (int)desc.size());
     note_launch();
     if (cudaGetLastError() != cudaSuccess) return set_error(FAST_ERR_CUDA, "batched CST step launch");
@@ -829,7 +859,7 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
                 aa.push_back({q.td_off[w], q.ctd[q.c->bfs[t]], q.td_list[w], q.alive[w], has[j]});
                 ent.push_back(q.kept[w]);
             }
-            FAST_TRY(run_tiles(k_any_alive_b, aa, ent, s));
+            FAST_TRY(run_tiles(k_any_alive_b, aa, ent, kTileItems, 1, s));
         }
         // refine rule 2: per (query, non-tree neighbour w of u), which rows
         // have a neighbour in C(w) as it stands now
@@ -1097,7 +1127,7 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
                               (unsigned long long*)c->ssum[w], sumf[j], ovf[j]});
                 ent.push_back(c->t_entries[w]);
             }
-            FAST_TRY(run_tiles(k_child_sums_b, cd, ent, s));
+            FAST_TRY(run_tiles(k_child_sums_b, cd, ent, kWarpTileItems, 8, s));
         }
         {
             std::vector<ProdDesc> pd;
