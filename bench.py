@@ -24,7 +24,9 @@ value = embeddings enumerated per second over the step.  Beside it:
     edges, 32 Zipf labels, a stream of 10,000 queries of 4-32 vertices --
     as Poisson arrivals into the request loop (continuous batching) at 0.25,
     0.5, 1, 2 and 4 times the per-query rate measured on the same stream,
-    with p50/p99 latency from arrival to result;
+    with p50/p99 latency from arrival to result, and at up to 1x the
+    per-query path under the same arrivals (one request at a time, first come
+    first served) beside it;
   - cpu_baseline: the oracle's search on the host cores, on a fixed sample
     of the same workload (one rule for it and for --impl reference).
 
@@ -492,8 +494,28 @@ def serve_leg(F, torch, args):
         m = int(min(max(50, rate * args.serve_seconds), 2000))
         stream_q = [qs[(pos + i) % len(qs)] for i in range(m)]
         pos += m
-        srv = F.Server(g, budget_bytes=120 << 30, cfg=scfg, workers=4)
         gaps = srng.exponential(1.0 / rate, size=m)
+        fifo = None
+        if f <= 1.0:
+            # the per-query path under the same arrivals: one request at a
+            # time, first come first served, each built, partitioned and
+            # matched on its own
+            fl = []
+            tf = time.perf_counter()
+            arr = 0.0
+            for (ql, qe), gap in zip(stream_q, gaps):
+                arr += gap
+                dt = arr - (time.perf_counter() - tf)
+                if dt > 0:
+                    time.sleep(dt)
+                cst = F.Cst(g, ql, qe, cfg)
+                ch = F.Chunks(cst, cfg)
+                F.match(cst, ch, cfg=cfg, check=False)
+                ch.close()
+                cst.close()
+                fl.append(1000 * (time.perf_counter() - tf - arr))
+            fifo = {"p50_ms": pct(fl, 0.5), "p99_ms": pct(fl, 0.99), "queries_per_sec": m / (time.perf_counter() - tf)}
+        srv = F.Server(g, budget_bytes=120 << 30, cfg=scfg, workers=4)
         done = []
         ts = time.perf_counter()
         nxt = 0.0
@@ -514,7 +536,8 @@ def serve_leg(F, torch, args):
                     "embeddings_per_sec": sum(r["count"] for r in done) / span,
                     "p50_ms": pct(lat_s, 0.5), "p99_ms": pct(lat_s, 0.99),
                     "mean_group": grouped / max(groups, 1),
-                    "failed": sum(1 for r in done if r["status"] not in (0, 3))})
+                    "failed": sum(1 for r in done if r["status"] not in (0, 3)),
+                    "per_query_fifo": fifo})
     g.close()
     return {"workload": (f"RMAT a=.57 b=c=.19 scale 23 (n=8,388,608, m=134,217,728), 32 Zipf(1.0) labels "
                          f"(seed {SERVE_SEED}); a stream of {len(qs)} random-walk queries of "

@@ -566,6 +566,15 @@ uint64_t fast_last_match_floor_bytes(void);
 /* Kernels launched by the library since the process started (all threads). */
 uint64_t fast_kernel_launches(void);
 
+/* Host round trips (device-to-host size reads the host waited for) of the
+ * calling thread's last batched CST build (fast_build_cst_batch, or a batch
+ * run with build_rule 2).  A batch of at most 8 queries whose bounded
+ * top-down arrays fit in 2 GB builds its top-down pass with none: its
+ * arrays are sized by host-known bounds (|C0| of the parent, the graph's
+ * count of adjacency entries between the two labels) and the kernels read
+ * the real sizes on the device. */
+uint64_t fast_last_build_round_trips(void);
+
 #ifdef __cplusplus
 }
 #endif

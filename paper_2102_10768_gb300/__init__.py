@@ -106,6 +106,7 @@ _SIGS = {
     "fast_last_match_ms": (ctypes.c_double, []),
     "fast_last_match_bytes": (ctypes.c_uint64, []),
     "fast_kernel_launches": (ctypes.c_uint64, []),
+    "fast_last_build_round_trips": (ctypes.c_uint64, []),
 }
 
 
@@ -615,3 +616,9 @@ def last_match_floor_bytes() -> int:
 def kernel_launches() -> int:
     """Kernels the library has launched in this process."""
     return int(lib().fast_kernel_launches())
+
+
+def last_build_round_trips() -> int:
+    """Host round trips of this thread's last batched CST build
+    (fast_last_build_round_trips)."""
+    return int(lib().fast_last_build_round_trips())

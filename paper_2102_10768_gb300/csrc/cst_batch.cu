@@ -94,7 +94,8 @@ __global__ void k_filter_b(const FilterDesc* __restrict__ D, const int32_t* __re
 // lengths leaves the edge-space size in len[n].
 struct CandSegDesc {
     const int32_t* cand;
-    int64_t n;
+    int64_t n;                       // rows (a bound when n_dev is set)
+    const int64_t* n_dev;            // device, nullable: the real rows
     int32_t l;
     int64_t* beg;
     int64_t* len;
@@ -104,7 +105,8 @@ __global__ void k_cand_segment_b(const CandSegDesc* __restrict__ D, const int64_
                                  GraphRuns G) {
     for_items(item_off, nseg, [&](int s, int64_t i) {
         const CandSegDesc& d = D[s];
-        if (i < d.n) label_segment(G, d.cand[i], d.l, d.beg + i, d.len + i);
+        const int64_t n = d.n_dev ? *d.n_dev : d.n;
+        if (i < n) label_segment(G, d.cand[i], d.l, d.beg + i, d.len + i);
         else d.len[i] = 0;
     });
 }
@@ -134,9 +136,6 @@ struct AnyAliveDesc {
     uint8_t* has;
 };
 
-// A tile of a tile-split kernel: its segment, its entry range [tb, te) and
-// the rows of its first and last entries (every entry's row lies between),
-// found once per tile by warp 0.
 // A warp's tile t of a tile-split batched step: its segment, its entries
 // [tb, te) and the rows r0, r1 of its first and last entries, found by the
 // 32 lanes together (every lane returns them).
@@ -502,6 +501,11 @@ enum : int {
     F_END = F_WF + 1
 };
 
+// Batches of at most this many queries, whose bounded top-down arrays fit
+// in kBoundedBytes, build the top-down pass without host round trips.
+constexpr int kBoundedQueries = 8;
+constexpr uint64_t kBoundedBytes = 2ull << 30;
+
 // One query of the batch.
 struct Q {
     int idx = 0;                  // in the caller's arrays
@@ -535,7 +539,10 @@ void order_and_nontree(const Q& q, fast_cst* c) {
     c->nnt = nontree_edges(q.k, q.A, c->order, c->parent, c->nt_from, c->nt_to);
 }
 
+thread_local uint64_t t_round_trips = 0;   // this thread's last batched build
+
 int fetch(const int64_t* d, std::vector<int64_t>& h, size_t words, cudaStream_t s) {
+    t_round_trips++;
     h.assign(words, 0);
     if (!words) return FAST_OK;
     cudaError_t e = cudaMemcpyAsync(h.data(), d, words * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -695,21 +702,45 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
     }
 
     // ----------------------------------------------------- top-down
+    //
+    // A small batch enqueues the whole pass with no host round trip: each
+    // level's arrays are sized by bounds the host knows -- the rows by
+    // |C0(parent)|, the edge space by the graph's count of adjacency entries
+    // from label l(parent) to label l(u) -- and the kernels read the real
+    // sizes on the device (rows from the previous level's count, the edge
+    // space's end from its offsets).  Otherwise, or when the bounds would
+    // take too much memory, each level fetches its exact sizes first.
+    bool bounded = false;
+    if (!g->lab_pair_host.empty() && nq <= kBoundedQueries) {
+        const int L = g->num_labels;
+        uint64_t bytes = 0;
+        for (auto& q : Qs)
+            for (int t = 1; t < q.k; t++) {
+                const int u = q.c->bfs[t], p = q.c->parent[u];
+                const int32_t lp = q.c->qlabel[p], lu = q.c->qlabel[u];
+                const int64_t e = (lp < L && lu < L) ? g->lab_pair_host[(size_t)lp * L + lu] : 0;
+                bytes += 4ull * (uint64_t)e + 24ull * (uint64_t)(q.c0[p] + 1);
+            }
+        bounded = bytes <= kBoundedBytes;
+    }
+    auto rows_of = [&](const Q& q, int p) { return bounded ? q.c0[p] : q.ctd[p]; };
     std::vector<unsigned char*> alive_blk(kMaxK, nullptr);
     std::vector<size_t> alive_bytes(kMaxK, 0);
     std::vector<int> act;
     for (int t = 1; t < K; t++) {
         act.clear();
         for (int qi = 0; qi < nq; qi++) if (Qs[qi].k > t) act.push_back(qi);
-        FAST_TRY(fetch(zp(F_TD + t - 1, 0), h, (size_t)nq, s));
-        for (int qi = 0; qi < nq; qi++)
-            if (Qs[qi].k > t - 1) Qs[qi].ctd[Qs[qi].c->bfs[t - 1]] = h[qi];
+        if (!bounded) {
+            FAST_TRY(fetch(zp(F_TD + t - 1, 0), h, (size_t)nq, s));
+            for (int qi = 0; qi < nq; qi++)
+                if (Qs[qi].k > t - 1) Qs[qi].ctd[Qs[qi].c->bfs[t - 1]] = h[qi];
+        }
         Scratch lvl(s);
         {
             Carver cv;
             for (int qi : act) {
                 Q& q = Qs[qi];
-                const int64_t rows = q.ctd[q.c->parent[q.c->bfs[t]]];
+                const int64_t rows = rows_of(q, q.c->parent[q.c->bfs[t]]);
                 cv.add(&q.e_off, rows + 1);
                 cv.add(&q.seg, rows);
             }
@@ -721,27 +752,30 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
             for (int qi : act) {
                 Q& q = Qs[qi];
                 const int u = q.c->bfs[t], p = q.c->parent[u];
-                const int64_t rows = q.ctd[p];
-                cd.push_back({q.td_cand[p], rows, q.c->qlabel[u], q.seg, q.e_off});
+                const int64_t rows = rows_of(q, p);
+                cd.push_back({q.td_cand[p], rows, bounded ? zp(F_TD + q.bpos[p], qi) : nullptr, q.c->qlabel[u], q.seg,
+                              q.e_off});
                 ni.push_back(rows + 1);
             }
             FAST_TRY(run_items(k_cand_segment_b, cd, ni, s, G));
             std::vector<ScanSeg<int64_t>> sc;
             for (int qi : act) {
                 Q& q = Qs[qi];
-                const int64_t rows = q.ctd[q.c->parent[q.c->bfs[t]]];
+                const int64_t rows = rows_of(q, q.c->parent[q.c->bfs[t]]);
                 sc.push_back({q.e_off, nullptr, q.e_off, rows + 1, zp(F_E + t, qi)});
             }
             FAST_TRY(scan_seg(sc, s));
         }
-        FAST_TRY(fetch(zp(F_E + t, 0), h, (size_t)nq, s));
+        if (!bounded) FAST_TRY(fetch(zp(F_E + t, 0), h, (size_t)nq, s));
         {
             Carver cl, cb;
             for (int qi : act) {
                 Q& q = Qs[qi];
-                const int u = q.c->bfs[t];
-                const int64_t rows = q.ctd[q.c->parent[u]];
-                q.E[u] = h[qi];
+                const int u = q.c->bfs[t], p = q.c->parent[u];
+                const int64_t rows = rows_of(q, p);
+                const int L = g->num_labels;
+                const int32_t lp = q.c->qlabel[p], lu = q.c->qlabel[u];
+                q.E[u] = !bounded ? h[qi] : (lp < L && lu < L) ? g->lab_pair_host[(size_t)lp * L + lu] : 0;
                 cl.add(&q.td_list[u], q.E[u]);
                 cl.add(&q.td_off[u], rows + 1);
                 cb.add(&q.alive[u], nw);
@@ -756,7 +790,7 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
             for (int qi : act) {
                 Q& q = Qs[qi];
                 const int u = q.c->bfs[t];
-                const int64_t rows = q.ctd[q.c->parent[u]];
+                const int64_t rows = rows_of(q, q.c->parent[u]);
                 TopDownF f{};
                 f.e_off = q.e_off; f.rows = rows; f.seg = q.seg; f.col = g->col; f.key = g->key;
                 f.want_key_hi = q.c->qlabel[u]; f.want_dq = q.dq[u]; f.reached = q.alive[u]; f.t_off = q.td_off[u];
@@ -1047,7 +1081,7 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
             for (size_t j = 0; j < nnp; j++) {
                 const fast_cst* c = Qs[ntq[j]].c;
                 const int e = nte[j];
-                cd.push_back({c->cand[c->nt_from[e]], rows[j], c->qlabel[c->nt_to[e]], sg[j], eo[j]});
+                cd.push_back({c->cand[c->nt_from[e]], rows[j], nullptr, c->qlabel[c->nt_to[e]], sg[j], eo[j]});
                 ni.push_back(rows[j] + 1);
                 sc.push_back({eo[j], nullptr, eo[j], rows[j] + 1, NZ + j});
             }
@@ -1196,6 +1230,7 @@ namespace fast {
 
 int build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, const fast_config* const* cfgs,
                     cudaStream_t s, fast_cst** outs, int32_t* status) {
+    t_round_trips = 0;
     for (int i = 0; i < nq; i++) outs[i] = nullptr;
     // Ranges of queries built together: groups of kGroup; a range whose
     // build runs out of device memory (its bound-sized buffers did not fit)
@@ -1266,6 +1301,8 @@ int build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, 
 }
 
 }  // namespace fast
+
+extern "C" uint64_t fast_last_build_round_trips(void) { return t_round_trips; }
 
 extern "C" int fast_build_cst_batch(const fast_graph* g, int32_t nq, const fast_query_desc* qs, const fast_config* cfg,
                                     void* stream, fast_cst** outs, int32_t* status) {

@@ -206,6 +206,55 @@ __global__ void k_row_runs(const int64_t* __restrict__ row_ptr, const int32_t* _
     }
 }
 
+// Adjacency entries per (label of the row's vertex, label of the
+// neighbour), M[a * L + b], from the label runs; counted in shared memory
+// when the L x L table fits there.
+constexpr int kPairSmem = 4096;
+
+__global__ void k_label_pairs(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ run_ptr,
+                              const int32_t* __restrict__ run_lab, const int64_t* __restrict__ run_beg,
+                              const int32_t* __restrict__ label, int64_t n, int L, unsigned long long* __restrict__ M) {
+    extern __shared__ unsigned long long pair_sm[];
+    const bool local = L * L <= kPairSmem;
+    if (local)
+        for (int i = threadIdx.x; i < L * L; i += blockDim.x) pair_sm[i] = 0;
+    __syncthreads();
+    unsigned long long* dst = local ? pair_sm : M;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = label[v];
+        const int64_t r1 = run_ptr[v + 1], end = row_ptr[v + 1];
+        for (int64_t r = run_ptr[v]; r < r1; r++) {
+            const int64_t len = (r + 1 < r1 ? run_beg[r + 1] : end) - run_beg[r];
+            atomicAdd(dst + a * L + run_lab[r], (unsigned long long)len);
+        }
+    }
+    __syncthreads();
+    if (local)
+        for (int i = threadIdx.x; i < L * L; i += blockDim.x)
+            if (pair_sm[i]) atomicAdd(M + i, pair_sm[i]);
+}
+
+int label_pair_counts(fast_graph* g, cudaStream_t s) {
+    const int L = g->num_labels;
+    if (!g->grouped || L <= 0 || L > kLabelPairMax) return FAST_OK;
+    unsigned long long* M = nullptr;
+    FAST_TRY(dalloc(&M, (int64_t)L * L, s));
+    cudaMemsetAsync(M, 0, (size_t)L * L * sizeof(unsigned long long), s);
+    const bool local = L * L <= kPairSmem;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->n, 256), (int64_t)num_sms() * 4));
+    k_label_pairs<<<blocks, 256, local ? (size_t)L * L * sizeof(unsigned long long) : 0, s>>>(
+        g->row_ptr, g->run_ptr, g->run_lab, g->run_beg, g->label, g->n, L, M);
+    note_launch();
+    std::vector<int64_t> h((size_t)L * L);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), M, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(M, s);
+    if (e != cudaSuccess) return cuda_status(e, "label pair counts", __FILE__, __LINE__);
+    g->lab_pair_host.swap(h);
+    return FAST_OK;
+}
+
 int build_label_runs(fast_graph* g, cudaStream_t s) {
     const int64_t n = g->n;
     int64_t* cnt = nullptr;
@@ -341,6 +390,7 @@ int load_graph(int64_t n, int64_t m, const int32_t* edges, const int32_t* labels
             dfree(ds, s);
             if (e != cudaSuccess) { rc = cuda_status(e, "label degree sums", __FILE__, __LINE__); break; }
         }
+        rc = label_pair_counts(g, s); if (rc) break;
         g->lab_ptr_host.resize(g->num_labels + 1);
         unsigned long long md = 0;
         if (cudaMemcpyAsync(g->lab_ptr_host.data(), g->lab_ptr, (g->num_labels + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -11,6 +11,8 @@ constexpr int kMaxK = FAST_MAX_QUERY;
 constexpr int kMaxNT = kMaxK * (kMaxK - 1) / 2;
 
 // Data graph G (Sec. II-A) on the device.
+constexpr int kLabelPairMax = 1024;
+
 struct fast_graph {
     int64_t n = 0;
     int64_t nadj = 0;          // stored adjacency entries (2|E|)
@@ -24,6 +26,10 @@ struct fast_graph {
     int32_t* lab_vtx = nullptr;   // [n] vertices grouped by label, ascending id
     std::vector<int64_t> lab_ptr_host;
     std::vector<int64_t> lab_degsum_host;   // per label: sum of degrees (bounds CST list sizes)
+    // adjacency entries per (label of the row's vertex a, label of the
+    // neighbour b) at [a * num_labels + b], when the rows are grouped by label
+    // and num_labels <= kLabelPairMax (else empty): bounds a top-down list
+    std::vector<int64_t> lab_pair_host;
     // Label runs: when `grouped`, each row of col is sorted by (label of the
     // neighbour, id), and row v's runs are run_ptr[v] .. run_ptr[v+1]-1: run
     // r holds the neighbours with label run_lab[r], from col position

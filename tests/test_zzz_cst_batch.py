@@ -96,6 +96,35 @@ def test_batch_er_workload(rule):
     check_batch(g, o, qs, RULES[rule])
 
 
+@pytest.mark.parametrize("rule", range(len(RULES)))
+@pytest.mark.parametrize("seed", range(4))
+def test_small_batches_build_without_round_trips(seed, rule):
+    """Batches of up to 8 queries build their top-down pass with no host
+    round trip (arrays sized by host-known bounds, real sizes read on the
+    device): the CSTs equal the oracle's, and the build waits on the host at
+    most six times whatever the query size; a batch of nine fetches every
+    level's sizes and gives the same CSTs."""
+    rng, n, e, lab, L = rand_graph(7100 + seed)
+    g, o = F.Graph(n, e, lab), oracle.Graph(n, e, lab)
+    qs = [rand_query(rng, L, int(rng.integers(2, 8))) for _ in range(9)]
+    for size in (1, 3, 8):
+        check_batch(g, o, qs[:size], RULES[rule])
+        csts, status = F.build_csts(g, qs[:size], F.default_config(**RULES[rule]))
+        assert F.last_build_round_trips() <= 6, size
+        for c in csts:
+            c.close()
+    cfg = F.default_config(**RULES[rule])
+    csts, status = F.build_csts(g, qs, cfg)
+    kmax = max(len(ql) for ql, _ in qs)
+    assert F.last_build_round_trips() >= 2 * (kmax - 1)
+    small, _ = F.build_csts(g, qs[:8], cfg)
+    for a, b in zip(small, csts[:8]):
+        _same_cst(a, b)
+        a.close()
+    for c in csts:
+        c.close()
+
+
 def _same_cst(a, b):
     """Two CSTs of the same query from the library: equal arrays (W's
     float64 twin within rounding, its sums being atomics)."""
@@ -133,6 +162,32 @@ def test_batch_powerlaw_equals_per_query():
             _same_cst(c, one)
             lim = F.default_config(limit=1 << 16, **rule)
             assert F.match(c, cfg=lim)["count"] == F.match(one, cfg=lim)["count"]
+            one.close()
+            c.close()
+
+
+def test_small_batches_powerlaw_equal_per_query():
+    """The bounded top-down pass on a power-law graph with hubs, batches of
+    one to eight queries of up to 16 vertices: every CST equals the one the
+    per-query build gives."""
+    n, e, lab = synth.powerlaw_graph(seed=2000, n=50_000, m=600_000)
+    g = F.Graph(n, e, lab)
+    wg = synth.WalkGraph(n, e)
+    qs = []
+    for k in (4, 8, 12, 16):
+        for r in range(3):
+            kind = ("induced", "sparse", "induced" if k == 4 else "dense")[r]
+            q = wg.query(lab, k, kind, seed=78, stream=10 * k + r)
+            qs.append((q.labels, q.edges))
+    wg.close()
+    cfg = F.default_config(filter_rule=1, order_rule=1)
+    for lo, hi in ((0, 1), (1, 4), (4, 12)):
+        csts, status = F.build_csts(g, qs[lo:hi], cfg)
+        assert status.tolist() == [0] * (hi - lo)
+        assert F.last_build_round_trips() <= 6
+        for (ql, qe), c in zip(qs[lo:hi], csts):
+            one = F.Cst(g, ql, qe, cfg)
+            _same_cst(c, one)
             one.close()
             c.close()
 
