@@ -15,6 +15,7 @@
 // from those round trips and carved from a few scratch blocks per step.
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "cst_funcs.cuh"
@@ -180,7 +181,10 @@ __device__ __forceinline__ bool tile_rows(const D* __restrict__ Dd, const int64_
         const int64_t tb = (t - tile_off[s]) * kTileItems;
         const int64_t te = tb + kTileItems < e_end ? tb + kTileItems : e_end;
         int64_t r0 = 0, r1 = 0;
-        if (tb < te) warp_rows_of(d.off, d.rows, tb, te - 1, &r0, &r1);
+        if (tb < te) {                  // one search after the other: 32 registers, 8 blocks per SM
+            r0 = warp_row_of(d.off, d.rows, tb);
+            r1 = warp_row_of(d.off, d.rows, te - 1);
+        }
         if (threadIdx.x == 0) { sh->s = s; sh->tb = tb; sh->te = te; sh->r0 = r0; sh->r1 = r1; }
     }
     __syncthreads();
@@ -624,28 +628,30 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
     auto zp = [&](int f, int qi) { return Z + (int64_t)f * nq + qi; };
 
     // ------------------------------------------------------------ filter
+    //
+    // Pairs with the same label, query degree and (label-frequency rule)
+    // requirement have the same C0: one of them is filtered, the others
+    // share its bitmap and take its count.
+    std::vector<std::pair<int, int>> alias((size_t)kMaxK * nq, {-1, -1});   // [u * nq + qi] -> its pair
     {
+        std::vector<FilterDesc> fd;
+        std::vector<std::pair<int, int>> rep;             // fd[i]'s (query, vertex)
+        std::map<std::vector<int64_t>, int> seen;
         Carver cv;
         int64_t maxb = 1;
-        for (auto& q : Qs)
+        for (int qi = 0; qi < nq; qi++) {
+            Q& q = Qs[qi];
             for (int u = 0; u < q.k; u++) {
                 const int32_t l = q.c->qlabel[u];
                 if (l < g->num_labels) { q.lo[u] = g->lab_ptr_host[l]; q.hi[u] = g->lab_ptr_host[l + 1]; }
                 else { q.lo[u] = q.hi[u] = 0; }
-                maxb = std::max<int64_t>(maxb, q.hi[u] - q.lo[u]);
-                if (q.nlf) cv.add(&q.nlfb[u], nw);
-            }
-        FAST_TRY(cv.alloc(keep, true));
-        std::vector<FilterDesc> fd;
-        for (int qi = 0; qi < nq; qi++) {
-            const Q& q = Qs[qi];
-            for (int u = 0; u < q.k; u++) {
                 FilterDesc d;
                 memset(&d, 0, sizeof(d));
                 d.lo = q.lo[u];
                 d.hi = q.hi[u];
                 d.dq = q.dq[u];
                 d.nlf = q.nlf ? 1 : 0;
+                std::vector<int64_t> key{d.lo, d.hi, d.dq, d.nlf};
                 if (q.nlf) {
                     for (int w = 0; w < q.k; w++) {
                         if (!q.A[u][w]) continue;
@@ -655,12 +661,37 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
                         if (t == d.r.nn) { d.r.lab[t] = lw; d.r.need[t] = 0; d.r.nn++; }
                         d.r.need[t]++;
                     }
-                    d.bits = q.nlfb[u];
+                    // in label order, so that equal requirements give equal keys
+                    for (int a = 1; a < d.r.nn; a++)
+                        for (int b = a; b > 0 && d.r.lab[b - 1] > d.r.lab[b]; b--) {
+                            std::swap(d.r.lab[b - 1], d.r.lab[b]);
+                            std::swap(d.r.need[b - 1], d.r.need[b]);
+                        }
+                    for (int t = 0; t < d.r.nn; t++) { key.push_back(d.r.lab[t]); key.push_back(d.r.need[t]); }
                 }
-                d.cnt = (unsigned long long*)zp(F_CNT + u, qi);
+                auto it = seen.find(key);
+                if (it != seen.end()) {
+                    alias[(size_t)u * nq + qi] = rep[it->second];
+                    continue;
+                }
+                seen.emplace(std::move(key), (int)fd.size());
+                rep.push_back({qi, u});
                 fd.push_back(d);
+                maxb = std::max<int64_t>(maxb, q.hi[u] - q.lo[u]);
+                if (q.nlf) cv.add(&q.nlfb[u], nw);
             }
         }
+        FAST_TRY(cv.alloc(keep, true));
+        for (size_t i = 0; i < fd.size(); i++) {
+            const Q& q = Qs[rep[i].first];
+            if (q.nlf) fd[i].bits = q.nlfb[rep[i].second];
+            fd[i].cnt = (unsigned long long*)zp(F_CNT + rep[i].second, rep[i].first);
+        }
+        for (int qi = 0; qi < nq; qi++)
+            for (int u = 0; u < Qs[qi].k; u++) {
+                const auto a = alias[(size_t)u * nq + qi];
+                if (a.first >= 0 && Qs[qi].nlf) Qs[qi].nlfb[u] = Qs[a.first].nlfb[a.second];
+            }
         Scratch sc(s);
         const FilterDesc* dd = nullptr;
         const int64_t* unused = nullptr;
@@ -673,6 +704,11 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
         if (cudaGetLastError() != cudaSuccess) return set_error(FAST_ERR_CUDA, "batched filter launch");
     }
     FAST_TRY(fetch(zp(F_CNT, 0), h, (size_t)kMaxK * nq, s));
+    for (int qi = 0; qi < nq; qi++)
+        for (int u = 0; u < Qs[qi].k; u++) {
+            const auto a = alias[(size_t)u * nq + qi];
+            if (a.first >= 0) h[(size_t)u * nq + qi] = h[(size_t)a.second * nq + a.first];
+        }
 
     // ------------------------------------------------- root and t_q
     for (int qi = 0; qi < nq; qi++) {
