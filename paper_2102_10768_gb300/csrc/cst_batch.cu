@@ -865,6 +865,10 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
             const int u = q.c->bfs[t];
             q.ctd[u] = h[(size_t)t * nq + qi];
             q.kept[u] = h[(size_t)(2 * kMaxK + t) * nq + qi];
+            // a bounded pass read at most its bound of each edge space (the
+            // compaction stops there); more would mean a wrong bound
+            if (bounded && t > 0 && h[(size_t)(kMaxK + t) * nq + qi] > q.E[u])
+                return set_error(FAST_ERR_CUDA, "batched CST build: an edge space exceeded its label-pair bound");
         }
     }
 
