@@ -508,9 +508,9 @@ uint64_t fast_now_ns(void);
  * bytes (about 5.9 MB: the counter block, a ring of 4096 donated runs and
  * up to 32768 root-run descriptors) that every GPU loading the library keeps
  * until the process exits.  The first call on a device looks up its address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the array and leave the last
- * call's contents in it; each call clears what must start at zero.  Calls
+ * (cudaGetSymbolAddress, with that device current).  All calls share the
+ * array and leave the last call's contents in it; each call clears what
+ * must start at zero.  Calls
  * whose work overlaps on the GPU (other streams, other host threads) race on
  * the shared array and must be serialised by the caller.
  *
