@@ -18,6 +18,9 @@ value = embeddings enumerated per second over the step.  Beside it:
   - e2e: the same call from host query arrays to host counts, host clock;
   - complete_queries: the queries whose total is below the limit, enumerated
     in full (no limit) as one batch;
+  - full_enumeration: queries of the same graph and sizes whose workload
+    estimate W (an upper bound of their counts) is small, enumerated in full
+    with no limit as one batched step;
   - per_query: the same 1,000 queries one at a time (fast_build_cst +
     fast_partition + fast_match_ex each), with latency p50/p99;
   - served: the serving workload -- RMAT (a=.57, b=c=.19) scale 23, 134M
@@ -390,6 +393,62 @@ def run_batch_steps(F, torch, bt, bq, stream, flush, steps):
     return tot
 
 
+FULL_SEED = 3500
+FULL_SIZES = (4, 8)                  # larger queries' W saturates on this graph
+FULL_POOL = 2000                     # candidate queries, 1000 of each size
+FULL_W_MAX = 1 << 33                 # W of a chosen query at most (W bounds its count)
+FULL_W_SUM = 1 << 36                 # and the chosen queries' W together
+
+
+def full_enumeration_leg(F, torch, g, n, e, lab, cfg, stream, flush, threads):
+    """Full enumeration, the paper's own task (no limit): random-walk queries
+    of 4 and 8 vertices on the headline graph whose CST workload estimate W
+    -- an upper bound of the embedding count (Sec. IV-C counts every
+    combination along the tree edges) -- is at most 2^33, taken in
+    increasing W while their W sum to at most 2^36 (so the step stays within
+    seconds), then enumerated in full as one batched step.  On this graph the
+    W of larger queries saturates 2^64."""
+    import synth
+    wg = synth.WalkGraph(n, e)
+    pool = synth.mixed_queries(wg, lab, FULL_SIZES, FULL_POOL // len(FULL_SIZES), FULL_SEED)
+    wg.close()
+    ccfg = F.Config.from_buffer_copy(cfg)
+    ccfg.limit = 0
+    csts, status = F.build_csts(g, pool, ccfg)
+    ws = []
+    for i, (c, st) in enumerate(zip(csts, status)):
+        if c is not None:
+            if st == F.FAST_OK:
+                ws.append((int(c.W), i))
+            c.close()
+    ws.sort()
+    chosen, wsum = [], 0
+    for w, i in ws:
+        if w > FULL_W_MAX or wsum + w > FULL_W_SUM or len(chosen) >= 1000:
+            break
+        chosen.append(i)
+        wsum += w
+    qs = [pool[i] for i in chosen]
+    if not qs:
+        return {"queries": 0}
+    b = F.Batch(g, len(qs), ccfg, threads=threads)
+    try:
+        b.run(qs, stream=stream.cuda_stream)
+        t = run_batch_steps(F, torch, b, qs, stream, flush, 1)
+    finally:
+        b.close()
+    counts = [int(x) for x in t["counts"]]
+    return {"value": t["emb"] / (t["ms"] / 1000.0), "unit": UNIT,
+            "queries": len(qs), "queries_per_sec": len(qs) / (t["ms"] / 1000.0),
+            "sizes": {str(k): sum(1 for ql, _ in qs if len(ql) == k) for k in FULL_SIZES},
+            "embeddings_per_step": t["emb"], "max_count": max(counts), "w_sum": wsum,
+            "ms_per_step": t["ms"], "build_ms_per_step": t["build_ms"], "match_ms_per_step": t["match_ms"],
+            "queries_cut_by_budget": t["cut"],
+            "selection": (f"{FULL_POOL} random-walk queries of 4 and 8 vertices (seed {FULL_SEED}), those with "
+                          f"W <= 2^33 in increasing W while the W sum <= 2^36"),
+            "counts_sha1": hashlib.sha1(json.dumps(counts).encode()).hexdigest()}
+
+
 def batch_leg(F, torch, g, bq, cfg, stream, flush, steps, threads, **over):
     """A batched step with other settings: throughput and phase split."""
     c2 = F.Config.from_buffer_copy(cfg)
@@ -655,6 +714,7 @@ def run_ours(args):
 
     legs = {}
     if args.legs and world == 1:
+        legs["full_enumeration"] = full_enumeration_leg(F, torch, g, n, e, lab, bcfg, stream, flush, args.threads)
         # the other matching orders (the paper's path-based one among them)
         # and the other build rules, on the same step
         for name, rule in ORDERS.items():

@@ -72,6 +72,32 @@ def test_batched_1000_mixed_queries(powerlaw_1m):
         assert s0.tolist() == status.tolist() and c0.tolist() == counts.tolist(), extra
 
 
+def test_full_enumeration_without_limit(powerlaw_1m):
+    """Full enumeration (no limit) on the power-law graph: the four
+    4-vertex queries of a 200-query pool with the smallest CST workload
+    estimate W (an upper bound of each count, Sec. IV-C), enumerated in one
+    batched launch; every count equals the oracle's complete search and is
+    at most W (tens of millions of embeddings each)."""
+    n, e, lab, g, o, wg = powerlaw_1m
+    pool = draw(wg, lab, (4,), 200, 3500)
+    cfg = F.default_config(order_rule=1, filter_rule=1, time_budget_s=60.0)
+    csts, status = F.build_csts(g, pool, cfg)
+    ws = []
+    for i, (c, st) in enumerate(zip(csts, status)):
+        if c is not None:
+            if st == 0:
+                ws.append((int(c.W), i))
+            c.close()
+    ws.sort()
+    chosen = ws[:4]
+    qs = [pool[i] for _, i in chosen]
+    counts, st = F.Batch(g, len(qs), cfg).run(qs)
+    assert st.tolist() == [0] * len(qs)
+    for (w, _), (ql, qe), c in zip(chosen, qs, counts.tolist()):
+        r = oracle.match(o, ql, qe, budget=10 ** 10)
+        assert r["complete"] and c == r["count"] and 0 < c <= w
+
+
 @pytest.fixture(scope="module")
 def rmat23():
     F.build()
