@@ -18,6 +18,10 @@ value = embeddings enumerated per second over the step.  Beside it:
   - e2e: the same call from host query arrays to host counts, host clock;
   - complete_queries: the queries whose total is below the limit, enumerated
     in full (no limit) as one batch;
+  - the step is autotuned first (fast_batch_autotune on a separate sample
+    of 10 queries per size: delta_w and max_chunks per size class, then the
+    launch shape); default_config: the same step with the defaults (with
+    --no-autotune the other way round, as autotuned);
   - full_enumeration: queries of the same graph and sizes whose workload
     estimate W (an upper bound of their counts) is small, enumerated in full
     with no limit as one batched step;
@@ -84,9 +88,9 @@ def parse(argv=None):
     p.add_argument("--serve-queries", type=int, default=10_000, help="queries in the serving stream")
     p.add_argument("--serve-limit", type=int, default=1 << 16, help="embeddings per served query")
     p.add_argument("--serve-seconds", type=float, default=6.0, help="arrival time per offered rate (at most)")
-    p.add_argument("--autotune", action="store_true",
-                   help="before timing, autotune the batch (delta_w, max_chunks, launch shape per size class) "
-                        "on a separate sample of queries (seed + 1)")
+    p.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="time the default configuration instead of autotuning the batch first (delta_w, "
+                        "max_chunks per size class, then the launch shape, on a separate sample: seed + 1)")
     p.add_argument("--filter", choices=["ldf", "nlf"], default="nlf",
                    help="candidate filter: label frequencies (nlf, default) or label and degree only (ldf)")
     p.add_argument("--order", choices=list(ORDERS), default="greedy",
@@ -449,12 +453,29 @@ def full_enumeration_leg(F, torch, g, n, e, lab, cfg, stream, flush, threads):
             "counts_sha1": hashlib.sha1(json.dumps(counts).encode()).hexdigest()}
 
 
-def batch_leg(F, torch, g, bq, cfg, stream, flush, steps, threads, **over):
-    """A batched step with other settings: throughput and phase split."""
+TUNED_FIELDS = ("delta_w", "max_chunks", "warps_per_block", "blocks_per_sm")
+
+
+def apply_tuned(F, bt, base, tuned):
+    """Give every size class of batch bt the configuration `base` with the
+    autotuner's picks for that class (tuned: {size: {field: value}})."""
+    for k in SIZES:
+        c = F.Config.from_buffer_copy(base)
+        for f in TUNED_FIELDS:
+            setattr(c, f, tuned[str(k)][f])
+        bt.config(k, c)
+
+
+def batch_leg(F, torch, g, bq, cfg, stream, flush, steps, threads, tuned=None, **over):
+    """A batched step with other settings: throughput and phase split.  With
+    `tuned`, the autotuner's picks of the headline step apply as well, so
+    that the leg differs from it only in `over`."""
     c2 = F.Config.from_buffer_copy(cfg)
     for k, v in over.items():
         setattr(c2, k, v)
     bt = F.Batch(g, len(bq), c2, threads=threads)
+    if tuned:
+        apply_tuned(F, bt, c2, tuned)
     try:
         bt.run(bq, stream=stream.cuda_stream)
         l0 = F.kernel_launches()
@@ -466,6 +487,32 @@ def batch_leg(F, torch, g, bq, cfg, stream, flush, steps, threads, **over):
             "build_ms_per_step": t["build_ms"] / steps, "match_ms_per_step": t["match_ms"] / steps,
             "gpu_launches_per_step": launches / steps, "queries_cut_by_budget_per_step": t["cut"] / steps,
             "matcher_budget_s": c2.time_budget_s,
+            "counts_sha1": hashlib.sha1(t["counts"].astype("int64").tobytes()).hexdigest()}
+
+
+def autotuned_leg(F, torch, g, n, e, lab, bq, cfg, stream, flush, steps, threads):
+    """The headline step after fast_batch_autotune on a separate sample (10
+    queries of each size, the next query seed): the tuner's picks (delta_w
+    and max_chunks per size class, then the launch shape), the time it took,
+    and the step with them -- to set against the default configuration."""
+    import synth
+    wg = synth.WalkGraph(n, e)
+    sample = synth.mixed_queries(wg, lab, SIZES, 10, query_seed(0) + 1)
+    wg.close()
+    bt = F.Batch(g, len(bq), cfg, threads=threads)
+    try:
+        t0 = time.perf_counter()
+        bt.autotune(sample, stream=stream.cuda_stream)
+        tune_s = time.perf_counter() - t0
+        picks = {str(k): {f: getattr(bt.config(k), f) for f in ("delta_w", "max_chunks", "warps_per_block",
+                                                                  "blocks_per_sm")} for k in SIZES}
+        bt.run(bq, stream=stream.cuda_stream)
+        t = run_batch_steps(F, torch, bt, bq, stream, flush, steps)
+    finally:
+        bt.close()
+    return {"value": t["emb"] / (t["ms"] / 1000.0), "unit": UNIT, "steps": steps, "ms_per_step": t["ms"] / steps,
+            "build_ms_per_step": t["build_ms"] / steps, "match_ms_per_step": t["match_ms"] / steps,
+            "tune_s": tune_s, "picks": picks,
             "counts_sha1": hashlib.sha1(t["counts"].astype("int64").tobytes()).hexdigest()}
 
 
@@ -647,9 +694,11 @@ def run_ours(args):
         wg = synth.WalkGraph(n, e)
         sample = synth.mixed_queries(wg, lab, SIZES, 10, query_seed(rank) + 1)
         wg.close()
+        t0 = time.perf_counter()
         bt.autotune(sample, stream=stream.cuda_stream)
-        tuned = {str(k): {f: getattr(bt.config(k), f) for f in ("delta_w", "max_chunks", "warps_per_block",
-                                                                 "blocks_per_sm")} for k in SIZES}
+        tuned = {str(k): {f: getattr(bt.config(k), f) for f in TUNED_FIELDS} for k in SIZES}
+        tuned["tune_s"] = time.perf_counter() - t0
+        tuned["sample"] = "10 queries of each size, query seed + 1 (not the timed queries)"
     run_batch_steps(F, torch, bt, bq, stream, flush, args.warmup)
     if dist:
         dist.barrier()
@@ -715,22 +764,27 @@ def run_ours(args):
     legs = {}
     if args.legs and world == 1:
         legs["full_enumeration"] = full_enumeration_leg(F, torch, g, n, e, lab, bcfg, stream, flush, args.threads)
+        if args.autotune:
+            legs["default_config"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads)
+        else:
+            legs["autotuned"] = autotuned_leg(F, torch, g, n, e, lab, bq, bcfg, stream, flush, 2, args.threads)
         # the other matching orders (the paper's path-based one among them)
-        # and the other build rules, on the same step
+        # and the other build rules, on the same step (with the tuner's picks)
         for name, rule in ORDERS.items():
             if name != args.order:
-                legs[f"{name}_order"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 1, args.threads,
+                legs[f"{name}_order"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 1, args.threads, tuned,
                                                   order_rule=rule, time_budget_s=10.0)
         for rule, name in ((0, "threads"), (1, "batched"), (2, "batched-all")):
             if name != args.build:
-                legs[f"build_{name}"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads,
+                legs[f"build_{name}"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads, tuned,
                                                   build_rule=rule)
         # refine rule 2 (the bottom-up pass with the non-tree neighbour test):
         # build time spent against matcher time saved
         if args.refine != "once_nt" and args.build != "threads":
-            legs["refine_once_nt"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads, refine_rule=2)
+            legs["refine_once_nt"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads, tuned,
+                                               refine_rule=2)
         # the warp-specialised matcher (expander and validator warps) on the same step
-        legs["matcher_ws"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads,
+        legs["matcher_ws"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads, tuned,
                                        matcher_rule=1, validators=1)
         legs["matcher_ws"]["validators_per_cta"] = 1
         per_query = per_query_leg(F, torch, g, qs, cfg, stream, flush)
