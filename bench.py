@@ -486,6 +486,7 @@ def batch_leg(F, torch, g, bq, cfg, stream, flush, steps, threads, tuned=None, *
     return {"value": t["emb"] / (t["ms"] / 1000.0), "unit": UNIT, "steps": steps, "ms_per_step": t["ms"] / steps,
             "build_ms_per_step": t["build_ms"] / steps, "match_ms_per_step": t["match_ms"] / steps,
             "gpu_launches_per_step": launches / steps, "queries_cut_by_budget_per_step": t["cut"] / steps,
+            "matcher_floor_gbs": t["floor"] / (t["match_ms"] / 1000.0) / 1e9 if t["match_ms"] else None,
             "matcher_budget_s": c2.time_budget_s,
             "counts_sha1": hashlib.sha1(t["counts"].astype("int64").tobytes()).hexdigest()}
 
@@ -622,6 +623,14 @@ def serve_leg(F, torch, args):
                 fl.append(1000 * (time.perf_counter() - tf - arr))
             fifo = {"p50_ms": pct(fl, 0.5), "p99_ms": pct(fl, 0.99), "queries_per_sec": m / (time.perf_counter() - tf)}
         srv = F.Server(g, budget_bytes=120 << 30, cfg=scfg, workers=4)
+        # warm-up, untimed: every worker's first groups (its batch's buffers and
+        # captured launches) on queries from before this rate's share
+        warm = [qs[(pos - m - 1 - i) % len(qs)] for i in range(16)]
+        for ql, qe in warm:
+            srv.submit(ql, qe)
+        got = 0
+        while got < len(warm):
+            got += len(srv.poll(256, wait_ms=100))
         done = []
         ts = time.perf_counter()
         nxt = 0.0

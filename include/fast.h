@@ -421,7 +421,8 @@ int fast_batch_config(fast_batch* b, int32_t size_class_k, fast_config* get, con
  * partition's delta_w and max_chunks (how deep the level-synchronous
  * partition goes before the depth-first matcher takes over), then the
  * matcher's launch shape (warps per CTA, CTAs per SM), each choice by the
- * wall time of batch runs over the sample.  *best_ms (nullable) receives
+ * wall time of batch runs over the sample (the better of two runs per
+ * choice).  *best_ms (nullable) receives
  * the best full-sample time.  Results stay in the batch's configuration.
  */
 int fast_batch_autotune(fast_batch* b, int32_t nq, const fast_query_desc* sample, double* best_ms, void* stream);

@@ -447,11 +447,16 @@ extern "C" int fast_batch_autotune(fast_batch* b, int32_t nq, const fast_query_d
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<uint64_t> cnt(nq);
     std::vector<int32_t> stv(nq);
+    // a choice's time: the better of two runs (the first may capture a launch)
     auto timed = [&](int m, const fast_query_desc* q, double* ms) -> int {
-        auto t0 = std::chrono::steady_clock::now();
-        int rc = batch_run(b, m, q, cnt.data(), stv.data(), s);
-        *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        return rc;
+        *ms = 1e300;
+        for (int rep = 0; rep < 2; rep++) {
+            auto t0 = std::chrono::steady_clock::now();
+            int rc = batch_run(b, m, q, cnt.data(), stv.data(), s);
+            if (rc != FAST_OK) return rc;
+            *ms = std::min(*ms, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+        }
+        return FAST_OK;
     };
     // per size class: delta_w and max_chunks (chunk size / depth of the BFS phase)
     const uint64_t dws[] = {1ull << 14, 1ull << 17, 1ull << 20, 1ull << 23};
