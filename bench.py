@@ -110,6 +110,8 @@ def parse(argv=None):
     args = p.parse_args(argv)
     if args.refine != "once" and args.build == "threads":
         p.error("--refine once_nt needs --build batched or batched-all")
+    if args.workload != "powerlaw":
+        args.autotune = False      # the tuner's sample runs would take minutes on the billion-edge graph
     return args
 
 
@@ -772,10 +774,12 @@ def run_ours(args):
 
     legs = {}
     if args.legs and world == 1:
-        legs["full_enumeration"] = full_enumeration_leg(F, torch, g, n, e, lab, bcfg, stream, flush, args.threads)
+        if args.workload == "powerlaw":
+            legs["full_enumeration"] = full_enumeration_leg(F, torch, g, n, e, lab, bcfg, stream, flush,
+                                                            args.threads)
         if args.autotune:
             legs["default_config"] = batch_leg(F, torch, g, bq, bcfg, stream, flush, 2, args.threads)
-        else:
+        elif args.workload == "powerlaw":
             legs["autotuned"] = autotuned_leg(F, torch, g, n, e, lab, bq, bcfg, stream, flush, 2, args.threads)
         # the other matching orders (the paper's path-based one among them)
         # and the other build rules, on the same step (with the tuner's picks)
