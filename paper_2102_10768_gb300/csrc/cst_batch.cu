@@ -218,6 +218,22 @@ __global__ void __launch_bounds__(256) k_any_alive_b(const AnyAliveDesc* __restr
     }
 }
 
+// {alive, rank} word pairs of a refined candidate bitmap, so that the
+// bottom-up rewrite and the non-tree step read a word and its prefix
+// popcount with one 8-byte load.
+struct PackDesc {
+    const uint32_t* alive;
+    const uint32_t* rank;
+    uint2* packed;
+};
+
+__global__ void k_pack_bits_b(const PackDesc* __restrict__ D, const int64_t* __restrict__ item_off, int nseg) {
+    for_items(item_off, nseg, [&](int s, int64_t w) {
+        const PackDesc& d = D[s];
+        d.packed[w] = make_uint2(d.alive[w], d.rank[w]);
+    });
+}
+
 // valid[r] = every child list of row r keeps an entry (as k_valid_rows_n).
 struct ValidDesc {
     ChildFlags cf;
@@ -531,6 +547,7 @@ struct Q {
     int64_t* td_off[kMaxK] = {};
     uint32_t* alive[kMaxK] = {};  // reached bitmap, then the bitmap of the refined C(u)
     uint32_t* rank[kMaxK] = {};
+    uint2* packed[kMaxK] = {};    // {alive, rank} word pairs of the refined C(u)
     uint32_t* nlfb[kMaxK] = {};   // label-frequency pass bitmaps
     int64_t* e_off = nullptr;     // the current step's edge space
     int64_t* seg = nullptr;
@@ -1031,7 +1048,7 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
                 const int w = pw[j];
                 WriteAliveF f{};
                 f.off = q.td_off[w]; f.nrows = zp(F_TD + t, qi); f.list = q.td_list[w];
-                f.alive = q.alive[w]; f.rank = q.rank[w];
+                f.alive = q.alive[w]; f.rank = q.rank[w]; f.packed = q.packed[w];
                 f.valid = valid[a]; f.newrow = newrow[a]; f.new_off = q.c->t_off[w];
                 wa.push_back({f, q.kept[w], q.c->t_idx[w], zp(F_T + q.bpos[w], qi)});
                 st.push_back({q.c->t_off[w], zp(F_C + t, qi), zp(F_T + q.bpos[w], qi)});
@@ -1075,6 +1092,18 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
                 rk.push_back({nullptr, q.alive[u], q.rank[u], nw, nullptr});
             }
             FAST_TRY(scan_seg(rk, s));
+            Carver cp;
+            for (int qi : act) cp.add(&Qs[qi].packed[Qs[qi].c->bfs[t]], nw);
+            FAST_TRY(cp.alloc(keep, false));
+            std::vector<PackDesc> pd;
+            std::vector<int64_t> pn;
+            for (int qi : act) {
+                Q& q = Qs[qi];
+                const int u = q.c->bfs[t];
+                pd.push_back({q.alive[u], q.rank[u], q.packed[u]});
+                pn.push_back(nw);
+            }
+            FAST_TRY(run_items(k_pack_bits_b, pd, pn, s));
         }
     }
     td.release();                          // top-down lists and sets: done
@@ -1147,7 +1176,7 @@ int build_all(const fast_graph* g, std::vector<Q>& Qs, cudaStream_t s) {
                 const int e = nte[j], ui = c->nt_to[e];
                 NonTreeF f{};
                 f.e_off = eo[j]; f.rows = rows[j]; f.seg = sg[j]; f.col = g->col;
-                f.alive = q.alive[ui]; f.rank = q.rank[ui]; f.n_off = c->n_off[e];
+                f.alive = q.alive[ui]; f.rank = q.rank[ui]; f.packed = q.packed[ui]; f.n_off = c->n_off[e];
                 f.E = eo[j] + rows[j];
                 cs.push_back({f, h[j], c->n_idx[e], NZ + nnp + j});
                 ft.push_back({eo[j], rows[j], NZ + nnp + j, c->n_off[e]});

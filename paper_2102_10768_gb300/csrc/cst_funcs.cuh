@@ -203,6 +203,7 @@ struct NonTreeF {
     const int32_t* col;
     const uint32_t* alive;     // bitmap of C(u_i)
     const uint32_t* rank;      // prefix popcounts of alive
+    const uint2* packed;       // nullable: {alive, rank} word pairs, one 8-byte load for both
     int64_t* n_off;
     const int64_t* E;
     int64_t row;
@@ -225,9 +226,10 @@ struct NonTreeF {
         if (i >= e_end) { v = 0; return false; }
         while (i >= e_off[row + 1]) { row++; nbase = seg[row] - e_off[row]; }
         int32_t x = col[nbase + i];
-        uint32_t w = alive[x >> 5], bit = 1u << (x & 31);
-        v = rank[x >> 5] + __popc(w & (bit - 1));
-        return (w & bit) != 0;
+        const uint2 ar = packed ? packed[x >> 5] : make_uint2(alive[x >> 5], rank[x >> 5]);
+        const uint32_t bit = 1u << (x & 31);
+        v = ar.y + __popc(ar.x & (bit - 1));
+        return (ar.x & bit) != 0;
     }
     __device__ int64_t tag(int64_t i) const { return (i < e_end && i == e_off[row]) ? first_row_at(e_off, row, i) : -1; }
     template <int N>
@@ -248,10 +250,19 @@ struct NonTreeF {
 #pragma unroll
         for (int j = 0; j < N; j++) x[j] = pos[j] >= 0 ? __ldg(col + pos[j]) : 0;
         uint32_t w[N], rk[N];
+        if (packed) {
 #pragma unroll
-        for (int j = 0; j < N; j++) {
-            w[j] = pos[j] >= 0 ? __ldg(alive + (x[j] >> 5)) : 0u;
-            rk[j] = pos[j] >= 0 ? __ldg(rank + (x[j] >> 5)) : 0u;
+            for (int j = 0; j < N; j++) {
+                const uint2 ar = pos[j] >= 0 ? __ldg(packed + (x[j] >> 5)) : make_uint2(0u, 0u);
+                w[j] = ar.x;
+                rk[j] = ar.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; j++) {
+                w[j] = pos[j] >= 0 ? __ldg(alive + (x[j] >> 5)) : 0u;
+                rk[j] = pos[j] >= 0 ? __ldg(rank + (x[j] >> 5)) : 0u;
+            }
         }
         uint32_t k = 0;
 #pragma unroll
@@ -361,6 +372,7 @@ struct WriteAliveF {
     const int32_t* list;
     const uint32_t* alive;
     const uint32_t* rank;
+    const uint2* packed;       // nullable: {alive, rank} word pairs, one 8-byte load for both
     const uint8_t* valid;
     const int64_t* newrow;
     int64_t* new_off;
@@ -385,9 +397,10 @@ struct WriteAliveF {
         while (i >= off[row + 1]) row++;
         if (!valid[row]) return false;
         int32_t x = list[i];
-        uint32_t wd = alive[x >> 5], bit = 1u << (x & 31);
-        v = rank[x >> 5] + __popc(wd & (bit - 1));
-        return (wd & bit) != 0;
+        const uint2 ar = packed ? packed[x >> 5] : make_uint2(alive[x >> 5], rank[x >> 5]);
+        const uint32_t bit = 1u << (x & 31);
+        v = ar.y + __popc(ar.x & (bit - 1));
+        return (ar.x & bit) != 0;
     }
     __device__ int64_t tag(int64_t i) const { return (i < e_end && i == off[row] && valid[row]) ? row : -1; }
     template <int N>
@@ -408,10 +421,19 @@ struct WriteAliveF {
 #pragma unroll
         for (int j = 0; j < N; j++) x[j] = ok[j] ? __ldg(list + i0 + j) : 0;
         uint32_t w[N], rk[N];
+        if (packed) {
 #pragma unroll
-        for (int j = 0; j < N; j++) {
-            w[j] = ok[j] ? __ldg(alive + (x[j] >> 5)) : 0u;
-            rk[j] = ok[j] ? __ldg(rank + (x[j] >> 5)) : 0u;
+            for (int j = 0; j < N; j++) {
+                const uint2 ar = ok[j] ? __ldg(packed + (x[j] >> 5)) : make_uint2(0u, 0u);
+                w[j] = ar.x;
+                rk[j] = ar.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; j++) {
+                w[j] = ok[j] ? __ldg(alive + (x[j] >> 5)) : 0u;
+                rk[j] = ok[j] ? __ldg(rank + (x[j] >> 5)) : 0u;
+            }
         }
         uint32_t k = 0;
 #pragma unroll
